@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Benchmark of the QMC-slicing fast kernel sum on GB300.
+
+One step = one full sum s = (1/P) sum_p [spread -> FFT filter -> interpolate]
+over one batch of synthetic inputs already resident in HBM (all stages of the
+hot path: projection of x and y, spread, FFT filter, interpolation, slice
+reduction).  The default workload is the MNIST-shaped d=784 problem:
+N=M=60000, P=2048 orthogonal directions, Laplace kernel (median rule),
+N_ft=1024, W=8.
+
+Prints ONE JSON line (rank 0).  Metric: Gpoint-slices/s = (N+M) P / time / 1e9.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload mnist_laplace|small_gauss|gauss64_negdist] [--proj fp32|...]
+                  [--no-error-check] [--no-cpu-baseline]
+
+With several GPUs (torchrun), every rank runs an independent replica of the
+workload ("replicas only": the sum needs no exchange between GPUs); the
+value is the total point-slices of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sliced kernel-sum ms & Gpoint-slices/s at fixed rel. error vs plain FP32"
+UNIT = "Gpoint-slices/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return pk, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def make_problem(name: str):
+    from paper_2410_01316_gb300 import workloads as W
+
+    if name == "mnist_laplace":
+        return W.mnist_laplace()
+    if name == "small_gauss":
+        return W.small_gauss()
+    if name == "gauss64_negdist":
+        return W.gauss64_negdist()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_desc(prob, proj):
+    return (f"{prob.name}: d={prob.d} N={prob.N} M={prob.M} P={prob.P} kernel={prob.kernel} "
+            f"N_ft={prob.n_ft} W={prob.window} proj={proj}")
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+def smi_gpu_id(dev) -> str:
+    """nvidia-smi id of a torch device (its UUID; falls back to the ordinal)."""
+    import torch
+
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev.index)
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# oracle legs (CPU)
+# ---------------------------------------------------------------------------
+def oracle_sample_rate(prob, n_slices: int, n_targets: int, threads: int = 0, seed: int = 99):
+    """Time the FP64 oracle on a bounded sample of the workload: the first
+    n_slices directions, all N sources, n_targets sampled targets.  Returns
+    (Gpoint-slices/s, seconds, description)."""
+    import oracle
+
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(prob.M, min(n_targets, prob.M), replace=False)
+    y = np.ascontiguousarray(prob.y[idx])
+    xi = np.ascontiguousarray(prob.xi[:n_slices])
+    t = oracle.tau(prob.kernel, prob.kparam, prob.R)
+    c = oracle.coeffs(prob.kernel, prob.kparam, prob.d, t, prob.n_ft)
+    t0 = time.perf_counter()
+    oracle.o1_sum(prob.x, prob.w, y, xi, t, c, threads)
+    dt = time.perf_counter() - t0
+    ps = (prob.N + y.shape[0]) * xi.shape[0]
+    desc = f"{xi.shape[0]} of {prob.P} slices, all {prob.N} sources, {y.shape[0]} of {prob.M} targets"
+    return ps / dt / 1e9, dt, desc
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle as it stands, on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    prob = make_problem(args.workload)
+    n_slices = max(1, min(prob.P, args.ref_slices))
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r, dt, desc = oracle_sample_rate(prob, n_slices, args.ref_targets, seed=1000 + i)
+        if i >= args.warmup:
+            rates.append((r, dt))
+    tot_ps = sum(r * dt for r, dt in rates)
+    tot_t = sum(dt for _, dt in rates)
+    value = tot_ps / tot_t
+    cores = host_cores()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(rates),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(prob, "oracle-fp64-direct-ndft"), "sample_per_step": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2410_01316_gb300 import QSPlan
+    from paper_2410_01316_gb300 import build as qbuild
+
+    qbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    prob = make_problem(args.workload)
+    proj = args.proj
+    plan = QSPlan(prob.d, prob.kernel, prob.P, prob.n_ft, prob.R, prob.kparam, dirs=prob.xi, window=prob.window,
+                  proj=proj, max_n=prob.N, max_m=prob.M)
+    x = torch.from_numpy(prob.x).to(dev)
+    y = torch.from_numpy(prob.y).to(dev)
+    w = torch.from_numpy(prob.w).to(dev)
+    s = torch.empty(prob.M, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    for _ in range(args.warmup):
+        plan.sum(x, w, y, out=s)
+    plan.check()
+
+    # ---- timed region: K steps, L2 flushed between steps (outside the events)
+    plan.set_timing(True)
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(smi_gpu_id(dev))
+    sampler.start()
+    time.sleep(0.3)
+    step_ms, stage_acc = [], {}
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        plan.sum(x, w, y, out=s)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        for k, v in plan.stage_times().items():
+            stage_acc[k] = stage_acc.get(k, 0.0) + v
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    dist_barrier(world)
+    plan.set_timing(False)
+    status = plan.status()
+
+    t_local = sum(step_ms) / 1e3
+    t_max = dist_max(t_local, world, dev)
+    ms_per_step = 1e3 * t_max / args.steps
+    ps_step = prob.point_slices
+    value = ps_step * args.steps * world / t_max / 1e9
+    stages = {k: v / args.steps for k, v in stage_acc.items()}
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    xh = torch.from_numpy(prob.x).pin_memory().numpy()
+    yh = torch.from_numpy(prob.y).pin_memory().numpy()
+    wh = torch.from_numpy(prob.w).pin_memory().numpy()
+    sh = torch.empty(prob.M, dtype=torch.float32).pin_memory().numpy()
+    plan.sum_host(xh, wh, yh, out=sh)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.sum_host(xh, wh, yh, out=sh)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_t = dist_max(sum(e2e_ms) / 1e3, world, dev)
+    h2d = (prob.N + prob.M) * prob.d * 4 + prob.N * 4
+    d2h = prob.M * 4
+
+    line = None
+    if rank == 0:
+        peaks, peak_src = _peaks()
+        props = torch.cuda.get_device_properties(dev)
+        sm_count = props.multi_processor_count
+        roof = roofline(prob, plan, stages, clocks, peaks, peak_src, sm_count)
+        err = None
+        err_desc = None
+        if not args.no_error_check:
+            err, err_desc = error_vs_oracle(prob, s, args.error_targets)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(prob, plan.proj), "parallelism": f"replicas{world}",
+                       "l2": "flushed between steps (256 MB write); inputs also exceed L2",
+                       "rel_err_vs_oracle": err, "rel_err_sample": err_desc,
+                       "rel_err_norm": "max_m |s - s_oracle| / (sum|w| max|F|)",
+                       "stage_ms": {k: round(v, 4) for k, v in stages.items()},
+                       "device_status": int(status)},
+            "roofline": roof,
+            "clocks": clocks,
+            "e2e": {"value": ps_step * args.steps * world / e2e_t / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": 1e3 * e2e_t / args.steps},
+            "gpu_launches": args.steps * launches_per_step(plan),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            r, dt, desc = oracle_sample_rate(prob, args.cpu_slices, args.cpu_targets)
+            line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                                    "sample": desc, "seconds": dt}
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def launches_per_step(plan) -> int:
+    return 5 if plan.proj in ("fp32", "bf16x3", "tf32") else 3
+
+
+def roofline(prob, plan, stages, clocks, peaks, peak_src, sm_count):
+    """Roofline of the dominant kernel of the step, from the in-stream events."""
+    dom = max(stages, key=lambda k: stages[k])
+    t = stages[dom] / 1e3
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    if dom in ("project_x", "project_y"):
+        rows = prob.N if dom == "project_x" else prob.M
+        flops = 2.0 * rows * prob.P * prob.d
+        if plan.proj == "fp32":
+            peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+            return {"kernel": f"projection GEMM ({dom}, FP32 SIMT)", "bound": "alu", "achieved": flops / t / 1e12,
+                    "peak": peak, "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None,
+                    "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (sampled median)",
+                    "algorithmic": f"2 N P d = {flops:.3e} flop per launch"}
+    # grid stages: algorithmic bytes = projections read + grid written / read
+    G = plan.G
+    if dom == "spread_filter":
+        byts = 4.0 * prob.N * prob.P + 4.0 * prob.N + 4.0 * prob.P * G
+        what = "4 B per source-slice (projection) + 4 N (weights) + 4 G per slice (filtered grid)"
+    elif dom == "interp":
+        byts = 4.0 * prob.M * prob.P + 4.0 * prob.P * G + 8.0 * prob.M * 1
+        what = "4 B per target-slice (projection) + 4 G per slice (filtered grid) + partials"
+    else:
+        byts = 4.0 * prob.M * 2
+        what = "partials"
+    peak = peaks["hbm_gbs"]
+    return {"kernel": dom, "bound": "hbm", "achieved": byts / t / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": byts / t / 1e9 / peak, "traffic": None, "peak_source": f"hbm_gbs ({peak_src})",
+            "algorithmic": what}
+
+
+def error_vs_oracle(prob, s, n_targets: int):
+    import oracle
+
+    idx = np.random.default_rng(4242).choice(prob.M, min(n_targets, prob.M), replace=False)
+    t = oracle.tau(prob.kernel, prob.kparam, prob.R)
+    c = oracle.coeffs(prob.kernel, prob.kparam, prob.d, t, prob.n_ft)
+    ref = oracle.o1_sum(prob.x, prob.w, np.ascontiguousarray(prob.y[idx]), prob.xi, t, c)
+    sg = s.detach().cpu().numpy().astype(np.float64)[idx]
+    norm = float(np.abs(prob.w.astype(np.float64)).sum()) * (prob.R if prob.kernel == "negdist" else 1.0)
+    return float(np.max(np.abs(sg - ref)) / norm), f"{idx.size} sampled targets, all sources and slices"
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing
+# ---------------------------------------------------------------------------
+_PG = None
+
+
+def dist_init():
+    global _PG
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        _PG = dist
+    return rank, world, local
+
+
+def dist_barrier(world):
+    if world > 1 and _PG is not None:
+        _PG.barrier()
+
+
+def dist_max(v: float, world: int, dev) -> float:
+    if world == 1 or _PG is None:
+        return v
+    import torch
+
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    _PG.all_reduce(t, op=_PG.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mnist_laplace")
+    ap.add_argument("--proj", default="fp32")
+    ap.add_argument("--no-error-check", action="store_true")
+    ap.add_argument("--error-targets", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-slices", type=int, default=128)
+    ap.add_argument("--cpu-targets", type=int, default=1024)
+    ap.add_argument("--ref-slices", type=int, default=16)
+    ap.add_argument("--ref-targets", type=int, default=1024)
+    args = ap.parse_args()
+    rank, world, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    if world > 1 and _PG is not None:
+        _PG.barrier()
+        _PG.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

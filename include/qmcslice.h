@@ -1,0 +1,185 @@
+/*
+ * qmcslice.h - C ABI of the GB300 (sm_103a) QMC-slicing fast kernel summation.
+ *
+ * Method: Hertrich, Jahn, Quellmalz, "Fast Summation of Radial Kernels via QMC
+ * Slicing", arXiv 2410.01316.  The library computes the kernel sums
+ *
+ *     s_m = sum_n w_n F(|x_n - y_m|),   m = 1..M                (Sec. 1, eq. kernel_sum)
+ *
+ * by slicing (Sec. 2.1, eq. kernel_sum_sliced): average over P directions
+ * xi_p of one-dimensional sums of the projections <x_n, xi_p>, <y_m, xi_p>
+ * with the sliced basis function f, each evaluated by one-dimensional fast
+ * Fourier summation (App. C, eq. 1d_sum_fourier; App. G, eq. Fourier-slicing):
+ *
+ *     a_{n,p} = tau <x_n, xi_p>,   b_{m,p} = tau <y_m, xi_p>
+ *     s_m ~= (1/P) sum_p Re sum_{k=-N_ft/2}^{N_ft/2-1} c_k e^{2 pi i k b_{m,p}}
+ *                            sum_n w_n e^{-2 pi i k a_{n,p}}
+ *
+ * The inner sums are computed with an oversampled grid of G = 2 N_ft cells
+ * per slice (window spreading, FFT, multiplication by c_k over the squared
+ * window transform, inverse FFT, window interpolation).
+ *
+ * Conventions shared by every entry point:
+ *  - Point arrays are row-major FP32: x is N x d, y is M x d; w has N entries,
+ *    s has M entries.  Pointers passed to qs_sum / qs_grad are DEVICE pointers
+ *    owned by the caller; the library never frees them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Argument errors are returned immediately.  Data errors detected on the
+ *    device (a projection outside the half period, a NaN/Inf input, an
+ *    exhausted wait) are recorded in the plan's device error flag and
+ *    returned by qs_check.
+ *  - No entry point throws, aborts or prints.  qs_last_error() returns a
+ *    human-readable message for the most recent failure on this thread.
+ *  - A plan may be used from one host thread at a time; calls on the same
+ *    plan must be ordered on one stream (they share the plan's workspace).
+ */
+#ifndef QMCSLICE_H
+#define QMCSLICE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qs_plan_s* qs_plan;
+
+typedef enum {
+    QS_OK = 0,
+    QS_ERR_ARG = 1,         /* invalid argument (NULL pointer, bad size, bad enum) */
+    QS_ERR_RANGE = 2,       /* a projection |tau <x, xi>| exceeded 1/2: radius too small */
+    QS_ERR_NONFINITE = 3,   /* NaN or Inf in x, y or w */
+    QS_ERR_OOM = 4,         /* device or host allocation failed (plan creation only) */
+    QS_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+    QS_ERR_UNSUPPORTED = 6, /* valid but not supported configuration */
+    QS_ERR_TIMEOUT = 7      /* a bounded device wait gave up */
+} qs_status;
+
+/* Radial kernels F (Table tab:kernels). */
+typedef enum {
+    QS_GAUSS = 0,   /* F(r) = exp(-r^2 / (2 sigma^2)),  kparam = sigma */
+    QS_LAPLACE = 1, /* F(r) = exp(-alpha r),            kparam = alpha */
+    QS_NEGDIST = 2  /* F(r) = -r (Riesz r = 1),          kparam unused  */
+} qs_kernel;
+
+/* Direction designs (Sec. 4.1, "QMC Sequences"). */
+typedef enum {
+    QS_DIR_USER = 0,       /* caller supplies P x d unit rows in dirs_host */
+    QS_DIR_FIBONACCI = 1,  /* spherical Fibonacci points, d = 3 only */
+    QS_DIR_ORTHOGONAL = 2, /* first P columns of ceil(P/d) Haar-orthogonal matrices */
+    QS_DIR_IID = 3         /* iid uniform on the sphere */
+} qs_dirs;
+
+/* Precision / form of the projection step a = tau X Xi^T. */
+typedef enum {
+    QS_PROJ_AUTO = 0,       /* library choice */
+    QS_PROJ_FP32 = 1,       /* FP32 SIMT GEMM into a P x N workspace */
+    QS_PROJ_FP32_FUSED = 2, /* FP32 dot products inside spread / interpolation (d <= 32) */
+    QS_PROJ_BF16X3 = 3,     /* tensor-core GEMM, x = hi + lo split in BF16, three products */
+    QS_PROJ_TF32 = 4        /* tensor-core GEMM in TF32 */
+} qs_proj;
+
+typedef struct {
+    int d;                 /* dimension, >= 1 */
+    qs_kernel kernel;
+    double kparam;         /* sigma (Gauss), alpha (Laplace); ignored for QS_NEGDIST */
+    int P;                 /* number of slices, >= 1 */
+    qs_dirs dirs;
+    uint64_t seed;         /* seed for QS_DIR_ORTHOGONAL / QS_DIR_IID */
+    const float* dirs_host;/* P x d host array for QS_DIR_USER (copied), else NULL */
+    int n_ft;              /* number of Fourier coefficients, power of two, 16 .. 8192 */
+    int window;            /* window taps W per point: 6, 8, 10 or 12 (0 = 8) */
+    double oversampling;   /* grid oversampling sigma_os; only 2.0 is supported (0 = 2) */
+    double radius;         /* R >= max|x_n| + max|y_m| (App. G, eq. radius_xy), > 0 */
+    qs_proj proj;
+    int64_t max_n, max_m;  /* largest N and M the plan will be called with */
+} qs_plan_desc;
+
+/*
+ * Create a plan: the rescaling factor tau (App. C Step 1 for Gauss / Laplace:
+ * tau = min(T/R, 1/(2 g_max)); App. G for the negative distance: tau =
+ * 1/(2R)), the directions, the Fourier coefficients c_k in FP64 on the device
+ * (App. C Step 2), the window tables, and all device workspace.  Runs on the
+ * current CUDA device and synchronises it.  On success *out holds the plan.
+ * Errors: QS_ERR_ARG, QS_ERR_UNSUPPORTED, QS_ERR_OOM, QS_ERR_CUDA.
+ */
+qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc);
+
+/* Release the plan and its device memory.  Synchronises the device.  NULL is a no-op. */
+qs_status qs_plan_destroy(qs_plan plan);
+
+/*
+ * Query the plan: tau (double), the grid size G, the number of slices and the
+ * device pointer of the FP32 P x d direction array used by the sums.  Any
+ * output pointer may be NULL.  The direction pointer stays valid until
+ * qs_plan_destroy.
+ */
+qs_status qs_plan_info(qs_plan plan, double* tau, int* grid_size, int* P, const float** dirs_dev);
+
+/*
+ * Copy the plan's FP32 directions (P x d, row-major) into a host buffer.
+ * Synchronous.
+ */
+qs_status qs_plan_directions(qs_plan plan, float* dirs_host);
+
+/*
+ * s = fast sliced kernel sum (the pipeline described at the top of this file).
+ * x: N x d, w: N (NULL = all weights one), y: M x d, s: M; all device memory.
+ * N <= max_n, M <= max_m.  Asynchronous on `stream`; allocates nothing and
+ * does not synchronise.  N = 0 gives s = 0; M = 0 is a no-op.
+ * Errors returned: QS_ERR_ARG, QS_ERR_CUDA (launch failure).  Data errors:
+ * qs_check.
+ */
+qs_status qs_sum(qs_plan plan, const float* x, int64_t N, const float* w,
+                 const float* y, int64_t M, float* s, void* stream);
+
+/*
+ * Same sum from HOST buffers: copies x, w, y into plan-owned device staging
+ * buffers, runs qs_sum on `stream`, copies s back into the host buffer and
+ * synchronises the stream.  Pinned host memory gives the fastest copies.
+ * Returns the data-error status as qs_check would.
+ */
+qs_status qs_sum_host(qs_plan plan, const float* x_host, int64_t N, const float* w_host,
+                      const float* y_host, int64_t M, float* s_host, void* stream);
+
+/*
+ * Synchronise `stream`, read and clear the plan's device error flag.
+ * Returns QS_OK, QS_ERR_RANGE, QS_ERR_NONFINITE, QS_ERR_TIMEOUT or QS_ERR_CUDA.
+ */
+qs_status qs_check(qs_plan plan, void* stream);
+
+/* Static English description of a status code. */
+const char* qs_status_string(qs_status status);
+
+/* Message describing the most recent failure on the calling thread ("" if none). */
+const char* qs_last_error(void);
+
+/*
+ * Host-only direction generator (no GPU needed): writes P x d unit rows into
+ * out_host for QS_DIR_FIBONACCI (d = 3), QS_DIR_ORTHOGONAL or QS_DIR_IID
+ * (Sec. 4.1).  Deterministic in `seed`.
+ */
+qs_status qs_directions(qs_dirs kind, int d, int P, uint64_t seed, float* out_host);
+
+/*
+ * Stage timing for benchmarks.  While enabled, qs_sum records a CUDA event on
+ * its stream between consecutive stages.  qs_stage_times waits for the events
+ * of the most recent qs_sum call on this plan and writes up to n stage
+ * durations in milliseconds:
+ *   [0] projection of x   [1] spread + FFT filter   [2] projection of y
+ *   [3] interpolation      [4] slice reduction
+ * Stages the plan's form does not run report 0.  Enabling creates the events
+ * (host-side driver objects, no device memory).  Do not enable while a stream
+ * that the plan uses is being captured into a CUDA graph.
+ */
+qs_status qs_set_timing(qs_plan plan, int enable);
+qs_status qs_stage_times(qs_plan plan, float* ms, int n);
+
+/* Library version string. */
+const char* qs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QMCSLICE_H */

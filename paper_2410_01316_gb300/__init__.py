@@ -1,0 +1,186 @@
+"""GB300-native fast radial kernel summation via QMC slicing (arXiv 2410.01316).
+
+Python binding of the C ABI in ``include/qmcslice.h``.  PyTorch supplies device
+memory and streams; all arithmetic runs in the CUDA library
+(``libqmcslice.so``), which must have been built (``build.build()``).
+
+    plan = QSPlan(d=3, kernel="gauss", kparam=0.5, P=64, n_ft=256, radius=2.0,
+                  dirs=xi, max_n=N, max_m=M)
+    s = plan.sum(x, w, y)          # x: (N, d), w: (N,), y: (M, d) float32 CUDA tensors
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import QSError
+
+__all__ = ["QSPlan", "QSError", "directions", "kernel_sum", "version"]
+
+
+def version() -> str:
+    return _lib.load().qs_version().decode()
+
+
+def directions(kind: str, d: int, P: int, seed: int = 0) -> np.ndarray:
+    """Host-side direction design from the library (Fibonacci / orthogonal / iid)."""
+    out = np.empty((P, d), dtype=np.float32)
+    _lib.check(_lib.load().qs_directions(_lib.DIRS[kind], d, P, seed, out.ctypes.data_as(ctypes.c_void_p)),
+               "qs_directions")
+    return out
+
+
+def _stream_handle(stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class QSPlan:
+    """A plan for sums s = sum_n w_n F(|x_n - y_m|) with fixed d, kernel, P, N_ft."""
+
+    def __init__(self, d: int, kernel: str, P: int, n_ft: int, radius: float, kparam: float = 0.0,
+                 dirs="orthogonal", seed: int = 0, window: int = 8, proj: str = "auto",
+                 max_n: int = 0, max_m: int = 0, device=None):
+        import torch
+
+        lib = _lib.load()
+        self._lib = lib
+        self._handle = ctypes.c_void_p()
+        desc = _lib.PlanDesc()
+        desc.d, desc.kernel, desc.kparam, desc.P = d, _lib.KERNELS[kernel], float(kparam), P
+        self._dirs_keep = None
+        if isinstance(dirs, str):
+            desc.dirs = _lib.DIRS[dirs]
+            desc.dirs_host = None
+        else:
+            arr = np.ascontiguousarray(dirs, dtype=np.float32)
+            if arr.shape != (P, d):
+                raise ValueError(f"dirs must have shape ({P}, {d}), got {arr.shape}")
+            self._dirs_keep = arr
+            desc.dirs = _lib.DIRS["user"]
+            desc.dirs_host = arr.ctypes.data_as(ctypes.c_void_p)
+        desc.seed = seed
+        desc.n_ft, desc.window, desc.oversampling = n_ft, window, 2.0
+        desc.radius = float(radius)
+        desc.proj = _lib.PROJ[proj]
+        desc.max_n, desc.max_m = int(max_n), int(max_m)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        with torch.cuda.device(self.device):
+            _lib.check(lib.qs_plan_create(ctypes.byref(self._handle), ctypes.byref(desc)), "qs_plan_create")
+        self.d, self.kernel, self.kparam, self.P, self.n_ft = d, kernel, kparam, P, n_ft
+        self.window, self.proj, self.max_n, self.max_m, self.radius = window, proj, max_n, max_m, radius
+        tau = ctypes.c_double()
+        G = ctypes.c_int()
+        _lib.check(lib.qs_plan_info(self._handle, ctypes.byref(tau), ctypes.byref(G), None, None), "qs_plan_info")
+        self.tau, self.G = tau.value, G.value
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "_handle", None) and self._handle.value:
+            self._lib.qs_plan_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- queries ----------------------------------------------------------
+    def directions(self) -> np.ndarray:
+        out = np.empty((self.P, self.d), dtype=np.float32)
+        _lib.check(self._lib.qs_plan_directions(self._handle, out.ctypes.data_as(ctypes.c_void_p)),
+                   "qs_plan_directions")
+        return out
+
+    # -- stage timing -----------------------------------------------------
+    STAGES = ("project_x", "spread_filter", "project_y", "interp", "reduce")
+
+    def set_timing(self, enable: bool) -> None:
+        _lib.check(self._lib.qs_set_timing(self._handle, 1 if enable else 0), "qs_set_timing")
+
+    def stage_times(self) -> dict:
+        """Stage durations (ms) of the most recent timed sum, from CUDA events."""
+        ms = (ctypes.c_float * 5)()
+        _lib.check(self._lib.qs_stage_times(self._handle, ms, 5), "qs_stage_times")
+        return dict(zip(self.STAGES, [float(v) for v in ms]))
+
+    # -- sums -------------------------------------------------------------
+    def _check_points(self, t, name, rows=None):
+        import torch
+
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+        if t.device != self.device:
+            raise ValueError(f"{name} is on {t.device}, plan on {self.device}")
+        if rows is not None and t.shape[0] != rows:
+            raise ValueError(f"{name} has {t.shape[0]} rows, expected {rows}")
+
+    def sum(self, x, w, y, out=None, stream=None):
+        """s_m = sum_n w_n F(|x_n - y_m|) on the device (asynchronous on the stream)."""
+        import torch
+
+        self._check_points(x, "x")
+        self._check_points(y, "y")
+        if x.dim() != 2 or x.shape[1] != self.d or y.dim() != 2 or y.shape[1] != self.d:
+            raise ValueError("x and y must have shape (*, d)")
+        N, M = x.shape[0], y.shape[0]
+        if w is not None:
+            self._check_points(w, "w", rows=N)
+        if out is None:
+            out = torch.empty(M, dtype=torch.float32, device=self.device)
+        else:
+            self._check_points(out, "out", rows=M)
+        _lib.check(self._lib.qs_sum(self._handle, x.data_ptr(), N, None if w is None else w.data_ptr(),
+                                    y.data_ptr(), M, out.data_ptr(), _stream_handle(stream)), "qs_sum")
+        return out
+
+    def sum_host(self, x: np.ndarray, w, y: np.ndarray, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """Same sum from host arrays (copies in, computes, copies out, synchronises)."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        wp = None
+        if w is not None:
+            w = np.ascontiguousarray(w, dtype=np.float32)
+            wp = w.ctypes.data_as(ctypes.c_void_p)
+        if out is None:
+            out = np.empty(y.shape[0], dtype=np.float32)
+        _lib.check(self._lib.qs_sum_host(self._handle, x.ctypes.data_as(ctypes.c_void_p), x.shape[0], wp,
+                                         y.ctypes.data_as(ctypes.c_void_p), y.shape[0],
+                                         out.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream)),
+                   "qs_sum_host")
+        return out
+
+    def check(self, stream=None) -> None:
+        """Synchronise and raise QSError if the device flagged a data error."""
+        _lib.check(self._lib.qs_check(self._handle, _stream_handle(stream)), "qs_check")
+
+    def status(self, stream=None) -> int:
+        """Synchronise and return the device error status without raising."""
+        return int(self._lib.qs_check(self._handle, _stream_handle(stream)))
+
+
+def kernel_sum(x, w, y, kernel: str, kparam: float = 0.0, P: int = 256, n_ft: int = 512, dirs="orthogonal",
+               seed: int = 0, radius: float | None = None, proj: str = "auto", window: int = 8):
+    """One-shot convenience wrapper: builds a plan sized for these inputs."""
+    import torch
+
+    if radius is None:
+        radius = float(x.norm(dim=1).max() + y.norm(dim=1).max()) * (1 + 1e-6)
+    with QSPlan(x.shape[1], kernel, P, n_ft, radius, kparam, dirs, seed, window, proj, x.shape[0], y.shape[0],
+                device=x.device.index) as plan:
+        s = plan.sum(x, w, y)
+        torch.cuda.current_stream().synchronize()
+        plan.check()
+        return s

@@ -1,0 +1,347 @@
+// Grid stages of the sliced fast Fourier summation (arXiv 2410.01316, App. C
+// Step 3, eq. 1d_sum_fourier; App. G, eq. Fourier-slicing):
+//
+//   coefficients  c_k = tau f^(tau k) in FP64 and the filter
+//                 D_k = c_k / psi^(k/G)^2                         (Step 2)
+//   spread        grid_p[l] = sum_n w_n psi(u_{n,p} - l)          (adjoint NFFT, window part)
+//   filter        h_p = IDFT( D . DFT(grid_p) ) restricted to |k| <= N_ft/2
+//   interpolate   t_{m,p} = sum_l h_p[l] psi(u_{m,p} - l)         (NFFT, window part)
+//   reduce        s_m = (1/P) sum_p t_{m,p}  in a fixed order with TwoSum
+//
+// The spread writes every point's W taps into a per-slice grid in shared
+// memory with shared-memory atomics; the FFT, the filter and the inverse FFT
+// run on the same shared-memory grid, so a slice touches HBM only to read its
+// projections and to write G filtered values.
+#include <math.h>
+
+#include "qs_internal.cuh"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// ---------------------------------------------------------------------------
+// FP64 Fourier coefficients (App. C Step 2; App. G), one thread per k.
+// Gauss:   f^(w) = sqrt(2) pi sigma (2 pi^2 sigma^2 w^2)^{(d-1)/2} e^{-2 pi^2 sigma^2 w^2} / Gamma(d/2)
+// Laplace: f^(w) = Gamma((d+1)/2) 2^d pi^{d-1/2} |w|^{d-1} / (Gamma(d/2) alpha^d)
+//                  (1 + 4 pi^2 w^2 / alpha^2)^{-(d+1)/2}
+// Both follow from F_1[f](w) = pi^{d/2}/Gamma(d/2) |w|^{d-1} F_d[F](|w|) and
+// are evaluated in log space (d up to the hundreds).  Negative distance: the
+// 1-periodic triangle wave -(c_d/tau)|t| with closed-form coefficients.
+// ---------------------------------------------------------------------------
+__device__ double coeff_k(int kernel, double kp, int d, double tau, int k)
+{
+    if (kernel == QS_NEGDIST) {
+        const double cd = exp(0.5 * log(kPi) + lgamma(0.5 * (d + 1)) - lgamma(0.5 * d));
+        const double amp = cd / tau;
+        if (k == 0) return -0.25 * amp;
+        if (k & 1) return amp / (kPi * kPi * (double)k * (double)k);
+        return 0.0;
+    }
+    const double w = fabs(tau * (double)k);
+    double lf;
+    if (kernel == QS_GAUSS) {
+        if (w == 0.0) return d == 1 ? tau * sqrt(2.0 * kPi) * kp : 0.0;
+        const double q = 2.0 * kPi * kPi * kp * kp * w * w;
+        lf = 0.5 * log(2.0) + log(kPi) + log(kp) + 0.5 * (d - 1) * log(q) - q - lgamma(0.5 * d);
+    } else {
+        if (w == 0.0) return d == 1 ? tau * 2.0 / kp : 0.0;
+        lf = lgamma(0.5 * (d + 1)) + d * log(2.0) + (d - 0.5) * log(kPi) + (d - 1) * log(w)
+             - lgamma(0.5 * d) - d * log(kp) - 0.5 * (d + 1) * log1p(4.0 * kPi * kPi * w * w / (kp * kp));
+    }
+    return tau * exp(lf);
+}
+
+__global__ void coeff_kernel(int kernel, double kp, int d, double tau, int n_ft, int G,
+                             const double* __restrict__ psihat, double* __restrict__ c_out,
+                             float* __restrict__ D_out)
+{
+    const int K = n_ft / 2;
+    const int Gh = G / 2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_ft) c_out[i] = coeff_k(kernel, kp, d, tau, i - K);
+    if (i <= Gh) {
+        float v = 0.0f;
+        if (i <= K) {
+            const double ph = psihat[i];
+            double dv = coeff_k(kernel, kp, d, tau, i) / (ph * ph);
+            // only k = -N_ft/2 is kept of the pair +-N_ft/2; its real part
+            // contributes half to each side of the Hermitian spectrum
+            if (i == K) dv *= 0.5;
+            v = (float)dv;
+        }
+        D_out[i] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// In-place radix-2 complex FFT of length n = G/2 in shared memory.
+// Forward uses e^{-2 pi i j / len}, inverse e^{+...}; both unnormalised.
+// tw[t] = e^{-2 pi i t / G}, t < G/2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+template <bool INV>
+__device__ void fft_inplace(float2* z, int n, int log2n, const float2* __restrict__ tw, int G)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int j = (int)(__brev((unsigned)i) >> (32 - log2n));
+        if (j > i) {
+            const float2 t = z[i];
+            z[i] = z[j];
+            z[j] = t;
+        }
+    }
+    __syncthreads();
+    for (int len = 2; len <= n; len <<= 1) {
+        const int half = len >> 1;
+        const int stride = G / len;
+        for (int b = threadIdx.x; b < (n >> 1); b += blockDim.x) {
+            const int pos = b & (half - 1);
+            const int i = ((b - pos) << 1) + pos;
+            const int j = i + half;
+            float2 wv = __ldg(&tw[pos * stride]);
+            if (INV) wv.y = -wv.y;
+            const float2 a = z[i];
+            const float2 t = cmul(z[j], wv);
+            z[i] = make_float2(a.x + t.x, a.y + t.y);
+            z[j] = make_float2(a.x - t.x, a.y - t.y);
+        }
+        __syncthreads();
+    }
+}
+
+// Real-input FFT post-processing, filter by D, and pre-processing of the
+// real-output inverse, all on the packed spectrum z (length Gh = G/2):
+//   z_j = g_{2j} + i g_{2j+1},  Z = FFT_Gh(z)
+//   X_k = (Z_k + conj Z_{Gh-k})/2 + e^{-2 pi i k/G} (Z_k - conj Z_{Gh-k})/(2i)   (k = 0..Gh)
+//   Y_k = D_k X_k
+//   Z'_k = (Y_k + conj Y_{Gh-k}) + i e^{2 pi i k/G} (Y_k - conj Y_{Gh-k})       (k < Gh)
+// so that IFFT_Gh(Z') interleaves the real sequence h_l = sum_k Y_k e^{2 pi i k l/G}.
+__device__ void real_filter(float2* z, int Gh, const float* __restrict__ D, const float2* __restrict__ tw)
+{
+    for (int k = threadIdx.x; k <= (Gh >> 1); k += blockDim.x) {
+        if (k == 0) {
+            const float2 z0 = z[0];
+            const float y0 = __ldg(&D[0]) * (z0.x + z0.y);
+            const float yh = __ldg(&D[Gh]) * (z0.x - z0.y);
+            z[0] = make_float2(y0 + yh, y0 - yh);
+            continue;
+        }
+        const int k2 = Gh - k;
+        const float2 zk = z[k];
+        const float2 zc = make_float2(z[k2].x, -z[k2].y);  // conj Z_{Gh-k}
+        const float2 A = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
+        const float2 B = make_float2(0.5f * (zk.y - zc.y), -0.5f * (zk.x - zc.x));  // -i (Zk - Zc)/2
+        const float2 t = __ldg(&tw[k]);
+        const float2 tB = cmul(t, B);
+        const float2 Xk = make_float2(A.x + tB.x, A.y + tB.y);
+        const float2 Xk2 = make_float2(A.x - tB.x, -(A.y - tB.y));  // conj(A - t B)
+        const float dk = __ldg(&D[k]);
+        const float dk2 = __ldg(&D[k2]);
+        const float2 Yk = make_float2(dk * Xk.x, dk * Xk.y);
+        const float2 Yk2 = make_float2(dk2 * Xk2.x, dk2 * Xk2.y);
+        const float2 tc = make_float2(t.x, -t.y);  // e^{+2 pi i k / G}
+        // Z'_k = (Yk + conj Yk2) + i tc (Yk - conj Yk2)
+        {
+            const float2 sum = make_float2(Yk.x + Yk2.x, Yk.y - Yk2.y);
+            const float2 dif = make_float2(Yk.x - Yk2.x, Yk.y + Yk2.y);
+            const float2 r = cmul(tc, dif);
+            z[k] = make_float2(sum.x - r.y, sum.y + r.x);
+        }
+        // Z'_{k2} = (Yk2 + conj Yk) + i (-t) (Yk2 - conj Yk)
+        {
+            const float2 sum = make_float2(Yk2.x + Yk.x, Yk2.y - Yk.y);
+            const float2 dif = make_float2(Yk2.x - Yk.x, Yk2.y + Yk.y);
+            const float2 r = cmul(make_float2(-t.x, -t.y), dif);
+            z[k2] = make_float2(sum.x - r.y, sum.y + r.x);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Spread + filter: one CTA per slice p.
+// ---------------------------------------------------------------------------
+template <int W, bool FUSED>
+__global__ void __launch_bounds__(256) spread_filter_kernel(qs_launch L, const float* __restrict__ x,
+                                                            const float* __restrict__ w)
+{
+    extern __shared__ float4 smem4[];
+    float* grid = reinterpret_cast<float*>(smem4);
+    __shared__ float xi_sm[QS_FUSED_MAX_D];
+    const int p = blockIdx.x;
+    const int G = L.G;
+    const int mask = G - 1;
+    for (int i = threadIdx.x; i < G; i += blockDim.x) grid[i] = 0.0f;
+    if (FUSED) {
+        for (int j = threadIdx.x; j < L.d; j += blockDim.x) xi_sm[j] = L.xi_s[(size_t)p * L.d + j];
+    }
+    __syncthreads();
+
+    const float* urow = L.U + (size_t)p * L.ldU;
+    for (int64_t n = threadIdx.x; n < L.N; n += blockDim.x) {
+        float u;
+        if (FUSED) {
+            const float* xn = x + (size_t)n * L.d;
+            u = 0.0f;
+            for (int j = 0; j < L.d; ++j) u = fmaf(xi_sm[j], __ldg(&xn[j]), u);
+        } else {
+            u = __ldg(&urow[n]);
+        }
+        u = qs_check_u(u, L.half_G, L.flag);
+        float wn = w ? __ldg(&w[n]) : 1.0f;
+        if (!isfinite(wn)) {
+            atomicOr(L.flag, QS_FLAG_NONFINITE);
+            wn = 0.0f;
+        }
+        int l0;
+        float tap[W];
+        qs_taps<W>(u, L.win, l0, tap);
+#pragma unroll
+        for (int j = 0; j < W; ++j) atomicAdd(&grid[(l0 + j) & mask], wn * tap[j]);
+    }
+    __syncthreads();
+
+    const int Gh = G >> 1;
+    const int log2n = 31 - __clz(Gh);
+    float2* z = reinterpret_cast<float2*>(grid);
+    fft_inplace<false>(z, Gh, log2n, L.tw, G);
+    real_filter(z, Gh, L.D, L.tw);
+    __syncthreads();
+    fft_inplace<true>(z, Gh, log2n, L.tw, G);
+
+    float4* dst = reinterpret_cast<float4*>(L.H + (size_t)p * G);
+    for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst[i] = smem4[i];
+}
+
+// ---------------------------------------------------------------------------
+// Interpolation + per-group compensated slice sums.
+// grid: (ceil(M/256), S); CTA (bx, g) handles targets bx*256.. and slices
+// [g P / S, (g+1) P / S) in increasing order.
+// ---------------------------------------------------------------------------
+template <int W, bool FUSED, int DMAX>
+__global__ void __launch_bounds__(256) interp_kernel(qs_launch L, const float* __restrict__ y)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.y;
+    const int S = gridDim.y;
+    if (m >= L.M) return;
+    const int p0 = (int)(((int64_t)g * L.P) / S);
+    const int p1 = (int)(((int64_t)(g + 1) * L.P) / S);
+    float yr[FUSED ? DMAX : 1];
+    if (FUSED) {
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j) yr[j] = j < L.d ? __ldg(&y[(size_t)m * L.d + j]) : 0.0f;
+    }
+    const int mask = L.G - 1;
+    float hi = 0.0f, lo = 0.0f;
+    for (int p = p0; p < p1; ++p) {
+        float u;
+        if (FUSED) {
+            const float* xs = L.xi_s + (size_t)p * L.d;
+            u = 0.0f;
+#pragma unroll
+            for (int j = 0; j < DMAX; ++j)
+                if (j < L.d) u = fmaf(__ldg(&xs[j]), yr[j], u);
+        } else {
+            u = __ldg(&L.U[(size_t)p * L.ldU + m]);
+        }
+        u = qs_check_u(u, L.half_G, L.flag);
+        int l0;
+        float tap[W];
+        qs_taps<W>(u, L.win, l0, tap);
+        const float* h = L.H + (size_t)p * L.G;
+        float t = 0.0f;
+#pragma unroll
+        for (int j = 0; j < W; ++j) t = fmaf(__ldg(&h[(l0 + j) & mask]), tap[j], t);
+        qs_two_sum(hi, lo, t);
+    }
+    L.part[(size_t)g * L.M + m] = hi;
+    L.part[(size_t)(S + g) * L.M + m] = lo;
+}
+
+// s_m = (1/P) sum over slice groups in increasing order (TwoSum).
+__global__ void reduce_kernel(const float* __restrict__ part, int S, int64_t M, int P, float* __restrict__ s)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    float hi = 0.0f, lo = 0.0f;
+    for (int g = 0; g < S; ++g) {
+        qs_two_sum(hi, lo, part[(size_t)g * M + m]);
+        lo += part[(size_t)(S + g) * M + m];
+    }
+    s[m] = (hi + lo) / (float)P;
+}
+
+template <int W>
+cudaError_t launch_spread_w(const qs_launch& L, const float* x, const float* w, bool fused, cudaStream_t st)
+{
+    const size_t smem = (size_t)L.G * sizeof(float);
+    auto kern = fused ? spread_filter_kernel<W, true> : spread_filter_kernel<W, false>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<L.P, 256, smem, st>>>(L, x, w);
+    return cudaGetLastError();
+}
+
+template <int W>
+cudaError_t launch_interp_w(const qs_launch& L, const float* y, bool fused, cudaStream_t st)
+{
+    dim3 grid((unsigned)((L.M + 255) / 256), (unsigned)L.S);
+    if (!fused) {
+        interp_kernel<W, false, 1><<<grid, 256, 0, st>>>(L, y);
+    } else if (L.d <= 4) {
+        interp_kernel<W, true, 4><<<grid, 256, 0, st>>>(L, y);
+    } else if (L.d <= 8) {
+        interp_kernel<W, true, 8><<<grid, 256, 0, st>>>(L, y);
+    } else if (L.d <= 16) {
+        interp_kernel<W, true, 16><<<grid, 256, 0, st>>>(L, y);
+    } else {
+        interp_kernel<W, true, 32><<<grid, 256, 0, st>>>(L, y);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t qs_launch_coeffs(int kernel, double kparam, int d, double tau, int n_ft, int G,
+                             const double* psihat, double* c_out, float* D_out, cudaStream_t st)
+{
+    const int n = (n_ft > G / 2 + 1 ? n_ft : G / 2 + 1);
+    coeff_kernel<<<(n + 127) / 128, 128, 0, st>>>(kernel, kparam, d, tau, n_ft, G, psihat, c_out, D_out);
+    return cudaGetLastError();
+}
+
+cudaError_t qs_launch_spread(const qs_launch& L, int W, const float* x, const float* w, bool fused,
+                             cudaStream_t st)
+{
+    switch (W) {
+        case 6: return launch_spread_w<6>(L, x, w, fused, st);
+        case 8: return launch_spread_w<8>(L, x, w, fused, st);
+        case 10: return launch_spread_w<10>(L, x, w, fused, st);
+        case 12: return launch_spread_w<12>(L, x, w, fused, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t qs_launch_interp(const qs_launch& L, int W, const float* y, bool fused, cudaStream_t st)
+{
+    switch (W) {
+        case 6: return launch_interp_w<6>(L, y, fused, st);
+        case 8: return launch_interp_w<8>(L, y, fused, st);
+        case 10: return launch_interp_w<10>(L, y, fused, st);
+        case 12: return launch_interp_w<12>(L, y, fused, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t qs_launch_reduce(const qs_launch& L, float* s, cudaStream_t st)
+{
+    reduce_kernel<<<(unsigned)((L.M + 255) / 256), 256, 0, st>>>(L.part, L.S, L.M, L.P, s);
+    return cudaGetLastError();
+}

@@ -1,0 +1,153 @@
+// Internal declarations shared by the CUDA sources of the qmcslice library.
+//
+// Notation (arXiv 2410.01316, App. C and App. G): a plan holds P directions
+// xi_p, the rescaling factor tau, N_ft Fourier coefficients c_k and an
+// oversampled grid of G = 2 N_ft cells per slice.  Projections are kept in
+// grid units, u = G tau <x, xi_p>, so one grid cell has width 1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qmcslice.h"
+
+// device error flag bits (qs_check maps them to qs_status)
+#define QS_FLAG_RANGE 1u
+#define QS_FLAG_NONFINITE 2u
+#define QS_FLAG_TIMEOUT 4u
+
+// Window: exponential of semicircle psi(v) = exp(beta (sqrt(1 - (v/m)^2) - 1))
+// on |v| < m = W/2 grid cells.  Each point touches W cells; the W tap values
+// are piecewise polynomials of the fractional offset.
+constexpr int QS_MAX_W = 12;
+constexpr int QS_MAX_HALF = QS_MAX_W / 2;
+constexpr int QS_MAX_TERMS = QS_MAX_HALF + 1;  // terms per even / odd part
+constexpr int QS_MAX_G = 16384;                // grid cells per slice (64 KB shared)
+constexpr int QS_FUSED_MAX_D = 32;             // largest d of the fused form
+
+// Tap polynomials.  For tap j of the first half (0 <= j < m), with the
+// centred fractional offset s in [-1/2, 1/2]:
+//   psi(s + m - 1/2 - j)         = E_j(s^2) + s O_j(s^2)
+//   psi(s + m - 1/2 - (W-1-j))   = E_j(s^2) - s O_j(s^2)   (psi is even)
+struct qs_window {
+    float e[QS_MAX_HALF][QS_MAX_TERMS];
+    float o[QS_MAX_HALF][QS_MAX_TERMS];
+};
+
+// Everything a launch of the sum pipeline needs (passed by value).
+struct qs_launch {
+    int d, P, G, n_ft;
+    int64_t N, M;
+    int64_t ldU;          // row stride (elements) of the P x ldU projection workspace
+    float half_G;         // |u| must stay <= G/2 (the half period)
+    const float* xi_s;    // P x d, directions scaled by G tau
+    const float* D;       // G/2 + 1 filter weights c_k / psi^(k/G)^2, 0 beyond N_ft/2
+    const float2* tw;     // G/2 twiddles e^{-2 pi i t / G}
+    float* H;             // P x G filtered grids
+    float* U;             // P x ldU projections (unfused forms)
+    float* part;          // 2 x S x M partial slice sums (hi, lo)
+    int S;                // number of slice groups of the interpolation
+    unsigned int* flag;   // device error flag
+    qs_window win;
+};
+
+struct qs_plan_s {
+    int device;
+    int sm_count;
+    qs_plan_desc desc;    // copy; dirs_host cleared
+    qs_proj proj;         // resolved form
+    double tau;
+    int G, W;
+    double beta;
+    int64_t ldU;
+    int S_max;            // slice-group capacity of the partial buffer
+    size_t U_elems;
+    qs_window win;
+    // device buffers
+    float* d_dirs;        // P x d
+    float* d_dirs_s;      // P x d scaled by G tau
+    double* d_c;          // n_ft coefficients c_k, k = -n_ft/2 .. n_ft/2-1
+    double* d_psihat;     // n_ft/2 + 1 window transform values (FP64)
+    float* d_D;           // G/2 + 1
+    float2* d_tw;         // G/2
+    float* d_U;
+    float* d_H;
+    float* d_part;
+    unsigned int* d_flag;
+    // staging for qs_sum_host
+    float* d_x;
+    float* d_w;
+    float* d_y;
+    float* d_s;
+    // tensor-core projection operands (BF16 split of the scaled directions)
+    void* d_xi_hi;
+    void* d_xi_lo;
+    void* d_xsplit;       // N x 3d (or M x 3d) BF16 staging of the split points
+    int64_t xsplit_rows;
+    // stage timing (qs_set_timing)
+    int timing;
+    int timed_calls;
+    cudaEvent_t ev[6];
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+// Tap values and first cell of a point at grid coordinate u.
+//   l0 = ceil(u - m),  s = u - l0 - (m - 1/2) in (-1/2, 1/2]
+//   tap[j] = psi(u - (l0 + j)),  j = 0 .. W-1
+template <int W>
+__device__ __forceinline__ void qs_taps(float u, const qs_window& win, int& l0, float (&tap)[W])
+{
+    constexpr int m = W / 2;
+    constexpr int T = m + 1;
+    const float fl = ceilf(u - (float)m);
+    l0 = (int)fl;
+    const float s = (u - fl) - ((float)m - 0.5f);
+    const float s2 = s * s;
+#pragma unroll
+    for (int j = 0; j < m; ++j) {
+        float e = win.e[j][T - 1];
+        float o = win.o[j][T - 1];
+#pragma unroll
+        for (int i = T - 2; i >= 0; --i) {
+            e = fmaf(e, s2, win.e[j][i]);
+            o = fmaf(o, s2, win.o[j][i]);
+        }
+        tap[j] = fmaf(s, o, e);
+        tap[W - 1 - j] = fmaf(-s, o, e);
+    }
+}
+
+// Error-free transformation of a + b (Knuth's TwoSum); the rounding error is
+// accumulated into lo.  No multiplications, so FMA contraction cannot alter it.
+__device__ __forceinline__ void qs_two_sum(float& hi, float& lo, float x)
+{
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+}
+
+// Validate a grid coordinate; returns a safe value and records the error.
+__device__ __forceinline__ float qs_check_u(float u, float half_G, unsigned int* flag)
+{
+    if (!(fabsf(u) <= half_G)) {
+        atomicOr(flag, (u != u || isinf(u)) ? QS_FLAG_NONFINITE : QS_FLAG_RANGE);
+        return 0.0f;
+    }
+    return u;
+}
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the .cu files); return cudaSuccess or the launch error
+// ---------------------------------------------------------------------------
+cudaError_t qs_launch_coeffs(int kernel, double kparam, int d, double tau, int n_ft, int G,
+                             const double* psihat, double* c_out, float* D_out, cudaStream_t st);
+cudaError_t qs_launch_project_fp32(const float* X, int64_t N, int d, const float* xi_s, int P,
+                                   float* U, int64_t ldU, cudaStream_t st);
+cudaError_t qs_launch_spread(const qs_launch& L, int W, const float* x, const float* w, bool fused,
+                             cudaStream_t st);
+cudaError_t qs_launch_interp(const qs_launch& L, int W, const float* y, bool fused, cudaStream_t st);
+cudaError_t qs_launch_reduce(const qs_launch& L, float* s, cudaStream_t st);

@@ -1,0 +1,665 @@
+// Host side of the qmcslice C ABI: plans, directions, window tables and the
+// orchestration of the sum pipeline (arXiv 2410.01316, App. C / App. G).
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "qs_internal.cuh"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+thread_local char g_last_error[512] = "";
+
+qs_status fail(qs_status st, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+qs_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(QS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess) ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// seeded host random numbers: splitmix64 stream -> uniform (0,1) -> Box-Muller
+// ---------------------------------------------------------------------------
+struct HostRng {
+    uint64_t state;
+    explicit HostRng(uint64_t seed) : state(seed ^ 0x6a09e667f3bcc909ULL) {}
+    uint64_t next()
+    {
+        uint64_t z = (state += 0x9e3779b97f4a7c15ULL);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return ((double)(next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+    double normal()
+    {
+        const double u1 = uniform(), u2 = uniform();
+        return sqrt(-2.0 * log(u1)) * cos(2.0 * kPi * u2);
+    }
+};
+
+// Haar-distributed d x d orthogonal matrix (column-major in q): Householder
+// QR of a Gaussian matrix, with column i multiplied by sign(R_ii).
+void haar_orthogonal(HostRng& rng, int d, std::vector<double>& q)
+{
+    std::vector<double> a((size_t)d * d);
+    for (auto& v : a) v = rng.normal();  // a[i + j*d] = A(i, j)
+    std::vector<double> vs((size_t)d * d, 0.0), rdiag(d);
+    for (int k = 0; k < d; ++k) {
+        double nrm = 0.0;
+        for (int i = k; i < d; ++i) nrm += a[i + (size_t)k * d] * a[i + (size_t)k * d];
+        nrm = sqrt(nrm);
+        const double akk = a[k + (size_t)k * d];
+        const double alpha = akk > 0 ? -nrm : nrm;  // R_kk
+        rdiag[k] = alpha;
+        double* v = &vs[(size_t)k * d];
+        for (int i = 0; i < d; ++i) v[i] = 0.0;
+        for (int i = k; i < d; ++i) v[i] = a[i + (size_t)k * d];
+        v[k] -= alpha;
+        double vn = 0.0;
+        for (int i = k; i < d; ++i) vn += v[i] * v[i];
+        if (vn > 0.0) {
+            const double inv = 1.0 / sqrt(vn);
+            for (int i = k; i < d; ++i) v[i] *= inv;
+            for (int j = k; j < d; ++j) {  // A <- (I - 2 v v^T) A
+                double dot = 0.0;
+                for (int i = k; i < d; ++i) dot += v[i] * a[i + (size_t)j * d];
+                for (int i = k; i < d; ++i) a[i + (size_t)j * d] -= 2.0 * dot * v[i];
+            }
+        }
+    }
+    // Q = H_0 H_1 ... H_{d-1}, accumulated backwards on the identity
+    q.assign((size_t)d * d, 0.0);
+    for (int i = 0; i < d; ++i) q[i + (size_t)i * d] = 1.0;
+    for (int k = d - 1; k >= 0; --k) {
+        const double* v = &vs[(size_t)k * d];
+        for (int j = 0; j < d; ++j) {
+            double dot = 0.0;
+            for (int i = k; i < d; ++i) dot += v[i] * q[i + (size_t)j * d];
+            for (int i = k; i < d; ++i) q[i + (size_t)j * d] -= 2.0 * dot * v[i];
+        }
+    }
+    for (int j = 0; j < d; ++j) {
+        const double sg = rdiag[j] < 0 ? -1.0 : 1.0;
+        for (int i = 0; i < d; ++i) q[i + (size_t)j * d] *= sg;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// window: exponential of semicircle on |v| < m, beta = 2.30 W for sigma_os = 2
+// ---------------------------------------------------------------------------
+double es_window(double v, int m, double beta)
+{
+    const double z = v / m;
+    if (fabs(z) >= 1.0) return 0.0;
+    return exp(beta * (sqrt(1.0 - z * z) - 1.0));
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on P_n.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w)
+{
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double t = cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int j = 1; j < n; ++j) {
+                const double p2 = ((2.0 * j + 1.0) * t * p1 - j * p0) / (j + 1.0);
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+            const double dt = p1 / dp;
+            t -= dt;
+            if (fabs(dt) < 1e-16) break;
+        }
+        x[i] = t;
+        w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
+// Fit the tap polynomials: Chebyshev interpolation of degree W+1 on
+// s in [-1/2, 1/2] for each tap of the first half, conversion to monomials
+// in s, split into even and odd parts.
+void fit_window(int W, double beta, qs_window& win)
+{
+    const int m = W / 2;
+    const int deg = W + 1;
+    const int n = deg + 1;
+    memset(&win, 0, sizeof(win));
+    // T_k(2s) as monomials in s: tm[k][i]
+    std::vector<std::vector<double>> tm(n, std::vector<double>(n, 0.0));
+    tm[0][0] = 1.0;
+    if (n > 1) tm[1][1] = 2.0;
+    for (int k = 2; k < n; ++k) {
+        for (int i = 0; i < n; ++i) {
+            double v = -tm[k - 2][i];
+            if (i > 0) v += 4.0 * tm[k - 1][i - 1];  // 2 * (2s) * T_{k-1}
+            tm[k][i] = v;
+        }
+    }
+    for (int j = 0; j < m; ++j) {
+        std::vector<double> cheb(n, 0.0), fval(n);
+        for (int i = 0; i < n; ++i) {
+            const double th = kPi * (i + 0.5) / n;
+            fval[i] = es_window(0.5 * cos(th) + m - 0.5 - j, m, beta);
+        }
+        for (int k = 0; k < n; ++k) {
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) acc += fval[i] * cos(k * kPi * (i + 0.5) / n);
+            cheb[k] = (k == 0 ? 1.0 : 2.0) * acc / n;
+        }
+        std::vector<double> mono(n, 0.0);
+        for (int k = 0; k < n; ++k)
+            for (int i = 0; i < n; ++i) mono[i] += cheb[k] * tm[k][i];
+        for (int i = 0; i < n; ++i) {
+            if (i % 2 == 0) win.e[j][i / 2] = (float)mono[i];
+            else win.o[j][i / 2] = (float)mono[i];
+        }
+    }
+}
+
+// Evaluate the FP32 tap polynomials (in double) for offset s and tap j.
+double window_tap(const qs_window& win, int W, int j, double s)
+{
+    const int m = W / 2;
+    const int T = m + 1;
+    const int jj = j < m ? j : W - 1 - j;
+    const double ss = j < m ? s : -s;
+    double e = 0.0, o = 0.0;
+    for (int i = T - 1; i >= 0; --i) {
+        e = e * ss * ss + (double)win.e[jj][i];
+        o = o * ss * ss + (double)win.o[jj][i];
+    }
+    return e + ss * o;
+}
+
+// Fourier transform (grid units) of the window as the GPU applies it:
+// psi_eff(v) = p_j(v - (m - 1/2 - j)) on the j-th unit cell.  Even, so
+// psi^(nu) = sum_j int_{-1/2}^{1/2} p_j(s) cos(2 pi nu (s + m - 1/2 - j)) ds.
+void window_transform(const qs_window& win, int W, int K, int G, std::vector<double>& out)
+{
+    const int m = W / 2;
+    std::vector<double> gx, gw;
+    gauss_legendre(24, gx, gw);
+    std::vector<double> tap((size_t)W * gx.size());
+    for (int j = 0; j < W; ++j)
+        for (size_t q = 0; q < gx.size(); ++q) tap[(size_t)j * gx.size() + q] = window_tap(win, W, j, 0.5 * gx[q]);
+    out.assign(K + 1, 0.0);
+    for (int k = 0; k <= K; ++k) {
+        const double nu = (double)k / G;
+        double acc = 0.0;
+        for (int j = 0; j < W; ++j) {
+            const double c = m - 0.5 - j;
+            for (size_t q = 0; q < gx.size(); ++q) {
+                const double s = 0.5 * gx[q];
+                acc += 0.5 * gw[q] * tap[(size_t)j * gx.size() + q] * cos(2.0 * kPi * nu * (s + c));
+            }
+        }
+        out[k] = acc;
+    }
+}
+
+// Rescaling factor (App. C Step 1; App. G for the negative distance).
+double tau_rule(qs_kernel kernel, double kparam, double R)
+{
+    switch (kernel) {
+        case QS_GAUSS: return fmin(0.3 / R, 1.0 / (2.0 * 5.0 * kparam));
+        case QS_LAPLACE: return fmin(0.1 / R, 1.0 / (2.0 * 5.0 / kparam));
+        case QS_NEGDIST: return 1.0 / (2.0 * R);
+    }
+    return -1.0;
+}
+
+void free_plan(qs_plan p)
+{
+    if (!p) return;
+    for (int i = 0; i < 6; ++i)
+        if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+    void* bufs[] = {p->d_dirs, p->d_dirs_s, p->d_c, p->d_psihat, p->d_D, p->d_tw, p->d_U, p->d_H,
+                    p->d_part, p->d_flag, p->d_x, p->d_w, p->d_y, p->d_s, p->d_xi_hi, p->d_xi_lo,
+                    p->d_xsplit};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete p;
+}
+
+template <class T>
+cudaError_t dalloc(T** ptr, size_t count)
+{
+    *ptr = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc((void**)ptr, count * sizeof(T));
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+qs_launch make_launch(const qs_plan p, int64_t N, int64_t M)
+{
+    qs_launch L;
+    memset(&L, 0, sizeof(L));
+    L.d = p->desc.d;
+    L.P = p->desc.P;
+    L.G = p->G;
+    L.n_ft = p->desc.n_ft;
+    L.N = N;
+    L.M = M;
+    L.ldU = p->ldU;
+    L.half_G = 0.5f * (float)p->G;
+    L.xi_s = p->d_dirs_s;
+    L.D = p->d_D;
+    L.tw = p->d_tw;
+    L.H = p->d_H;
+    L.U = p->d_U;
+    L.part = p->d_part;
+    L.flag = p->d_flag;
+    L.win = p->win;
+    // slice groups of the interpolation: enough CTAs to fill the device,
+    // chosen from M and P only so results do not depend on the GPU model
+    const int64_t blocks_m = (M + 255) / 256;
+    int64_t S = (1024 + blocks_m - 1) / (blocks_m > 0 ? blocks_m : 1);
+    if (S < 1) S = 1;
+    if (S > p->S_max) S = p->S_max;
+    L.S = (int)S;
+    return L;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* qs_version(void) { return "qmcslice 0.1 (sm_103a)"; }
+
+const char* qs_last_error(void) { return g_last_error; }
+
+const char* qs_status_string(qs_status s)
+{
+    switch (s) {
+        case QS_OK: return "ok";
+        case QS_ERR_ARG: return "invalid argument";
+        case QS_ERR_RANGE: return "projection outside the half period (radius too small)";
+        case QS_ERR_NONFINITE: return "non-finite input value";
+        case QS_ERR_OOM: return "out of memory";
+        case QS_ERR_CUDA: return "CUDA runtime error";
+        case QS_ERR_UNSUPPORTED: return "unsupported configuration";
+        case QS_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+qs_status qs_directions(qs_dirs kind, int d, int P, uint64_t seed, float* out)
+{
+    if (!out || d < 1 || P < 1) return fail(QS_ERR_ARG, "qs_directions: bad arguments");
+    if (kind == QS_DIR_FIBONACCI) {
+        if (d != 3) return fail(QS_ERR_ARG, "qs_directions: Fibonacci directions need d = 3");
+        const double golden = 0.5 * (1.0 + sqrt(5.0));
+        for (int p = 0; p < P; ++p) {
+            const double z = 1.0 - (2.0 * p + 1.0) / P;
+            const double phi = 2.0 * kPi * p / golden;
+            const double r = sqrt(fmax(0.0, 1.0 - z * z));
+            out[3 * p + 0] = (float)(r * cos(phi));
+            out[3 * p + 1] = (float)(r * sin(phi));
+            out[3 * p + 2] = (float)z;
+        }
+        return QS_OK;
+    }
+    HostRng rng(seed);
+    if (kind == QS_DIR_IID) {
+        std::vector<double> g(d);
+        for (int p = 0; p < P; ++p) {
+            double nrm = 0.0;
+            for (int j = 0; j < d; ++j) {
+                g[j] = rng.normal();
+                nrm += g[j] * g[j];
+            }
+            nrm = sqrt(nrm);
+            for (int j = 0; j < d; ++j) out[(size_t)p * d + j] = (float)(g[j] / nrm);
+        }
+        return QS_OK;
+    }
+    if (kind == QS_DIR_ORTHOGONAL) {
+        std::vector<double> q;
+        for (int p0 = 0; p0 < P; p0 += d) {
+            haar_orthogonal(rng, d, q);
+            for (int c = 0; c < d && p0 + c < P; ++c)
+                for (int j = 0; j < d; ++j) out[(size_t)(p0 + c) * d + j] = (float)q[j + (size_t)c * d];
+        }
+        return QS_OK;
+    }
+    return fail(QS_ERR_ARG, "qs_directions: unknown kind %d", (int)kind);
+}
+
+qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
+{
+    if (!out || !desc) return fail(QS_ERR_ARG, "qs_plan_create: NULL argument");
+    *out = nullptr;
+    const qs_plan_desc& D = *desc;
+    if (D.d < 1 || D.P < 1) return fail(QS_ERR_ARG, "qs_plan_create: d and P must be >= 1");
+    if (D.kernel != QS_GAUSS && D.kernel != QS_LAPLACE && D.kernel != QS_NEGDIST)
+        return fail(QS_ERR_ARG, "qs_plan_create: unknown kernel %d", (int)D.kernel);
+    if (D.kernel != QS_NEGDIST && !(D.kparam > 0.0 && isfinite(D.kparam)))
+        return fail(QS_ERR_ARG, "qs_plan_create: kernel parameter must be positive");
+    if (!(D.radius > 0.0 && isfinite(D.radius))) return fail(QS_ERR_ARG, "qs_plan_create: radius must be > 0");
+    if (!is_pow2(D.n_ft) || D.n_ft < 16 || D.n_ft > QS_MAX_G / 2)
+        return fail(QS_ERR_UNSUPPORTED, "qs_plan_create: n_ft must be a power of two in [16, %d]", QS_MAX_G / 2);
+    const int W = D.window == 0 ? 8 : D.window;
+    if (W != 6 && W != 8 && W != 10 && W != 12)
+        return fail(QS_ERR_UNSUPPORTED, "qs_plan_create: window must be 6, 8, 10 or 12");
+    const double os = D.oversampling == 0.0 ? 2.0 : D.oversampling;
+    if (os != 2.0) return fail(QS_ERR_UNSUPPORTED, "qs_plan_create: only oversampling 2 is supported");
+    if (D.max_n < 0 || D.max_m < 0) return fail(QS_ERR_ARG, "qs_plan_create: max_n / max_m must be >= 0");
+    if (D.dirs == QS_DIR_USER && !D.dirs_host) return fail(QS_ERR_ARG, "qs_plan_create: dirs_host is NULL");
+    if (D.dirs == QS_DIR_FIBONACCI && D.d != 3)
+        return fail(QS_ERR_ARG, "qs_plan_create: Fibonacci directions need d = 3");
+
+    qs_proj proj = D.proj;
+    if (proj == QS_PROJ_AUTO) proj = D.d <= 16 ? QS_PROJ_FP32_FUSED : QS_PROJ_FP32;
+    if (proj == QS_PROJ_FP32_FUSED && D.d > QS_FUSED_MAX_D)
+        return fail(QS_ERR_UNSUPPORTED, "qs_plan_create: fused projection needs d <= %d", QS_FUSED_MAX_D);
+    if (proj != QS_PROJ_FP32 && proj != QS_PROJ_FP32_FUSED)
+        return fail(QS_ERR_UNSUPPORTED, "qs_plan_create: projection form %d not available", (int)proj);
+
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "qs_plan_create: cudaGetDevice");
+    int sms = 0;
+    ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "qs_plan_create: device attribute");
+
+    qs_plan p = new (std::nothrow) qs_plan_s;
+    if (!p) return fail(QS_ERR_OOM, "qs_plan_create: host allocation");
+    memset(p, 0, sizeof(*p));
+    p->device = dev;
+    p->sm_count = sms;
+    p->desc = D;
+    p->desc.dirs_host = nullptr;
+    p->desc.window = W;
+    p->desc.oversampling = os;
+    p->proj = proj;
+    p->W = W;
+    p->G = 2 * D.n_ft;
+    p->beta = 2.30 * W;
+    p->tau = tau_rule(D.kernel, D.kparam, D.radius);
+    p->S_max = D.P < 64 ? D.P : 64;
+    const int64_t maxnm = D.max_n > D.max_m ? D.max_n : D.max_m;
+    p->ldU = ((maxnm + 127) / 128) * 128;
+    if (p->ldU == 0) p->ldU = 128;
+    const int G = p->G, K = D.n_ft / 2, d = D.d, P = D.P;
+
+    // directions (host), FP32
+    std::vector<float> dirs((size_t)P * d);
+    if (D.dirs == QS_DIR_USER) {
+        for (size_t i = 0; i < dirs.size(); ++i) {
+            if (!isfinite(desc->dirs_host[i])) {
+                free_plan(p);
+                return fail(QS_ERR_ARG, "qs_plan_create: non-finite direction entry");
+            }
+            dirs[i] = desc->dirs_host[i];
+        }
+    } else {
+        qs_status st = qs_directions(D.dirs, d, P, D.seed, dirs.data());
+        if (st != QS_OK) {
+            free_plan(p);
+            return st;
+        }
+    }
+    std::vector<float> dirs_s(dirs.size());
+    const double scale = (double)G * p->tau;
+    for (size_t i = 0; i < dirs.size(); ++i) dirs_s[i] = (float)(scale * (double)dirs[i]);
+
+    // window tables
+    fit_window(W, p->beta, p->win);
+    std::vector<double> psihat;
+    window_transform(p->win, W, K, G, psihat);
+    std::vector<float2> tw(G / 2);
+    for (int t = 0; t < G / 2; ++t) {
+        const double ang = 2.0 * kPi * (double)t / (double)G;
+        tw[t] = make_float2((float)cos(ang), (float)(-sin(ang)));
+    }
+
+    // device buffers
+#define QS_ALLOC(ptr, n)                                                       \
+    do {                                                                       \
+        cudaError_t e_ = dalloc(&(ptr), (n));                                  \
+        if (e_ != cudaSuccess) {                                               \
+            cudaGetLastError();                                                \
+            free_plan(p);                                                      \
+            return fail(QS_ERR_OOM, "qs_plan_create: cudaMalloc(%s, %zu B): %s", #ptr, \
+                        (size_t)(n) * sizeof(*(ptr)), cudaGetErrorString(e_)); \
+        }                                                                      \
+    } while (0)
+    QS_ALLOC(p->d_dirs, (size_t)P * d);
+    QS_ALLOC(p->d_dirs_s, (size_t)P * d);
+    QS_ALLOC(p->d_c, (size_t)D.n_ft);
+    QS_ALLOC(p->d_psihat, (size_t)K + 1);
+    QS_ALLOC(p->d_D, (size_t)G / 2 + 1);
+    QS_ALLOC(p->d_tw, (size_t)G / 2);
+    QS_ALLOC(p->d_H, (size_t)P * G);
+    QS_ALLOC(p->d_part, (size_t)2 * p->S_max * (D.max_m > 0 ? D.max_m : 1));
+    QS_ALLOC(p->d_flag, 1);
+    if (proj == QS_PROJ_FP32) {
+        p->U_elems = (size_t)P * (size_t)p->ldU;
+        QS_ALLOC(p->d_U, p->U_elems);
+    }
+    QS_ALLOC(p->d_x, (size_t)(D.max_n > 0 ? D.max_n : 1) * d);
+    QS_ALLOC(p->d_w, (size_t)(D.max_n > 0 ? D.max_n : 1));
+    QS_ALLOC(p->d_y, (size_t)(D.max_m > 0 ? D.max_m : 1) * d);
+    QS_ALLOC(p->d_s, (size_t)(D.max_m > 0 ? D.max_m : 1));
+#undef QS_ALLOC
+
+#define QS_CHECK(call, what)          \
+    do {                              \
+        cudaError_t e_ = (call);      \
+        if (e_ != cudaSuccess) {      \
+            free_plan(p);             \
+            return cuda_fail(e_, what); \
+        }                             \
+    } while (0)
+    QS_CHECK(cudaMemcpy(p->d_dirs, dirs.data(), dirs.size() * sizeof(float), cudaMemcpyHostToDevice), "copy dirs");
+    QS_CHECK(cudaMemcpy(p->d_dirs_s, dirs_s.data(), dirs_s.size() * sizeof(float), cudaMemcpyHostToDevice),
+             "copy scaled dirs");
+    QS_CHECK(cudaMemcpy(p->d_psihat, psihat.data(), psihat.size() * sizeof(double), cudaMemcpyHostToDevice),
+             "copy window transform");
+    QS_CHECK(cudaMemcpy(p->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice), "copy twiddles");
+    QS_CHECK(cudaMemset(p->d_flag, 0, sizeof(unsigned int)), "clear flag");
+    QS_CHECK(qs_launch_coeffs((int)D.kernel, D.kparam, d, p->tau, D.n_ft, G, p->d_psihat, p->d_c, p->d_D, 0),
+             "coefficient kernel launch");
+    QS_CHECK(cudaDeviceSynchronize(), "coefficient kernel");
+#undef QS_CHECK
+    *out = p;
+    g_last_error[0] = 0;
+    return QS_OK;
+}
+
+qs_status qs_plan_destroy(qs_plan p)
+{
+    if (!p) return QS_OK;
+    DeviceGuard g(p->device);
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return QS_OK;
+}
+
+qs_status qs_plan_info(qs_plan p, double* tau, int* grid_size, int* P, const float** dirs_dev)
+{
+    if (!p) return fail(QS_ERR_ARG, "qs_plan_info: NULL plan");
+    if (tau) *tau = p->tau;
+    if (grid_size) *grid_size = p->G;
+    if (P) *P = p->desc.P;
+    if (dirs_dev) *dirs_dev = p->d_dirs;
+    return QS_OK;
+}
+
+qs_status qs_plan_directions(qs_plan p, float* dirs_host)
+{
+    if (!p || !dirs_host) return fail(QS_ERR_ARG, "qs_plan_directions: NULL argument");
+    DeviceGuard g(p->device);
+    cudaError_t e = cudaMemcpy(dirs_host, p->d_dirs, (size_t)p->desc.P * p->desc.d * sizeof(float),
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_plan_directions");
+    return QS_OK;
+}
+
+qs_status qs_sum(qs_plan p, const float* x, int64_t N, const float* w, const float* y, int64_t M, float* s,
+                 void* stream)
+{
+    if (!p) return fail(QS_ERR_ARG, "qs_sum: NULL plan");
+    if (N < 0 || M < 0) return fail(QS_ERR_ARG, "qs_sum: negative size");
+    if (N > p->desc.max_n || M > p->desc.max_m)
+        return fail(QS_ERR_ARG, "qs_sum: N=%lld / M=%lld exceed the plan's max_n=%lld / max_m=%lld",
+                    (long long)N, (long long)M, (long long)p->desc.max_n, (long long)p->desc.max_m);
+    if ((N > 0 && !x) || (M > 0 && (!y || !s))) return fail(QS_ERR_ARG, "qs_sum: NULL data pointer");
+    if (M == 0) return QS_OK;
+    DeviceGuard g(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (N == 0) {
+        e = cudaMemsetAsync(s, 0, (size_t)M * sizeof(float), st);
+        return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_sum: memset");
+    }
+    qs_launch L = make_launch(p, N, M);
+    const bool fused = p->proj == QS_PROJ_FP32_FUSED;
+    const bool tm = p->timing != 0;
+#define QS_MARK(i)                                              \
+    do {                                                        \
+        if (tm) {                                               \
+            e = cudaEventRecord(p->ev[i], st);                  \
+            if (e != cudaSuccess) return cuda_fail(e, "qs_sum: timing event"); \
+        }                                                       \
+    } while (0)
+    QS_MARK(0);
+    if (!fused) {
+        e = qs_launch_project_fp32(x, N, L.d, p->d_dirs_s, L.P, p->d_U, p->ldU, st);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_sum: projection of x");
+    }
+    QS_MARK(1);
+    e = qs_launch_spread(L, p->W, x, w, fused, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_sum: spread");
+    QS_MARK(2);
+    if (!fused) {
+        e = qs_launch_project_fp32(y, M, L.d, p->d_dirs_s, L.P, p->d_U, p->ldU, st);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_sum: projection of y");
+    }
+    QS_MARK(3);
+    e = qs_launch_interp(L, p->W, y, fused, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_sum: interpolation");
+    QS_MARK(4);
+    e = qs_launch_reduce(L, s, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_sum: reduction");
+    QS_MARK(5);
+#undef QS_MARK
+    if (tm) p->timed_calls++;
+    return QS_OK;
+}
+
+qs_status qs_set_timing(qs_plan p, int enable)
+{
+    if (!p) return fail(QS_ERR_ARG, "qs_set_timing: NULL plan");
+    DeviceGuard g(p->device);
+    if (enable && !p->ev[0]) {
+        for (int i = 0; i < 6; ++i) {
+            cudaError_t e = cudaEventCreate(&p->ev[i]);
+            if (e != cudaSuccess) return cuda_fail(e, "qs_set_timing: cudaEventCreate");
+        }
+    }
+    p->timing = enable ? 1 : 0;
+    p->timed_calls = 0;
+    return QS_OK;
+}
+
+qs_status qs_stage_times(qs_plan p, float* ms, int n)
+{
+    if (!p || !ms || n < 0) return fail(QS_ERR_ARG, "qs_stage_times: bad argument");
+    if (!p->ev[0] || p->timed_calls == 0) return fail(QS_ERR_ARG, "qs_stage_times: no timed call recorded");
+    DeviceGuard g(p->device);
+    cudaError_t e = cudaEventSynchronize(p->ev[5]);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_stage_times: event");
+    for (int i = 0; i < n && i < 5; ++i) {
+        float t = 0.0f;
+        e = cudaEventElapsedTime(&t, p->ev[i], p->ev[i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_stage_times: elapsed");
+        ms[i] = t;
+    }
+    for (int i = 5; i < n; ++i) ms[i] = 0.0f;
+    return QS_OK;
+}
+
+qs_status qs_check(qs_plan p, void* stream)
+{
+    if (!p) return fail(QS_ERR_ARG, "qs_check: NULL plan");
+    DeviceGuard g(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int flag = 0;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_check: stream");
+    e = cudaMemcpy(&flag, p->d_flag, sizeof(flag), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_check: read flag");
+    e = cudaMemset(p->d_flag, 0, sizeof(flag));
+    if (e != cudaSuccess) return cuda_fail(e, "qs_check: clear flag");
+    if (flag & QS_FLAG_TIMEOUT) return fail(QS_ERR_TIMEOUT, "device wait timed out");
+    if (flag & QS_FLAG_NONFINITE) return fail(QS_ERR_NONFINITE, "NaN or Inf in the inputs");
+    if (flag & QS_FLAG_RANGE) return fail(QS_ERR_RANGE, "a projection exceeded the half period; increase radius");
+    return QS_OK;
+}
+
+qs_status qs_sum_host(qs_plan p, const float* xh, int64_t N, const float* wh, const float* yh, int64_t M,
+                      float* sh, void* stream)
+{
+    if (!p) return fail(QS_ERR_ARG, "qs_sum_host: NULL plan");
+    if (N < 0 || M < 0 || N > p->desc.max_n || M > p->desc.max_m)
+        return fail(QS_ERR_ARG, "qs_sum_host: sizes outside the plan's limits");
+    if ((N > 0 && !xh) || (M > 0 && (!yh || !sh))) return fail(QS_ERR_ARG, "qs_sum_host: NULL data pointer");
+    if (M == 0) return QS_OK;
+    DeviceGuard g(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int d = p->desc.d;
+    cudaError_t e = cudaSuccess;
+    if (N > 0) e = cudaMemcpyAsync(p->d_x, xh, (size_t)N * d * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && N > 0 && wh)
+        e = cudaMemcpyAsync(p->d_w, wh, (size_t)N * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_y, yh, (size_t)M * d * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: copy in");
+    qs_status rs = qs_sum(p, p->d_x, N, wh ? p->d_w : nullptr, p->d_y, M, p->d_s, stream);
+    if (rs != QS_OK) return rs;
+    e = cudaMemcpyAsync(sh, p->d_s, (size_t)M * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: copy out");
+    return qs_check(p, stream);
+}
+
+}  // extern "C"

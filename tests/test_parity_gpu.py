@@ -1,0 +1,180 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance: the FP32 path must match the oracle's sliced, Fourier-truncated sum
+within 1e-5 relative, normalised by sum_n |w_n| * max|F| (max|F| = 1 for the
+Gauss and Laplace kernels, R for the negative distance on the data range).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_01316_gb300 import QSError, QSPlan
+from paper_2410_01316_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-5
+
+
+def _norm(prob, w=True):
+    sw = float(np.abs(prob.w.astype(np.float64)).sum()) if w else float(prob.N)
+    return sw * (prob.R if prob.kernel == "negdist" else 1.0)
+
+
+def _plan(prob, proj, window=8, max_n=None, max_m=None):
+    return QSPlan(prob.d, prob.kernel, prob.P, prob.n_ft, prob.R, prob.kparam, dirs=prob.xi, window=window,
+                  proj=proj, max_n=prob.N if max_n is None else max_n, max_m=prob.M if max_m is None else max_m)
+
+
+def _gpu_sum(prob, proj, window=8, use_w=True):
+    import torch
+
+    with _plan(prob, proj, window) as plan:
+        x = torch.from_numpy(prob.x).cuda()
+        y = torch.from_numpy(prob.y).cuda()
+        w = torch.from_numpy(prob.w).cuda() if use_w else None
+        s = plan.sum(x, w, y)
+        plan.check()
+        return s.cpu().numpy().astype(np.float64), plan.tau
+
+
+def _oracle(prob, use_w=True, y=None):
+    t = oracle.tau(prob.kernel, prob.kparam, prob.R)
+    c = oracle.coeffs(prob.kernel, prob.kparam, prob.d, t, prob.n_ft)
+    return oracle.o1_sum(prob.x, prob.w if use_w else None, prob.y if y is None else y, prob.xi, t, c)
+
+
+def _err(s, ref, prob, use_w=True):
+    return float(np.max(np.abs(s - ref))) / _norm(prob, use_w)
+
+
+@pytest.mark.parametrize("proj", ["fp32_fused", "fp32"])
+def test_small_gauss_config(proj):
+    # d=3, N=M=1000, Gauss sigma=0.5, P=64 spherical Fibonacci, N_ft=256, W=8
+    prob = W.small_gauss()
+    s, tau = _gpu_sum(prob, proj)
+    assert tau == pytest.approx(oracle.tau(prob.kernel, prob.kparam, prob.R), rel=2e-16)
+    assert _err(s, _oracle(prob), prob) < TOL_FP32
+
+
+@pytest.mark.parametrize("kernel,kp", [("gauss", 0.7), ("laplace", 1.4), ("negdist", 0.0)])
+@pytest.mark.parametrize("proj", ["fp32_fused", "fp32"])
+def test_ragged_sizes(kernel, kp, proj):
+    # sizes that leave ragged tails in every tiling: N, M not multiples of
+    # 128/256, P not a multiple of the 128-slice tile, d not a multiple of 4
+    prob = W.tiny(d=5, N=1037, M=301, P=131, kernel=kernel, kparam=kp, n_ft=128, seed=31)
+    s, _ = _gpu_sum(prob, proj)
+    assert _err(s, _oracle(prob), prob) < TOL_FP32
+
+
+@pytest.mark.parametrize("window", [6, 8, 10, 12])
+def test_window_widths(window):
+    prob = W.tiny(d=4, N=700, M=200, P=24, kernel="laplace", kparam=2.0, n_ft=256, seed=5)
+    s, _ = _gpu_sum(prob, "fp32_fused", window=window)
+    assert _err(s, _oracle(prob), prob) < TOL_FP32
+
+
+@pytest.mark.parametrize("n_ft", [16, 8192])
+def test_grid_size_limits(n_ft):
+    prob = W.tiny(d=3, N=400, M=100, P=8, kernel="negdist", kparam=0.0, n_ft=n_ft, seed=12)
+    s, _ = _gpu_sum(prob, "fp32_fused")
+    assert _err(s, _oracle(prob), prob) < TOL_FP32
+
+
+def test_unfused_vectorised_projection_d64():
+    prob = W.tiny(d=64, N=3000, M=1500, P=96, kernel="negdist", kparam=0.0, n_ft=512, seed=8)
+    s, _ = _gpu_sum(prob, "fp32")
+    assert _err(s, _oracle(prob), prob) < TOL_FP32
+
+
+def test_fused_and_unfused_agree_d16():
+    prob = W.tiny(d=16, N=2000, M=700, P=64, kernel="gauss", kparam=3.0, n_ft=256, seed=14)
+    s1, _ = _gpu_sum(prob, "fp32_fused")
+    s2, _ = _gpu_sum(prob, "fp32")
+    ref = _oracle(prob)
+    assert _err(s1, ref, prob) < TOL_FP32
+    assert _err(s2, ref, prob) < TOL_FP32
+
+
+def test_unit_weights_when_w_is_none():
+    prob = W.tiny(d=3, N=500, M=90, P=16, kernel="gauss", kparam=1.0, n_ft=128, seed=3)
+    s, _ = _gpu_sum(prob, "fp32_fused", use_w=False)
+    assert _err(s, _oracle(prob, use_w=False), prob, use_w=False) < TOL_FP32
+
+
+def test_single_point_and_empty_inputs():
+    import torch
+
+    prob = W.tiny(d=3, N=1, M=1, P=4, kernel="laplace", kparam=1.0, n_ft=64, seed=1)
+    s, _ = _gpu_sum(prob, "fp32_fused")
+    assert _err(s, _oracle(prob), prob) < TOL_FP32
+    with _plan(prob, "fp32", max_n=10, max_m=10) as plan:
+        x = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+        y = torch.from_numpy(prob.y).cuda()
+        out = torch.full((1,), 7.0, device="cuda")
+        plan.sum(x, None, y, out=out)
+        plan.check()
+        assert out.item() == 0.0
+        empty = plan.sum(torch.from_numpy(prob.x).cuda(), None, torch.zeros((0, 3), device="cuda"))
+        assert empty.numel() == 0
+
+
+def test_sizes_beyond_plan_limits_are_rejected():
+    import torch
+
+    prob = W.tiny(d=3, N=50, M=20, P=4, kernel="gauss", kparam=1.0, n_ft=64, seed=1)
+    with _plan(prob, "fp32_fused", max_n=10, max_m=20) as plan:
+        with pytest.raises(QSError) as ei:
+            plan.sum(torch.from_numpy(prob.x).cuda(), None, torch.from_numpy(prob.y).cuda())
+        assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("proj", ["fp32_fused", "fp32"])
+def test_range_error_is_reported(proj):
+    import torch
+
+    prob = W.tiny(d=3, N=200, M=50, P=8, kernel="gauss", kparam=1.0, n_ft=64, seed=2)
+    prob.R = prob.R / 20  # far too small a radius
+    with _plan(prob, proj) as plan:
+        plan.sum(torch.from_numpy(prob.x).cuda(), None, torch.from_numpy(prob.y).cuda())
+        assert plan.status() == 2  # QS_ERR_RANGE
+        assert plan.status() == 0  # the flag is cleared by the check
+
+
+@pytest.mark.parametrize("where", ["x", "w", "y"])
+def test_nonfinite_input_is_reported(where):
+    import torch
+
+    prob = W.tiny(d=3, N=200, M=50, P=8, kernel="laplace", kparam=1.0, n_ft=64, seed=2)
+    arr = {"x": prob.x.copy(), "w": prob.w.copy(), "y": prob.y.copy()}
+    arr[where].flat[7] = np.nan
+    with _plan(prob, "fp32_fused") as plan:
+        plan.sum(torch.from_numpy(arr["x"]).cuda(), torch.from_numpy(arr["w"]).cuda(),
+                 torch.from_numpy(arr["y"]).cuda())
+        assert plan.status() == 3  # QS_ERR_NONFINITE
+
+
+def test_host_entry_point_matches_device_entry_point():
+    prob = W.tiny(d=8, N=900, M=333, P=40, kernel="gauss", kparam=2.0, n_ft=128, seed=9)
+    s_dev, _ = _gpu_sum(prob, "fp32")
+    with _plan(prob, "fp32") as plan:
+        s_host = plan.sum_host(prob.x, prob.w, prob.y).astype(np.float64)
+    assert np.max(np.abs(s_host - s_dev)) / _norm(prob) < 1e-6
+    assert _err(s_host, _oracle(prob), prob) < TOL_FP32
+
+
+def test_repeated_calls_are_stable():
+    prob = W.tiny(d=3, N=5000, M=400, P=32, kernel="negdist", kparam=0.0, n_ft=256, seed=4)
+    a, _ = _gpu_sum(prob, "fp32_fused")
+    b, _ = _gpu_sum(prob, "fp32_fused")
+    assert np.max(np.abs(a - b)) / _norm(prob) < 1e-6
+
+
+def test_mnist_laplace_full_size_sampled_targets():
+    """d=784, N=M=60000, P=2048, N_ft=1024 (the benchmark workload), checked on
+    128 sampled targets; the oracle's adjoint NDFT runs over all 60000 sources."""
+    prob = W.mnist_laplace()
+    s, _ = _gpu_sum(prob, "fp32")
+    idx = np.random.default_rng(77).choice(prob.M, 128, replace=False)
+    ref = _oracle(prob, y=prob.y[idx])
+    assert _err(s[idx], ref, prob) < TOL_FP32
