@@ -48,11 +48,17 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def make_problem(name: str):
+def make_problem(name: str, P: int = 0, N: int = 0):
+    """The named workload; P / N > 0 shrink it (small cases for profiler captures)."""
     from paper_2410_01316_gb300 import workloads as W
 
     if name == "mnist_laplace":
-        return W.mnist_laplace()
+        kw = {}
+        if P:
+            kw["P"] = P
+        if N:
+            kw["N"] = kw["M"] = N
+        return W.mnist_laplace(**kw)
     if name == "small_gauss":
         return W.small_gauss()
     if name == "gauss64_negdist":
@@ -202,7 +208,7 @@ def run_ours(args, rank, world, local_rank):
     qbuild.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    prob = make_problem(args.workload)
+    prob = make_problem(args.workload, args.P, args.N)
     proj = args.proj
     plan = QSPlan(prob.d, prob.kernel, prob.P, prob.n_ft, prob.R, prob.kparam, dirs=prob.xi, window=prob.window,
                   proj=proj, max_n=prob.N, max_m=prob.M)
@@ -394,6 +400,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mnist_laplace")
     ap.add_argument("--proj", default="fp32")
+    ap.add_argument("--P", type=int, default=0, help="override the number of slices (profiling small cases)")
+    ap.add_argument("--N", type=int, default=0, help="override N = M (profiling small cases)")
     ap.add_argument("--no-error-check", action="store_true")
     ap.add_argument("--error-targets", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
