@@ -308,7 +308,8 @@ def run_ours(args, rank, world, local_rank):
 
 
 def launches_per_step(plan) -> int:
-    return 5 if plan.proj in ("fp32", "bf16x3", "tf32") else 3
+    # projection x, weight bound, spread+filter, projection y, interpolation, reduction
+    return 6 if plan.proj in ("fp32", "bf16x3", "tf32") else 4
 
 
 def roofline(prob, plan, stages, clocks, peaks, peak_src, sm_count):

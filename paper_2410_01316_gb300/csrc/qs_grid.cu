@@ -9,9 +9,16 @@
 //   reduce        s_m = (1/P) sum_p t_{m,p}  in a fixed order with TwoSum
 //
 // The spread writes every point's W taps into a per-slice grid in shared
-// memory with shared-memory atomics; the FFT, the filter and the inverse FFT
-// run on the same shared-memory grid, so a slice touches HBM only to read its
-// projections and to write G filtered values.
+// memory; the FFT, the filter and the inverse FFT run on the same
+// shared-memory grid, so a slice touches HBM only to read its projections and
+// to write G filtered values.
+//
+// The grid is accumulated in 32-bit fixed point with integer shared-memory
+// atomics: every cell is bounded by B = sum_n |w_n| (the window is <= 1), so
+// with the scale 2^30 / B no sum can overflow, each contribution is rounded
+// once to B 2^-31, and integer addition makes the grid independent of the
+// order in which threads add.  (FP32 atomicAdd on shared memory is retried
+// under contention; the projections of clustered data hit a few hundred cells.)
 #include <math.h>
 
 #include "qs_internal.cuh"
@@ -163,6 +170,47 @@ __device__ void real_filter(float2* z, int Gh, const float* __restrict__ D, cons
 }
 
 // ---------------------------------------------------------------------------
+// B = sum_n |w_n| (N if w is NULL) in a fixed order; writes the fixed-point
+// scale 2^30 / B and its inverse.  One CTA of 1024 threads.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) weight_scale_kernel(const float* __restrict__ w, int64_t N,
+                                                            float* __restrict__ out, unsigned int* flag)
+{
+    __shared__ float red[32];
+    float acc = 0.0f;
+    if (w) {
+        for (int64_t n = threadIdx.x; n < N; n += blockDim.x) acc += fabsf(__ldg(&w[n]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) {
+            // FP32 summation error is far below the factor-2 headroom of the
+            // 2^30 scale (the grid overflows only past 2^31).
+            const float B = w ? acc : (float)N;
+            float scale = 0.0f, inv = 0.0f;
+            if (!isfinite(B)) {
+                atomicOr(flag, QS_FLAG_NONFINITE);
+            } else if (B > 0.0f) {
+                scale = 1073741824.0f / B;
+                inv = B / 1073741824.0f;
+                if (!isfinite(scale)) {  // B below 2^-98: all weights negligible
+                    scale = 0.0f;
+                    inv = 0.0f;
+                }
+            }
+            out[0] = scale;
+            out[1] = inv;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Spread + filter: one CTA per slice p.
 // ---------------------------------------------------------------------------
 template <int W, bool FUSED>
@@ -170,15 +218,18 @@ __global__ void __launch_bounds__(256) spread_filter_kernel(qs_launch L, const f
                                                             const float* __restrict__ w)
 {
     extern __shared__ float4 smem4[];
+    int* gridi = reinterpret_cast<int*>(smem4);
     float* grid = reinterpret_cast<float*>(smem4);
     __shared__ float xi_sm[QS_FUSED_MAX_D];
     const int p = blockIdx.x;
     const int G = L.G;
     const int mask = G - 1;
-    for (int i = threadIdx.x; i < G; i += blockDim.x) grid[i] = 0.0f;
+    for (int i = threadIdx.x; i < G; i += blockDim.x) gridi[i] = 0;
     if (FUSED) {
         for (int j = threadIdx.x; j < L.d; j += blockDim.x) xi_sm[j] = L.xi_s[(size_t)p * L.d + j];
     }
+    const float scale = __ldg(&L.wscale[0]);
+    const float inv_scale = __ldg(&L.wscale[1]);
     __syncthreads();
 
     const float* urow = L.U + (size_t)p * L.ldU;
@@ -197,12 +248,15 @@ __global__ void __launch_bounds__(256) spread_filter_kernel(qs_launch L, const f
             atomicOr(L.flag, QS_FLAG_NONFINITE);
             wn = 0.0f;
         }
+        const float ws = wn * scale;
         int l0;
         float tap[W];
         qs_taps<W>(u, L.win, l0, tap);
 #pragma unroll
-        for (int j = 0; j < W; ++j) atomicAdd(&grid[(l0 + j) & mask], wn * tap[j]);
+        for (int j = 0; j < W; ++j) atomicAdd(&gridi[(l0 + j) & mask], __float2int_rn(ws * tap[j]));
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < G; i += blockDim.x) grid[i] = (float)gridi[i] * inv_scale;
     __syncthreads();
 
     const int Gh = G >> 1;
@@ -314,6 +368,12 @@ cudaError_t qs_launch_coeffs(int kernel, double kparam, int d, double tau, int n
 {
     const int n = (n_ft > G / 2 + 1 ? n_ft : G / 2 + 1);
     coeff_kernel<<<(n + 127) / 128, 128, 0, st>>>(kernel, kparam, d, tau, n_ft, G, psihat, c_out, D_out);
+    return cudaGetLastError();
+}
+
+cudaError_t qs_launch_weight_scale(const qs_launch& L, const float* w, cudaStream_t st)
+{
+    weight_scale_kernel<<<1, 1024, 0, st>>>(w, L.N, L.wscale, L.flag);
     return cudaGetLastError();
 }
 

@@ -48,6 +48,7 @@ struct qs_launch {
     float* part;          // 2 x S x M partial slice sums (hi, lo)
     int S;                // number of slice groups of the interpolation
     unsigned int* flag;   // device error flag
+    float* wscale;        // [0] = 2^30 / sum|w| (fixed-point scale of the grids), [1] = its inverse
     qs_window win;
 };
 
@@ -74,6 +75,7 @@ struct qs_plan_s {
     float* d_H;
     float* d_part;
     unsigned int* d_flag;
+    float* d_wscale;      // 2 floats, written by the weight-bound kernel of each sum
     // staging for qs_sum_host
     float* d_x;
     float* d_w;
@@ -147,6 +149,7 @@ cudaError_t qs_launch_coeffs(int kernel, double kparam, int d, double tau, int n
                              const double* psihat, double* c_out, float* D_out, cudaStream_t st);
 cudaError_t qs_launch_project_fp32(const float* X, int64_t N, int d, const float* xi_s, int P,
                                    float* U, int64_t ldU, cudaStream_t st);
+cudaError_t qs_launch_weight_scale(const qs_launch& L, const float* w, cudaStream_t st);
 cudaError_t qs_launch_spread(const qs_launch& L, int W, const float* x, const float* w, bool fused,
                              cudaStream_t st);
 cudaError_t qs_launch_interp(const qs_launch& L, int W, const float* y, bool fused, cudaStream_t st);

@@ -250,7 +250,7 @@ void free_plan(qs_plan p)
     for (int i = 0; i < 6; ++i)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
     void* bufs[] = {p->d_dirs, p->d_dirs_s, p->d_c, p->d_psihat, p->d_D, p->d_tw, p->d_U, p->d_H,
-                    p->d_part, p->d_flag, p->d_x, p->d_w, p->d_y, p->d_s, p->d_xi_hi, p->d_xi_lo,
+                    p->d_part, p->d_flag, p->d_wscale, p->d_x, p->d_w, p->d_y, p->d_s, p->d_xi_hi, p->d_xi_lo,
                     p->d_xsplit};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -286,6 +286,7 @@ qs_launch make_launch(const qs_plan p, int64_t N, int64_t M)
     L.U = p->d_U;
     L.part = p->d_part;
     L.flag = p->d_flag;
+    L.wscale = p->d_wscale;
     L.win = p->win;
     // slice groups of the interpolation: enough CTAs to fill the device,
     // chosen from M and P only so results do not depend on the GPU model
@@ -473,6 +474,7 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     QS_ALLOC(p->d_H, (size_t)P * G);
     QS_ALLOC(p->d_part, (size_t)2 * p->S_max * (D.max_m > 0 ? D.max_m : 1));
     QS_ALLOC(p->d_flag, 1);
+    QS_ALLOC(p->d_wscale, 2);
     if (proj == QS_PROJ_FP32) {
         p->U_elems = (size_t)P * (size_t)p->ldU;
         QS_ALLOC(p->d_U, p->U_elems);
@@ -569,6 +571,8 @@ qs_status qs_sum(qs_plan p, const float* x, int64_t N, const float* w, const flo
         if (e != cudaSuccess) return cuda_fail(e, "qs_sum: projection of x");
     }
     QS_MARK(1);
+    e = qs_launch_weight_scale(L, w, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_sum: weight bound");
     e = qs_launch_spread(L, p->W, x, w, fused, st);
     if (e != cudaSuccess) return cuda_fail(e, "qs_sum: spread");
     QS_MARK(2);

@@ -48,8 +48,10 @@ __global__ void __launch_bounds__(256) project_fp32_kernel(const float* __restri
     const int tid = threadIdx.x;
     const int tx = tid & 15;
     const int ty = tid >> 4;
-    const int p0 = blockIdx.y * BM;
-    const int64_t n0 = (int64_t)blockIdx.x * BN;
+    // blockIdx.x walks the slice tiles so that CTAs sharing one X tile run
+    // back to back and X is read from DRAM once
+    const int p0 = blockIdx.x * BM;
+    const int64_t n0 = (int64_t)blockIdx.y * BN;
     const int lrow = tid >> 1;
     const int lk = (tid & 1) * 4;
 
@@ -114,7 +116,8 @@ cudaError_t qs_launch_project_fp32(const float* X, int64_t N, int d, const float
                                    int64_t ldU, cudaStream_t st)
 {
     if (N <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((P + BM - 1) / BM));
+    dim3 grid((unsigned)((P + BM - 1) / BM), (unsigned)((N + BN - 1) / BN));
+    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
     const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
                      ((reinterpret_cast<uintptr_t>(xi_s) & 15) == 0);
     if (vec)
