@@ -134,6 +134,15 @@ qs_status qs_sum(qs_plan plan, const float* x, int64_t N, const float* w,
                  const float* y, int64_t M, float* s, void* stream);
 
 /*
+ * The projection step alone (Sec. 2.1, eq. kernel_sum_sliced; App. C Step 1):
+ * u_out[p * ldu + n] = G tau <x_n, xi_p> for p < P, n < N, computed in the
+ * plan's projection form (FP32, BF16x3 or TF32; the fused form uses FP32).
+ * x: N x d device memory; u_out: P x ldu device memory, ldu >= N.
+ * Asynchronous on `stream`; uses the plan's workspace, allocates nothing.
+ */
+qs_status qs_project(qs_plan plan, const float* x, int64_t N, float* u_out, int64_t ldu, void* stream);
+
+/*
  * Same sum from HOST buffers: copies x, w, y into plan-owned device staging
  * buffers, runs qs_sum on `stream`, copies s back into the host buffer and
  * synchronises the stream.  Pinned host memory gives the fastest copies.

@@ -146,6 +146,18 @@ class QSPlan:
                                     y.data_ptr(), M, out.data_ptr(), _stream_handle(stream)), "qs_sum")
         return out
 
+    def project(self, x, out=None, stream=None):
+        """u[p, n] = G tau <x_n, xi_p> in the plan's projection form (P x N tensor)."""
+        import torch
+
+        self._check_points(x, "x")
+        N = x.shape[0]
+        if out is None:
+            out = torch.empty((self.P, N), dtype=torch.float32, device=self.device)
+        _lib.check(self._lib.qs_project(self._handle, x.data_ptr(), N, out.data_ptr(), out.stride(0),
+                                        _stream_handle(stream)), "qs_project")
+        return out
+
     def sum_host(self, x: np.ndarray, w, y: np.ndarray, out: np.ndarray | None = None, stream=None) -> np.ndarray:
         """Same sum from host arrays (copies in, computes, copies out, synchronises)."""
         x = np.ascontiguousarray(x, dtype=np.float32)

@@ -81,11 +81,14 @@ struct qs_plan_s {
     float* d_w;
     float* d_y;
     float* d_s;
-    // tensor-core projection operands (BF16 split of the scaled directions)
-    void* d_xi_hi;
-    void* d_xi_lo;
-    void* d_xsplit;       // N x 3d (or M x 3d) BF16 staging of the split points
-    int64_t xsplit_rows;
+    // tensor-core projection operands: BF16 hi/lo split (BF16x3) or TF32
+    // rounding of the scaled directions and of the points being projected
+    int ldk;              // row stride (elements) of the operand copies
+    void* d_xi_hi;        // P x ldk
+    void* d_xi_lo;        // P x ldk (BF16x3 only)
+    void* d_xs_hi;        // max(max_n, max_m) x ldk staging of the points
+    void* d_xs_lo;        // (BF16x3 only)
+    alignas(64) unsigned char tmaps[4][128];  // CUtensorMap: points hi/lo, directions hi/lo
     // stage timing (qs_set_timing)
     int timing;
     int timed_calls;
@@ -149,6 +152,11 @@ cudaError_t qs_launch_coeffs(int kernel, double kparam, int d, double tau, int n
                              const double* psihat, double* c_out, float* D_out, cudaStream_t st);
 cudaError_t qs_launch_project_fp32(const float* X, int64_t N, int d, const float* xi_s, int P,
                                    float* U, int64_t ldU, cudaStream_t st);
+bool qs_make_tmap(void* map_out, const void* base, int elem_bytes, int d, int64_t rows, int ldk, int box_rows);
+cudaError_t qs_launch_split_bf16(const float* X, int64_t rows, int d, int ldk, void* hi, void* lo, cudaStream_t st);
+cudaError_t qs_launch_round_tf32(const float* X, int64_t rows, int d, int ldk, float* out, cudaStream_t st);
+cudaError_t qs_launch_project_tc(int kind, const void* maps, int64_t N, int d, int P, float* U, int64_t ldU,
+                                 unsigned int* flag, cudaStream_t st);
 cudaError_t qs_launch_weight_scale(const qs_launch& L, const float* w, cudaStream_t st);
 cudaError_t qs_launch_spread(const qs_launch& L, int W, const float* x, const float* w, bool fused,
                              cudaStream_t st);

@@ -251,7 +251,7 @@ void free_plan(qs_plan p)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
     void* bufs[] = {p->d_dirs, p->d_dirs_s, p->d_c, p->d_psihat, p->d_D, p->d_tw, p->d_U, p->d_H,
                     p->d_part, p->d_flag, p->d_wscale, p->d_x, p->d_w, p->d_y, p->d_s, p->d_xi_hi, p->d_xi_lo,
-                    p->d_xsplit};
+                    p->d_xs_hi, p->d_xs_lo};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete p;
@@ -296,6 +296,25 @@ qs_launch make_launch(const qs_plan p, int64_t N, int64_t M)
     if (S > p->S_max) S = p->S_max;
     L.S = (int)S;
     return L;
+}
+
+// U = G tau X Xi^T for the plan's projection form.
+cudaError_t project(const qs_plan p, const float* X, int64_t rows, cudaStream_t st)
+{
+    const int d = p->desc.d, P = p->desc.P;
+    cudaError_t e;
+    switch (p->proj) {
+        case QS_PROJ_FP32: return qs_launch_project_fp32(X, rows, d, p->d_dirs_s, P, p->d_U, p->ldU, st);
+        case QS_PROJ_BF16X3:
+            e = qs_launch_split_bf16(X, rows, d, p->ldk, p->d_xs_hi, p->d_xs_lo, st);
+            if (e != cudaSuccess) return e;
+            return qs_launch_project_tc(0, p->tmaps, rows, d, P, p->d_U, p->ldU, p->d_flag, st);
+        case QS_PROJ_TF32:
+            e = qs_launch_round_tf32(X, rows, d, p->ldk, (float*)p->d_xs_hi, st);
+            if (e != cudaSuccess) return e;
+            return qs_launch_project_tc(1, p->tmaps, rows, d, P, p->d_U, p->ldU, p->d_flag, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
@@ -393,7 +412,7 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     if (proj == QS_PROJ_AUTO) proj = D.d <= 16 ? QS_PROJ_FP32_FUSED : QS_PROJ_FP32;
     if (proj == QS_PROJ_FP32_FUSED && D.d > QS_FUSED_MAX_D)
         return fail(QS_ERR_UNSUPPORTED, "qs_plan_create: fused projection needs d <= %d", QS_FUSED_MAX_D);
-    if (proj != QS_PROJ_FP32 && proj != QS_PROJ_FP32_FUSED)
+    if (proj != QS_PROJ_FP32 && proj != QS_PROJ_FP32_FUSED && proj != QS_PROJ_BF16X3 && proj != QS_PROJ_TF32)
         return fail(QS_ERR_UNSUPPORTED, "qs_plan_create: projection form %d not available", (int)proj);
 
     int dev = 0;
@@ -475,9 +494,30 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     QS_ALLOC(p->d_part, (size_t)2 * p->S_max * (D.max_m > 0 ? D.max_m : 1));
     QS_ALLOC(p->d_flag, 1);
     QS_ALLOC(p->d_wscale, 2);
-    if (proj == QS_PROJ_FP32) {
+    const bool tc = proj == QS_PROJ_BF16X3 || proj == QS_PROJ_TF32;
+    if (proj == QS_PROJ_FP32 || tc) {
         p->U_elems = (size_t)P * (size_t)p->ldU;
         QS_ALLOC(p->d_U, p->U_elems);
+    }
+    const int64_t stage_rows = maxnm > 0 ? maxnm : 1;
+    if (proj == QS_PROJ_BF16X3) {
+        p->ldk = (d + 7) / 8 * 8;  // 16-byte row stride for TMA
+        uint16_t *xh = nullptr, *xl = nullptr, *sh = nullptr, *sl = nullptr;
+        QS_ALLOC(xh, (size_t)P * p->ldk);
+        p->d_xi_hi = xh;
+        QS_ALLOC(xl, (size_t)P * p->ldk);
+        p->d_xi_lo = xl;
+        QS_ALLOC(sh, (size_t)stage_rows * p->ldk);
+        p->d_xs_hi = sh;
+        QS_ALLOC(sl, (size_t)stage_rows * p->ldk);
+        p->d_xs_lo = sl;
+    } else if (proj == QS_PROJ_TF32) {
+        p->ldk = (d + 3) / 4 * 4;
+        float *xh = nullptr, *sh = nullptr;
+        QS_ALLOC(xh, (size_t)P * p->ldk);
+        p->d_xi_hi = xh;
+        QS_ALLOC(sh, (size_t)stage_rows * p->ldk);
+        p->d_xs_hi = sh;
     }
     QS_ALLOC(p->d_x, (size_t)(D.max_n > 0 ? D.max_n : 1) * d);
     QS_ALLOC(p->d_w, (size_t)(D.max_n > 0 ? D.max_n : 1));
@@ -502,6 +542,22 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     QS_CHECK(cudaMemset(p->d_flag, 0, sizeof(unsigned int)), "clear flag");
     QS_CHECK(qs_launch_coeffs((int)D.kernel, D.kparam, d, p->tau, D.n_ft, G, p->d_psihat, p->d_c, p->d_D, 0),
              "coefficient kernel launch");
+    if (tc) {
+        const int eb = proj == QS_PROJ_BF16X3 ? 2 : 4;
+        if (proj == QS_PROJ_BF16X3)
+            QS_CHECK(qs_launch_split_bf16(p->d_dirs_s, P, d, p->ldk, p->d_xi_hi, p->d_xi_lo, 0), "split directions");
+        else
+            QS_CHECK(qs_launch_round_tf32(p->d_dirs_s, P, d, p->ldk, (float*)p->d_xi_hi, 0), "round directions");
+        bool ok = qs_make_tmap(p->tmaps[0], p->d_xs_hi, eb, d, stage_rows, p->ldk, 128) &&
+                  qs_make_tmap(p->tmaps[2], p->d_xi_hi, eb, d, P, p->ldk, 256);
+        if (ok && proj == QS_PROJ_BF16X3)
+            ok = qs_make_tmap(p->tmaps[1], p->d_xs_lo, eb, d, stage_rows, p->ldk, 128) &&
+                 qs_make_tmap(p->tmaps[3], p->d_xi_lo, eb, d, P, p->ldk, 256);
+        if (!ok) {
+            free_plan(p);
+            return fail(QS_ERR_CUDA, "qs_plan_create: cuTensorMapEncodeTiled failed");
+        }
+    }
     QS_CHECK(cudaDeviceSynchronize(), "coefficient kernel");
 #undef QS_CHECK
     *out = p;
@@ -567,7 +623,7 @@ qs_status qs_sum(qs_plan p, const float* x, int64_t N, const float* w, const flo
     } while (0)
     QS_MARK(0);
     if (!fused) {
-        e = qs_launch_project_fp32(x, N, L.d, p->d_dirs_s, L.P, p->d_U, p->ldU, st);
+        e = project(p, x, N, st);
         if (e != cudaSuccess) return cuda_fail(e, "qs_sum: projection of x");
     }
     QS_MARK(1);
@@ -577,7 +633,7 @@ qs_status qs_sum(qs_plan p, const float* x, int64_t N, const float* w, const flo
     if (e != cudaSuccess) return cuda_fail(e, "qs_sum: spread");
     QS_MARK(2);
     if (!fused) {
-        e = qs_launch_project_fp32(y, M, L.d, p->d_dirs_s, L.P, p->d_U, p->ldU, st);
+        e = project(p, y, M, st);
         if (e != cudaSuccess) return cuda_fail(e, "qs_sum: projection of y");
     }
     QS_MARK(3);
@@ -622,6 +678,23 @@ qs_status qs_stage_times(qs_plan p, float* ms, int n)
     }
     for (int i = 5; i < n; ++i) ms[i] = 0.0f;
     return QS_OK;
+}
+
+qs_status qs_project(qs_plan p, const float* x, int64_t N, float* u_out, int64_t ldu, void* stream)
+{
+    if (!p) return fail(QS_ERR_ARG, "qs_project: NULL plan");
+    if (N < 0 || N > (p->desc.max_n > p->desc.max_m ? p->desc.max_n : p->desc.max_m) || ldu < N)
+        return fail(QS_ERR_ARG, "qs_project: bad size");
+    if (N > 0 && (!x || !u_out)) return fail(QS_ERR_ARG, "qs_project: NULL data pointer");
+    if (N == 0) return QS_OK;
+    if (!p->d_U) return fail(QS_ERR_UNSUPPORTED, "qs_project: the fused form keeps no projection workspace");
+    DeviceGuard g(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = project(p, x, N, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_project: projection");
+    e = cudaMemcpy2DAsync(u_out, (size_t)ldu * sizeof(float), p->d_U, (size_t)p->ldU * sizeof(float),
+                          (size_t)N * sizeof(float), (size_t)p->desc.P, cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_project: copy");
 }
 
 qs_status qs_check(qs_plan p, void* stream)
