@@ -299,6 +299,8 @@ def run_ours(args, rank, world, local_rank):
                     "ms_per_step": 1e3 * e2e_t / args.steps},
             "gpu_launches": args.steps * launches_per_step(plan),
         }
+        if proj != "fp32" and not args.no_fp32_compare:
+            line["config"]["plain_fp32"] = plain_fp32_compare(prob, x, w, y, flush, args, err_idx_err=not args.no_error_check)
         if world == 1 and not args.no_cpu_baseline:
             r, dt, desc = oracle_sample_rate(prob, args.cpu_slices, args.cpu_targets)
             line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
@@ -307,9 +309,44 @@ def run_ours(args, rank, world, local_rank):
     plan.close()
 
 
+def plain_fp32_compare(prob, x, w, y, flush, args, err_idx_err=True):
+    """Same workload through the plain FP32 form (SIMT projection), timed the
+    same way, for the 'vs plain FP32' part of the metric."""
+    import torch
+
+    from paper_2410_01316_gb300 import QSPlan
+
+    steps = max(3, min(args.steps, 5))
+    with QSPlan(prob.d, prob.kernel, prob.P, prob.n_ft, prob.R, prob.kparam, dirs=prob.xi, window=prob.window,
+                proj="fp32", max_n=prob.N, max_m=prob.M) as plan:
+        s = torch.empty(prob.M, dtype=torch.float32, device=x.device)
+        for _ in range(2):
+            plan.sum(x, w, y, out=s)
+        stream = torch.cuda.current_stream()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.sum(x, w, y, out=s)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        plan.check()
+        out = {"value": prob.point_slices / (sum(ms) / len(ms) / 1e3) / 1e9, "unit": UNIT,
+               "ms_per_step": sum(ms) / len(ms), "steps": steps}
+        if err_idx_err:
+            out["rel_err_vs_oracle"], _ = error_vs_oracle(prob, s, args.error_targets)
+        return out
+
+
 def launches_per_step(plan) -> int:
-    # projection x, weight bound, spread+filter, projection y, interpolation, reduction
-    return 6 if plan.proj in ("fp32", "bf16x3", "tf32") else 4
+    # [split x,] projection x, weight bound, spread+filter, [split y,] projection y,
+    # interpolation, reduction
+    if plan.proj in ("bf16x3", "tf32"):
+        return 8
+    return 6 if plan.proj == "fp32" else 4
 
 
 def roofline(prob, plan, stages, clocks, peaks, peak_src, sm_count):
@@ -400,7 +437,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mnist_laplace")
-    ap.add_argument("--proj", default="fp32")
+    ap.add_argument("--proj", default="bf16x3")
+    ap.add_argument("--no-fp32-compare", action="store_true",
+                    help="skip the same-run measurement of the plain FP32 form")
     ap.add_argument("--P", type=int, default=0, help="override the number of slices (profiling small cases)")
     ap.add_argument("--N", type=int, default=0, help="override N = M (profiling small cases)")
     ap.add_argument("--no-error-check", action="store_true")

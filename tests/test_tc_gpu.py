@@ -4,7 +4,10 @@ The projection stage is checked element by element against the plain FP64
 definition u[p, n] = G tau <x_n, xi_p> (a library matmul in double) under the
 rounding-error bound of each form, |u - u_ref| <= e_form * (G tau |X| |Xi|^T)[p, n]:
   FP32    e = (d + 2) 2^-24                   (FMA accumulation, scaled directions)
-  BF16x3  e = 3 2^-18 + 4 (3d + 2) 2^-24      (dropped lo*lo term and two BF16 splits)
+  BF16x3  e = 3 2^-18 + 2^-17 + 4 (3d + 2) 2^-24
+          (dropped lo*lo term and two BF16 splits; the 2^-17 term covers the
+          tensor core's internal accumulation, whose rounding is not specified
+          bit-exactly and was measured at ~2^-17.5 for K = 5)
   TF32    e = 2^-10 + 4 (d + 2) 2^-24         (round-to-nearest TF32 of both operands)
 Full sums are checked against the FP64 oracle: 1e-5 relative for FP32, 1e-3
 for the reduced-precision projections (normalised by sum|w| max|F|).
@@ -24,7 +27,7 @@ def _bound(form, d):
     if form == "fp32":
         return (d + 2) * u
     if form == "bf16x3":
-        return 3 * 2.0 ** -18 + 4 * (3 * d + 2) * u
+        return 3 * 2.0 ** -18 + 2.0 ** -17 + 4 * (3 * d + 2) * u
     return 2.0 ** -10 + 4 * (d + 2) * u
 
 
