@@ -184,6 +184,37 @@ qs_status qs_directions(qs_dirs kind, int d, int P, uint64_t seed, float* out_ho
 qs_status qs_set_timing(qs_plan plan, int enable);
 qs_status qs_stage_times(qs_plan plan, float* ms, int n);
 
+/*
+ * The sum for callers that cannot allocate device memory.  (The paper has
+ * no counterpart; this is a deployment entry point.)
+ *
+ * Some callers cannot call cudaMalloc: code running under a framework whose
+ * caching allocator owns the device memory, loops that must not stall on an
+ * allocation, or plugins that are handed their buffers and nothing else.
+ * Plan creation allocates, so they cannot hold a plan.  qs_sum_noalloc takes
+ * the plan description directly and keeps every intermediate in one static
+ * device array of 16 MiB that the library reserves on each GPU it is loaded
+ * on, until the process exits.  It allocates nothing.
+ *
+ * desc: as for qs_plan_create; dirs, seed, dirs_host, max_n and max_m are
+ *       ignored and proj must be QS_PROJ_AUTO or QS_PROJ_FP32_FUSED (FP32 dot
+ *       products inside the spread and interpolation; d <= 32).
+ * dirs_dev: P x d FP32 directions in device memory (caller-owned).
+ * x, w, y, s: as for qs_sum (device memory, w may be NULL).
+ * Sizes: P * 2 n_ft grid values, the tables and the slice partial sums must
+ * fit in the 16 MiB array (e.g. P = 1024 slices with n_ft = 1024 and M up to
+ * about a million targets); larger problems return QS_ERR_UNSUPPORTED with a
+ * message giving the bytes needed.  N and M are otherwise unbounded.
+ * Synchronous: waits for `stream` and returns the data-error status that
+ * qs_check would return.
+ * The first call on a device looks up the array's device address; make that
+ * first call before capturing the stream into a CUDA graph.  All calls share
+ * the array: calls whose GPU work overlaps (other streams or threads on the
+ * same device) race and must be serialised by the caller.
+ */
+qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_dev, const float* x, int64_t N,
+                         const float* w, const float* y, int64_t M, float* s, void* stream);
+
 /* Library version string. */
 const char* qs_version(void);
 

@@ -152,6 +152,7 @@ cudaError_t qs_launch_coeffs(int kernel, double kparam, int d, double tau, int n
                              const double* psihat, double* c_out, float* D_out, cudaStream_t st);
 cudaError_t qs_launch_project_fp32(const float* X, int64_t N, int d, const float* xi_s, int P,
                                    float* U, int64_t ldU, cudaStream_t st);
+void qs_set_error_message(const char* msg);
 bool qs_make_tmap(void* map_out, const void* base, int elem_bytes, int d, int64_t rows, int ldk, int box_rows);
 cudaError_t qs_launch_split_bf16(const float* X, int64_t rows, int d, int ldk, void* hi, void* lo, cudaStream_t st);
 cudaError_t qs_launch_round_tf32(const float* X, int64_t rows, int d, int ldk, float* out, cudaStream_t st);

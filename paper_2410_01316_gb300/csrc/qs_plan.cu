@@ -319,6 +319,12 @@ cudaError_t project(const qs_plan p, const float* X, int64_t rows, cudaStream_t 
 
 }  // namespace
 
+// Set the thread's last-error message (for entry points defined in other files).
+void qs_set_error_message(const char* msg)
+{
+    snprintf(g_last_error, sizeof(g_last_error), "%s", msg ? msg : "");
+}
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
