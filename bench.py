@@ -341,6 +341,86 @@ def plain_fp32_compare(prob, x, w, y, flush, args, err_idx_err=True):
         return out
 
 
+def run_mmd_flow(args, rank, world, local_rank):
+    """MMD gradient flow with the negative distance kernel (App. H, MMD flows):
+    particles y move by explicit Euler steps y <- y - h M grad_y G(y), where
+    G(y) = MMD^2 between the particles and the fixed targets x, and the
+    gradient is one qs_grad call over the joint sources [y; x] with weights
+    [1/M^2; -1/(MN)].  A step = one gradient + one update."""
+    import torch
+
+    from paper_2410_01316_gb300 import QSPlan
+    from paper_2410_01316_gb300 import build as qbuild
+    from paper_2410_01316_gb300 import workloads as W
+
+    qbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    st = W.mmd_flow16()
+    x = torch.from_numpy(st["x"]).to(dev)
+    y0 = torch.from_numpy(st["y"]).to(dev)
+    N, M, d, P, n_ft = x.shape[0], y0.shape[0], st["d"], st["P"], st["n_ft"]
+    xi = W.make_directions("orthogonal", P, d, st["seed"] + 11)
+    R = 1.25 * 2 * float(max(x.norm(dim=1).max(), y0.norm(dim=1).max()))
+    plan = QSPlan(d, "negdist", P, n_ft, R, dirs=xi, proj="fp32_fused", max_n=N + M, max_m=N + M)
+    z = torch.cat([y0, x]).contiguous()          # sources; z[:M] are the moving particles
+    y = z[:M]
+    wz = torch.cat([torch.full((M,), 1.0 / (M * M)), torch.full((N,), -1.0 / (M * N))]).float().to(dev)
+    we = torch.cat([torch.full((M,), 0.5 / (M * M)), torch.full((N,), -1.0 / (M * N))]).float().to(dev)
+    wx = torch.full((N,), 0.5 / (N * N), dtype=torch.float32, device=dev)
+    h = 1.0
+    gy = torch.empty((M, d), dtype=torch.float32, device=dev)
+    from paper_2410_01316_gb300 import _lib
+    import ctypes
+
+    def step():
+        _lib.check(plan._lib.qs_grad(plan._handle, z.data_ptr(), N + M, wz.data_ptr(), y.data_ptr(), M, None,
+                                     None, None, gy.data_ptr(), torch.cuda.current_stream().cuda_stream), "qs_grad")
+        y.add_(gy, alpha=-h * M)
+
+    def mmd2():
+        yc = y.contiguous()
+        a = plan.sum(z, we, yc).double().sum()
+        b = plan.sum(x, wx, x).double().sum()
+        return float(a + b)
+
+    curve = [(0, mmd2())]
+    for _ in range(args.warmup):
+        step()
+    y.copy_(y0)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(smi_gpu_id(dev))
+    sampler.start()
+    time.sleep(0.3)
+    ms = []
+    for i in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        if (i + 1) % 10 == 0:
+            curve.append((i + 1, mmd2()))
+    clocks = sampler.stop()
+    status = plan.status()
+    t = sum(ms) / 1e3
+    ps = (N + M + M) * P
+    line = {"metric": METRIC, "value": ps * args.steps / t / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"mmd_flow16: d={d} N={N} targets, M={M} particles, P={P} orthogonal, "
+                                   f"negdist, N_ft={n_ft}, Euler h={h} on M grad (gradient over {N + M} sources)",
+                       "mmd2_curve": curve, "device_status": int(status),
+                       "point_slices_per_step": f"(N + M sources + M targets) P = {ps}"},
+            "clocks": clocks, "gpu_launches": args.steps * 4}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def launches_per_step(plan) -> int:
     # [split x,] projection x, weight bound, spread+filter, [split y,] projection y,
     # interpolation, reduction
@@ -453,6 +533,8 @@ def main():
     rank, world, local = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "mmd_flow16":
+        run_mmd_flow(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1 and _PG is not None:

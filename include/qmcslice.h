@@ -134,6 +134,24 @@ qs_status qs_sum(qs_plan plan, const float* x, int64_t N, const float* w,
                  const float* y, int64_t M, float* s, void* stream);
 
 /*
+ * Gradients of L = sum_m v_m s_m with s = qs_sum(x, w, y) (the derivative of
+ * the sliced Fourier sum of Sec. 2.1 / App. C; its use for MMD gradient flows
+ * is App. H).  With g(t) = Re sum_k c_k e^{2 pi i k t} (even) and g' odd:
+ *   gy[m] = dL/dy_m = (tau/P) v_m sum_p xi_p sum_n w_n g'(b_{m,p} - a_{n,p})
+ *   gx[n] = dL/dx_n = (tau/P) w_n sum_p xi_p sum_m v_m g'(a_{n,p} - b_{m,p})
+ *   gw[n] = dL/dw_n = (1/P) sum_p sum_m v_m g(a_{n,p} - b_{m,p})
+ * computed by the same spread / FFT / interpolation pipeline with the filter
+ * 2 pi i k c_k / psi^2 and a back-projection onto the directions (x and w
+ * swap roles with y and v).  x: N x d, w: N (NULL = ones), y: M x d,
+ * v: M (NULL = ones), gx: N x d, gw: N, gy: M x d; all device memory; any
+ * output may be NULL to skip it.  Needs d <= 32.  Asynchronous on `stream`,
+ * allocates nothing.  Errors: QS_ERR_ARG, QS_ERR_UNSUPPORTED (d > 32),
+ * QS_ERR_CUDA; data errors via qs_check.
+ */
+qs_status qs_grad(qs_plan plan, const float* x, int64_t N, const float* w, const float* y, int64_t M,
+                  const float* v, float* gx, float* gw, float* gy, void* stream);
+
+/*
  * The projection step alone (Sec. 2.1, eq. kernel_sum_sliced; App. C Step 1):
  * u_out[p * ldu + n] = G tau <x_n, xi_p> for p < P, n < N, computed in the
  * plan's projection form (FP32, BF16x3 or TF32; the fused form uses FP32).

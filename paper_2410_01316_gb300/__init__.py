@@ -17,7 +17,7 @@ import numpy as np
 from . import _lib
 from ._lib import QSError
 
-__all__ = ["QSPlan", "QSError", "directions", "kernel_sum", "version"]
+__all__ = ["QSPlan", "QSError", "KernelSumFn", "directions", "kernel_sum", "version"]
 
 
 def version() -> str:
@@ -158,6 +158,25 @@ class QSPlan:
                                         _stream_handle(stream)), "qs_project")
         return out
 
+    def grad(self, x, w, y, v=None, want=("x", "w", "y"), stream=None):
+        """Gradients of L = sum_m v_m s_m (dict with 'x', 'w', 'y'; None where not wanted)."""
+        import torch
+
+        self._check_points(x, "x")
+        self._check_points(y, "y")
+        N, M = x.shape[0], y.shape[0]
+        if w is not None:
+            self._check_points(w, "w", rows=N)
+        if v is not None:
+            self._check_points(v, "v", rows=M)
+        gx = torch.empty((N, self.d), dtype=torch.float32, device=self.device) if "x" in want else None
+        gw = torch.empty(N, dtype=torch.float32, device=self.device) if "w" in want else None
+        gy = torch.empty((M, self.d), dtype=torch.float32, device=self.device) if "y" in want else None
+        ptr = lambda t: None if t is None else t.data_ptr()
+        _lib.check(self._lib.qs_grad(self._handle, x.data_ptr(), N, ptr(w), y.data_ptr(), M, ptr(v), ptr(gx),
+                                     ptr(gw), ptr(gy), _stream_handle(stream)), "qs_grad")
+        return {"x": gx, "w": gw, "y": gy}
+
     def sum_host(self, x: np.ndarray, w, y: np.ndarray, out: np.ndarray | None = None, stream=None) -> np.ndarray:
         """Same sum from host arrays (copies in, computes, copies out, synchronises)."""
         x = np.ascontiguousarray(x, dtype=np.float32)
@@ -181,6 +200,45 @@ class QSPlan:
     def status(self, stream=None) -> int:
         """Synchronise and return the device error status without raising."""
         return int(self._lib.qs_check(self._handle, _stream_handle(stream)))
+
+
+def _make_fn():
+    import torch
+
+    class KernelSumFn(torch.autograd.Function):
+        """s = plan.sum(x, w, y) with gradients from qs_grad (w may be None).
+
+        backward(v) returns dL/dx, dL/dw, dL/dy for L = <v, s>, computed on the
+        device by the adjoint pipeline (derivative filter + back-projection)."""
+
+        @staticmethod
+        def forward(ctx, x, w, y, plan):
+            ctx.plan = plan
+            ctx.has_w = w is not None
+            ctx.save_for_backward(x, w if w is not None else x.new_empty(0), y)
+            return plan.sum(x.contiguous(), None if w is None else w.contiguous(), y.contiguous())
+
+        @staticmethod
+        def backward(ctx, v):
+            x, w, y = ctx.saved_tensors
+            need = ctx.needs_input_grad
+            want = tuple(k for k, n in zip(("x", "w", "y"), need[:3]) if n)
+            g = ctx.plan.grad(x.contiguous(), w if ctx.has_w else None, y.contiguous(), v.contiguous(), want=want)
+            return g["x"], (g["w"] if ctx.has_w else None), g["y"], None
+
+    return KernelSumFn
+
+
+class _LazyFn:
+    _fn = None
+
+    def __getattr__(self, name):
+        if _LazyFn._fn is None:
+            _LazyFn._fn = _make_fn()
+        return getattr(_LazyFn._fn, name)
+
+
+KernelSumFn = _LazyFn()
 
 
 def kernel_sum(x, w, y, kernel: str, kparam: float = 0.0, P: int = 256, n_ft: int = 512, dirs="orthogonal",

@@ -128,11 +128,19 @@ __device__ void fft_inplace(float2* z, int n, int log2n, const float2* __restric
 //   Y_k = D_k X_k
 //   Z'_k = (Y_k + conj Y_{Gh-k}) + i e^{2 pi i k/G} (Y_k - conj Y_{Gh-k})       (k < Gh)
 // so that IFFT_Gh(Z') interleaves the real sequence h_l = sum_k Y_k e^{2 pi i k l/G}.
+// DERIV: the filter is i g_k with the real table g (derivative coefficients
+// 2 pi i k c_k over psi^2), i.e. Y_k = i g_k X_k.
+template <bool DERIV>
 __device__ void real_filter(float2* z, int Gh, const float* __restrict__ D, const float2* __restrict__ tw)
 {
     for (int k = threadIdx.x; k <= (Gh >> 1); k += blockDim.x) {
         if (k == 0) {
             const float2 z0 = z[0];
+            if (DERIV) {
+                // g_0 = 0 and g_{Gh} = 0 (Gh > N_ft/2): the real parts at k = 0, Gh vanish
+                z[0] = make_float2(0.0f, 0.0f);
+                continue;
+            }
             const float y0 = __ldg(&D[0]) * (z0.x + z0.y);
             const float yh = __ldg(&D[Gh]) * (z0.x - z0.y);
             z[0] = make_float2(y0 + yh, y0 - yh);
@@ -149,8 +157,8 @@ __device__ void real_filter(float2* z, int Gh, const float* __restrict__ D, cons
         const float2 Xk2 = make_float2(A.x - tB.x, -(A.y - tB.y));  // conj(A - t B)
         const float dk = __ldg(&D[k]);
         const float dk2 = __ldg(&D[k2]);
-        const float2 Yk = make_float2(dk * Xk.x, dk * Xk.y);
-        const float2 Yk2 = make_float2(dk2 * Xk2.x, dk2 * Xk2.y);
+        const float2 Yk = DERIV ? make_float2(-dk * Xk.y, dk * Xk.x) : make_float2(dk * Xk.x, dk * Xk.y);
+        const float2 Yk2 = DERIV ? make_float2(-dk2 * Xk2.y, dk2 * Xk2.x) : make_float2(dk2 * Xk2.x, dk2 * Xk2.y);
         const float2 tc = make_float2(t.x, -t.y);  // e^{+2 pi i k / G}
         // Z'_k = (Yk + conj Yk2) + i tc (Yk - conj Yk2)
         {
@@ -263,12 +271,172 @@ __global__ void __launch_bounds__(256) spread_filter_kernel(qs_launch L, const f
     const int log2n = 31 - __clz(Gh);
     float2* z = reinterpret_cast<float2*>(grid);
     fft_inplace<false>(z, Gh, log2n, L.tw, G);
-    real_filter(z, Gh, L.D, L.tw);
+    real_filter<false>(z, Gh, L.D, L.tw);
     __syncthreads();
     fft_inplace<true>(z, Gh, log2n, L.tw, G);
 
     float4* dst = reinterpret_cast<float4*>(L.H + (size_t)p * G);
     for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst[i] = smem4[i];
+}
+
+// ---------------------------------------------------------------------------
+// Spread for the gradients (fused projection, d <= 32), one CTA per slice.
+// MODE 1: H2 <- derivative filter (table Dd).  MODE 2: L.H <- plain filter
+// (table L.D) and H2 <- derivative filter from the same spread grid.
+// ---------------------------------------------------------------------------
+template <int W, int MODE>
+__global__ void __launch_bounds__(256) spread_grad_kernel(qs_launch L, const float* __restrict__ x,
+                                                          const float* __restrict__ w, const float* __restrict__ Dd,
+                                                          float* __restrict__ H2)
+{
+    extern __shared__ float4 smem4[];
+    int* gridi = reinterpret_cast<int*>(smem4);
+    float* grid = reinterpret_cast<float*>(smem4);
+    float* grid2 = grid + L.G;
+    __shared__ float xi_sm[QS_FUSED_MAX_D];
+    const int p = blockIdx.x;
+    const int G = L.G;
+    const int mask = G - 1;
+    for (int i = threadIdx.x; i < G; i += blockDim.x) gridi[i] = 0;
+    for (int j = threadIdx.x; j < L.d; j += blockDim.x) xi_sm[j] = L.xi_s[(size_t)p * L.d + j];
+    const float scale = __ldg(&L.wscale[0]);
+    const float inv_scale = __ldg(&L.wscale[1]);
+    __syncthreads();
+    for (int64_t n = threadIdx.x; n < L.N; n += blockDim.x) {
+        const float* xn = x + (size_t)n * L.d;
+        float u = 0.0f;
+        for (int j = 0; j < L.d; ++j) u = fmaf(xi_sm[j], __ldg(&xn[j]), u);
+        u = qs_check_u(u, L.half_G, L.flag);
+        float wn = w ? __ldg(&w[n]) : 1.0f;
+        if (!isfinite(wn)) {
+            atomicOr(L.flag, QS_FLAG_NONFINITE);
+            wn = 0.0f;
+        }
+        const float ws = wn * scale;
+        int l0;
+        float tap[W];
+        qs_taps<W>(u, L.win, l0, tap);
+#pragma unroll
+        for (int j = 0; j < W; ++j) atomicAdd(&gridi[(l0 + j) & mask], __float2int_rn(ws * tap[j]));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < G; i += blockDim.x) grid[i] = (float)gridi[i] * inv_scale;
+    __syncthreads();
+    const int Gh = G >> 1;
+    const int log2n = 31 - __clz(Gh);
+    float2* z = reinterpret_cast<float2*>(grid);
+    float2* z2 = reinterpret_cast<float2*>(grid2);
+    fft_inplace<false>(z, Gh, log2n, L.tw, G);
+    if (MODE == 2) {
+        for (int i = threadIdx.x; i < Gh; i += blockDim.x) z2[i] = z[i];
+        __syncthreads();
+        real_filter<false>(z, Gh, L.D, L.tw);
+        real_filter<true>(z2, Gh, Dd, L.tw);
+        __syncthreads();
+        fft_inplace<true>(z, Gh, log2n, L.tw, G);
+        fft_inplace<true>(z2, Gh, log2n, L.tw, G);
+        float4* dst = reinterpret_cast<float4*>(L.H + (size_t)p * G);
+        const float4* src = reinterpret_cast<const float4*>(grid);
+        for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst[i] = src[i];
+        float4* dst2 = reinterpret_cast<float4*>(H2 + (size_t)p * G);
+        const float4* src2 = reinterpret_cast<const float4*>(grid2);
+        for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst2[i] = src2[i];
+    } else {
+        real_filter<true>(z, Gh, Dd, L.tw);
+        __syncthreads();
+        fft_inplace<true>(z, Gh, log2n, L.tw, G);
+        float4* dst2 = reinterpret_cast<float4*>(H2 + (size_t)p * G);
+        for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst2[i] = smem4[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Derivative interpolation + back-projection (fused projection, d <= DMAX):
+//   q_{m,p} = sum_l h'_p[l] psi(u_{m,p} - l),  acc_m += q_{m,p} xi_p
+// per slice group, compensated per component.  part: [2][S][M][d].
+// ---------------------------------------------------------------------------
+template <int W, int DMAX>
+__global__ void __launch_bounds__(256) interp_grad_kernel(qs_launch L, const float* __restrict__ y,
+                                                          const float* __restrict__ Hd, const float* __restrict__ xi,
+                                                          float* __restrict__ part)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.y;
+    const int S = gridDim.y;
+    if (m >= L.M) return;
+    const int d = L.d;
+    const int p0 = (int)(((int64_t)g * L.P) / S);
+    const int p1 = (int)(((int64_t)(g + 1) * L.P) / S);
+    float yr[DMAX], hi[DMAX], lo[DMAX];
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) {
+        yr[j] = j < d ? __ldg(&y[(size_t)m * d + j]) : 0.0f;
+        hi[j] = 0.0f;
+        lo[j] = 0.0f;
+    }
+    const int mask = L.G - 1;
+    for (int p = p0; p < p1; ++p) {
+        const float* xs = L.xi_s + (size_t)p * d;
+        float u = 0.0f;
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j)
+            if (j < d) u = fmaf(__ldg(&xs[j]), yr[j], u);
+        u = qs_check_u(u, L.half_G, L.flag);
+        int l0;
+        float tap[W];
+        qs_taps<W>(u, L.win, l0, tap);
+        const float* h = Hd + (size_t)p * L.G;
+        float q = 0.0f;
+#pragma unroll
+        for (int j = 0; j < W; ++j) q = fmaf(__ldg(&h[(l0 + j) & mask]), tap[j], q);
+        const float* xp = xi + (size_t)p * d;
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j)
+            if (j < d) qs_two_sum(hi[j], lo[j], q * __ldg(&xp[j]));
+    }
+    float* ph = part + ((size_t)g * L.M + m) * d;
+    float* pl = part + ((size_t)(S + g) * L.M + m) * d;
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j)
+        if (j < d) {
+            ph[j] = hi[j];
+            pl[j] = lo[j];
+        }
+}
+
+// g[m][j] = scale * fac_m * sum over slice groups (in order) of the partials.
+__global__ void reduce_grad_kernel(const float* __restrict__ part, int S, int64_t M, int d, float scale,
+                                   const float* __restrict__ fac, float* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * d) return;
+    const int64_t m = i / d;
+    float hi = 0.0f, lo = 0.0f;
+    for (int g = 0; g < S; ++g) {
+        qs_two_sum(hi, lo, part[(size_t)g * M * d + i]);
+        lo += part[(size_t)(S + g) * M * d + i];
+    }
+    const float f = fac ? __ldg(&fac[m]) : 1.0f;
+    out[i] = (hi + lo) * scale * f;
+}
+
+// Derivative filter table: g_k = 2 pi k c_k / psi^(k/G)^2 for 0 <= k <= N_ft/2
+// (half weight at k = N_ft/2, as for the plain filter), 0 beyond.
+__global__ void deriv_table_kernel(const double* __restrict__ c, const double* __restrict__ psihat, int n_ft, int G,
+                                   float* __restrict__ Dd)
+{
+    const int K = n_ft / 2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > G / 2) return;
+    float v = 0.0f;
+    if (i <= K) {
+        const double ck = i < K ? c[i + K] : c[0];  // c_{N_ft/2} = c_{-N_ft/2} (even)
+        const double ph = psihat[i];
+        double dv = 2.0 * kPi * (double)i * ck / (ph * ph);
+        if (i == K) dv *= 0.5;
+        v = (float)dv;
+    }
+    Dd[i] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -361,7 +529,75 @@ cudaError_t launch_interp_w(const qs_launch& L, const float* y, bool fused, cuda
     return cudaGetLastError();
 }
 
+template <int W>
+cudaError_t launch_spread_grad_w(const qs_launch& L, const float* x, const float* w, int mode, const float* Dd,
+                                 float* H2, cudaStream_t st)
+{
+    const size_t smem = (size_t)L.G * sizeof(float) * (mode == 2 ? 2 : 1);
+    auto kern = mode == 2 ? spread_grad_kernel<W, 2> : spread_grad_kernel<W, 1>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<L.P, 256, smem, st>>>(L, x, w, Dd, H2);
+    return cudaGetLastError();
+}
+
+template <int W>
+cudaError_t launch_interp_grad_w(const qs_launch& L, const float* y, const float* Hd, const float* xi, float* part,
+                                 cudaStream_t st)
+{
+    dim3 grid((unsigned)((L.M + 255) / 256), (unsigned)L.S);
+    if (L.d <= 4)
+        interp_grad_kernel<W, 4><<<grid, 256, 0, st>>>(L, y, Hd, xi, part);
+    else if (L.d <= 8)
+        interp_grad_kernel<W, 8><<<grid, 256, 0, st>>>(L, y, Hd, xi, part);
+    else if (L.d <= 16)
+        interp_grad_kernel<W, 16><<<grid, 256, 0, st>>>(L, y, Hd, xi, part);
+    else
+        interp_grad_kernel<W, 32><<<grid, 256, 0, st>>>(L, y, Hd, xi, part);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t qs_launch_deriv_table(const double* c, const double* psihat, int n_ft, int G, float* Dd, cudaStream_t st)
+{
+    deriv_table_kernel<<<(G / 2 + 1 + 127) / 128, 128, 0, st>>>(c, psihat, n_ft, G, Dd);
+    return cudaGetLastError();
+}
+
+cudaError_t qs_launch_spread_grad(const qs_launch& L, int W, const float* x, const float* w, int mode,
+                                  const float* Dd, float* H2, cudaStream_t st)
+{
+    switch (W) {
+        case 6: return launch_spread_grad_w<6>(L, x, w, mode, Dd, H2, st);
+        case 8: return launch_spread_grad_w<8>(L, x, w, mode, Dd, H2, st);
+        case 10: return launch_spread_grad_w<10>(L, x, w, mode, Dd, H2, st);
+        case 12: return launch_spread_grad_w<12>(L, x, w, mode, Dd, H2, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t qs_launch_interp_grad(const qs_launch& L, int W, const float* y, const float* Hd, const float* xi,
+                                  float* part, cudaStream_t st)
+{
+    switch (W) {
+        case 6: return launch_interp_grad_w<6>(L, y, Hd, xi, part, st);
+        case 8: return launch_interp_grad_w<8>(L, y, Hd, xi, part, st);
+        case 10: return launch_interp_grad_w<10>(L, y, Hd, xi, part, st);
+        case 12: return launch_interp_grad_w<12>(L, y, Hd, xi, part, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t qs_launch_reduce_grad(const float* part, int S, int64_t M, int d, float scale, const float* fac,
+                                  float* out, cudaStream_t st)
+{
+    const int64_t n = M * d;
+    reduce_grad_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, S, M, d, scale, fac, out);
+    return cudaGetLastError();
+}
 
 cudaError_t qs_launch_coeffs(int kernel, double kparam, int d, double tau, int n_ft, int G,
                              const double* psihat, double* c_out, float* D_out, cudaStream_t st)

@@ -76,6 +76,11 @@ struct qs_plan_s {
     float* d_part;
     unsigned int* d_flag;
     float* d_wscale;      // 2 floats, written by the weight-bound kernel of each sum
+    // gradients (d <= 32): derivative filter, second grid, vector partials
+    float* d_Dd;          // G/2 + 1
+    float* d_H2;          // P x G
+    float* d_gpart;       // 2 x (S M)max x d
+    size_t gpart_elems;
     // staging for qs_sum_host
     float* d_x;
     float* d_w;
@@ -153,6 +158,13 @@ cudaError_t qs_launch_coeffs(int kernel, double kparam, int d, double tau, int n
 cudaError_t qs_launch_project_fp32(const float* X, int64_t N, int d, const float* xi_s, int P,
                                    float* U, int64_t ldU, cudaStream_t st);
 void qs_set_error_message(const char* msg);
+cudaError_t qs_launch_deriv_table(const double* c, const double* psihat, int n_ft, int G, float* Dd, cudaStream_t st);
+cudaError_t qs_launch_spread_grad(const qs_launch& L, int W, const float* x, const float* w, int mode,
+                                  const float* Dd, float* H2, cudaStream_t st);
+cudaError_t qs_launch_interp_grad(const qs_launch& L, int W, const float* y, const float* Hd, const float* xi,
+                                  float* part, cudaStream_t st);
+cudaError_t qs_launch_reduce_grad(const float* part, int S, int64_t M, int d, float scale, const float* fac,
+                                  float* out, cudaStream_t st);
 bool qs_make_tmap(void* map_out, const void* base, int elem_bytes, int d, int64_t rows, int ldk, int box_rows);
 cudaError_t qs_launch_split_bf16(const float* X, int64_t rows, int d, int ldk, void* hi, void* lo, cudaStream_t st);
 cudaError_t qs_launch_round_tf32(const float* X, int64_t rows, int d, int ldk, float* out, cudaStream_t st);

@@ -251,7 +251,7 @@ void free_plan(qs_plan p)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
     void* bufs[] = {p->d_dirs, p->d_dirs_s, p->d_c, p->d_psihat, p->d_D, p->d_tw, p->d_U, p->d_H,
                     p->d_part, p->d_flag, p->d_wscale, p->d_x, p->d_w, p->d_y, p->d_s, p->d_xi_hi, p->d_xi_lo,
-                    p->d_xs_hi, p->d_xs_lo};
+                    p->d_xs_hi, p->d_xs_lo, p->d_Dd, p->d_H2, p->d_gpart};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete p;
@@ -497,7 +497,23 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     QS_ALLOC(p->d_D, (size_t)G / 2 + 1);
     QS_ALLOC(p->d_tw, (size_t)G / 2);
     QS_ALLOC(p->d_H, (size_t)P * G);
-    QS_ALLOC(p->d_part, (size_t)2 * p->S_max * (D.max_m > 0 ? D.max_m : 1));
+    // slice-group partials: sized for targets up to max(max_n, max_m), since the
+    // gradients evaluate at x as well as at y
+    QS_ALLOC(p->d_part, (size_t)2 * p->S_max * (maxnm > 0 ? maxnm : 1));
+    if (d <= QS_FUSED_MAX_D) {
+        // largest S(M) * M over M <= max(max_n, max_m), S as in make_launch
+        size_t sm = 1;
+        for (int64_t b = 1; b <= (maxnm + 255) / 256; ++b) {
+            int64_t S = (1024 + b - 1) / b;
+            if (S > p->S_max) S = p->S_max;
+            const int64_t rows = 256 * b < maxnm ? 256 * b : maxnm;
+            if ((size_t)(S * rows) > sm) sm = (size_t)(S * rows);
+        }
+        p->gpart_elems = 2 * sm * (size_t)d;
+        QS_ALLOC(p->d_Dd, (size_t)G / 2 + 1);
+        QS_ALLOC(p->d_H2, (size_t)P * G);
+        QS_ALLOC(p->d_gpart, p->gpart_elems);
+    }
     QS_ALLOC(p->d_flag, 1);
     QS_ALLOC(p->d_wscale, 2);
     const bool tc = proj == QS_PROJ_BF16X3 || proj == QS_PROJ_TF32;
@@ -548,6 +564,7 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     QS_CHECK(cudaMemset(p->d_flag, 0, sizeof(unsigned int)), "clear flag");
     QS_CHECK(qs_launch_coeffs((int)D.kernel, D.kparam, d, p->tau, D.n_ft, G, p->d_psihat, p->d_c, p->d_D, 0),
              "coefficient kernel launch");
+    if (p->d_Dd) QS_CHECK(qs_launch_deriv_table(p->d_c, p->d_psihat, D.n_ft, G, p->d_Dd, 0), "derivative table");
     if (tc) {
         const int eb = proj == QS_PROJ_BF16X3 ? 2 : 4;
         if (proj == QS_PROJ_BF16X3)
@@ -701,6 +718,60 @@ qs_status qs_project(qs_plan p, const float* x, int64_t N, float* u_out, int64_t
     e = cudaMemcpy2DAsync(u_out, (size_t)ldu * sizeof(float), p->d_U, (size_t)p->ldU * sizeof(float),
                           (size_t)N * sizeof(float), (size_t)p->desc.P, cudaMemcpyDeviceToDevice, st);
     return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_project: copy");
+}
+
+qs_status qs_grad(qs_plan p, const float* x, int64_t N, const float* w, const float* y, int64_t M, const float* v,
+                  float* gx, float* gw, float* gy, void* stream)
+{
+    if (!p) return fail(QS_ERR_ARG, "qs_grad: NULL plan");
+    if (N < 0 || M < 0 || N > p->desc.max_n || M > p->desc.max_m)
+        return fail(QS_ERR_ARG, "qs_grad: sizes outside the plan's limits");
+    if ((N > 0 && !x) || (M > 0 && !y)) return fail(QS_ERR_ARG, "qs_grad: NULL point array");
+    if (!gx && !gw && !gy) return QS_OK;
+    if (!p->d_gpart)
+        return fail(QS_ERR_UNSUPPORTED, "qs_grad: gradients need d <= %d (the plan has d = %d)", QS_FUSED_MAX_D,
+                    p->desc.d);
+    DeviceGuard g(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int d = p->desc.d;
+    const float scale = (float)(p->tau / (double)p->desc.P);
+    cudaError_t e = cudaSuccess;
+    // dL/dy_m = (tau/P) v_m sum_p xi_p sum_n w_n g'(b_{m,p} - a_{n,p}): sources x, targets y
+    if (gy && M > 0) {
+        if (N == 0) {
+            e = cudaMemsetAsync(gy, 0, (size_t)M * d * sizeof(float), st);
+        } else {
+            qs_launch L = make_launch(p, N, M);
+            e = qs_launch_weight_scale(L, w, st);
+            if (e == cudaSuccess) e = qs_launch_spread_grad(L, p->W, x, w, 1, p->d_Dd, p->d_H2, st);
+            if (e == cudaSuccess) e = qs_launch_interp_grad(L, p->W, y, p->d_H2, p->d_dirs, p->d_gpart, st);
+            if (e == cudaSuccess) e = qs_launch_reduce_grad(p->d_gpart, L.S, M, d, scale, v, gy, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "qs_grad: gradient in y");
+    }
+    // dL/dx_n = (tau/P) w_n sum_p xi_p sum_m v_m g'(a_{n,p} - b_{m,p}) and
+    // dL/dw_n = (1/P) sum_p sum_m v_m g(a_{n,p} - b_{m,p}): sources y (weights v), targets x
+    if ((gx || gw) && N > 0) {
+        if (M == 0) {
+            if (gx) e = cudaMemsetAsync(gx, 0, (size_t)N * d * sizeof(float), st);
+            if (e == cudaSuccess && gw) e = cudaMemsetAsync(gw, 0, (size_t)N * sizeof(float), st);
+        } else {
+            qs_launch L = make_launch(p, M, N);
+            e = qs_launch_weight_scale(L, v, st);
+            if (e == cudaSuccess) {
+                if (gx)
+                    e = qs_launch_spread_grad(L, p->W, y, v, gw ? 2 : 1, p->d_Dd, p->d_H2, st);
+                else
+                    e = qs_launch_spread(L, p->W, y, v, true, st);
+            }
+            if (e == cudaSuccess && gx) e = qs_launch_interp_grad(L, p->W, x, p->d_H2, p->d_dirs, p->d_gpart, st);
+            if (e == cudaSuccess && gx) e = qs_launch_reduce_grad(p->d_gpart, L.S, N, d, scale, w, gx, st);
+            if (e == cudaSuccess && gw) e = qs_launch_interp(L, p->W, x, true, st);
+            if (e == cudaSuccess && gw) e = qs_launch_reduce(L, gw, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "qs_grad: gradients in x / w");
+    }
+    return QS_OK;
 }
 
 qs_status qs_check(qs_plan p, void* stream)

@@ -1,0 +1,117 @@
+"""Gradients of the sliced Fourier sum on the GPU (qs_grad, KernelSumFn).
+
+Parity with the oracle's o1_grad.  Normalisation, the analogue of the sum's
+sum|w| max|F|: |g'| <= sum_k |2 pi k c_k| = D1, so
+  dL/dy:  tau * sum|w| * max|v| * D1      dL/dx:  tau * max|w| * sum|v| * D1
+  dL/dw:  sum|v| * max|F|
+and the FP32 path must stay within 1e-5 of each.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_01316_gb300 import KernelSumFn, QSPlan
+from paper_2410_01316_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _plan(prob, proj="fp32_fused", max_n=None, max_m=None):
+    return QSPlan(prob.d, prob.kernel, prob.P, prob.n_ft, prob.R, prob.kparam, dirs=prob.xi, proj=proj,
+                  max_n=max_n or prob.N, max_m=max_m or prob.M)
+
+
+def _cuda(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("kernel,kp,d", [("gauss", 1.2, 3), ("laplace", 0.8, 8), ("negdist", 0.0, 16)])
+@pytest.mark.parametrize("proj", ["fp32_fused", "bf16x3"])
+def test_grad_matches_oracle(kernel, kp, d, proj):
+    prob = W.tiny(d=d, N=1500, M=700, P=40, kernel=kernel, kparam=kp, n_ft=256, seed=40 + d)
+    v = np.random.default_rng(3).standard_normal(prob.M).astype(np.float32)
+    with _plan(prob, proj) as plan:
+        g = plan.grad(_cuda(prob.x), _cuda(prob.w), _cuda(prob.y), _cuda(v))
+        plan.check()
+        g = {k: t.cpu().numpy().astype(np.float64) for k, t in g.items()}
+    t = oracle.tau(prob.kernel, prob.kparam, prob.R)
+    c = oracle.coeffs(prob.kernel, prob.kparam, prob.d, t, prob.n_ft)
+    ref = oracle.o1_grad(prob.x, prob.w, prob.y, v, prob.xi, t, c)
+    k = np.arange(-prob.n_ft // 2, prob.n_ft // 2)
+    D1 = float(np.sum(np.abs(2 * np.pi * k * c)))
+    sw, mw = float(np.abs(prob.w).sum()), float(np.abs(prob.w).max())
+    sv, mv = float(np.abs(v).sum()), float(np.abs(v).max())
+    maxF = prob.R if kernel == "negdist" else 1.0
+    assert np.max(np.abs(g["y"] - ref["y"])) / (t * sw * mv * D1) < TOL
+    assert np.max(np.abs(g["x"] - ref["x"])) / (t * mw * sv * D1) < TOL
+    assert np.max(np.abs(g["w"] - ref["w"])) / (sv * maxF) < TOL
+    # the gradient is not trivially small relative to its normalisation
+    assert np.max(np.abs(ref["y"])) / (t * sw * mv * D1) > 1e-4
+
+
+def test_grad_single_outputs_and_unit_weights():
+    prob = W.tiny(d=5, N=800, M=300, P=24, kernel="gauss", kparam=2.0, n_ft=128, seed=5)
+    with _plan(prob) as plan:
+        full = plan.grad(_cuda(prob.x), None, _cuda(prob.y), None)
+        only_y = plan.grad(_cuda(prob.x), None, _cuda(prob.y), None, want=("y",))
+        only_w = plan.grad(_cuda(prob.x), None, _cuda(prob.y), None, want=("w",))
+        plan.check()
+    assert only_y["x"] is None and only_y["w"] is None
+    assert np.array_equal(full["y"].cpu().numpy(), only_y["y"].cpu().numpy())
+    assert np.array_equal(full["w"].cpu().numpy(), only_w["w"].cpu().numpy())
+    t = oracle.tau(prob.kernel, prob.kparam, prob.R)
+    c = oracle.coeffs(prob.kernel, prob.kparam, prob.d, t, prob.n_ft)
+    ones = np.ones(prob.M, np.float32)
+    ref = oracle.o1_grad(prob.x, None, prob.y, ones, prob.xi, t, c)
+    k = np.arange(-prob.n_ft // 2, prob.n_ft // 2)
+    D1 = float(np.sum(np.abs(2 * np.pi * k * c)))
+    assert np.max(np.abs(full["y"].cpu().numpy() - ref["y"])) / (t * prob.N * D1) < TOL
+
+
+def test_grad_fp32_finite_difference_smoke():
+    # FP32 central differences of L = <v, s(x, w, y)> against gy (smooth Gauss kernel)
+    import torch
+
+    prob = W.tiny(d=3, N=400, M=60, P=32, kernel="gauss", kparam=1.5, n_ft=128, seed=8)
+    v = _cuda(np.random.default_rng(1).standard_normal(prob.M).astype(np.float32))
+    x, w, y = _cuda(prob.x), _cuda(prob.w), _cuda(prob.y)
+    with _plan(prob) as plan:
+        gy = plan.grad(x, w, y, v, want=("y",))["y"].double()
+        h = 1e-2
+        for (m, j) in [(0, 0), (7, 2), (33, 1)]:
+            yp, ym = y.clone(), y.clone()
+            yp[m, j] += h
+            ym[m, j] -= h
+            fd = (torch.dot(v.double(), plan.sum(x, w, yp).double()) -
+                  torch.dot(v.double(), plan.sum(x, w, ym).double())) / (2 * h)
+            assert float(gy[m, j]) == pytest.approx(float(fd), rel=2e-2, abs=2e-3 * float(gy.abs().max()))
+
+
+def test_autograd_function_backward_equals_qs_grad():
+    import torch
+
+    prob = W.tiny(d=4, N=600, M=200, P=16, kernel="laplace", kparam=1.0, n_ft=128, seed=2)
+    with _plan(prob) as plan:
+        x = _cuda(prob.x).requires_grad_(True)
+        w = _cuda(prob.w).requires_grad_(True)
+        y = _cuda(prob.y).requires_grad_(True)
+        v = _cuda(np.random.default_rng(4).standard_normal(prob.M).astype(np.float32))
+        s = KernelSumFn.apply(x, w, y, plan)
+        (s * v).sum().backward()
+        g = plan.grad(x.detach(), w.detach(), y.detach(), v)
+        for name, t in (("x", x), ("w", w), ("y", y)):
+            assert torch.equal(t.grad, g[name]), name
+
+
+def test_grad_rejects_large_dimension():
+    from paper_2410_01316_gb300 import QSError
+
+    prob = W.tiny(d=40, N=100, M=50, P=8, kernel="gauss", kparam=3.0, n_ft=64, seed=1)
+    with _plan(prob, proj="fp32") as plan:
+        with pytest.raises(QSError) as ei:
+            plan.grad(_cuda(prob.x), _cuda(prob.w), _cuda(prob.y), None)
+        assert ei.value.status == 6
