@@ -62,7 +62,12 @@ def make_problem(name: str, P: int = 0, N: int = 0):
     if name == "small_gauss":
         return W.small_gauss()
     if name == "gauss64_negdist":
-        return W.gauss64_negdist()
+        kw = {}
+        if P:
+            kw["P"] = P
+        if N:
+            kw["N"] = kw["M"] = N
+        return W.gauss64_negdist(**kw)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -219,6 +224,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
+    spread_variant = plan.autotune(x, w)
     for _ in range(args.warmup):
         plan.sum(x, w, y, out=s)
     plan.check()
@@ -291,6 +297,7 @@ def run_ours(args, rank, world, local_rank):
                        "rel_err_vs_oracle": err, "rel_err_sample": err_desc,
                        "rel_err_norm": "max_m |s - s_oracle| / (sum|w| max|F|)",
                        "stage_ms": {k: round(v, 4) for k, v in stages.items()},
+                       "spread_variant": spread_variant,
                        "device_status": int(status)},
             "roofline": roof,
             "clocks": clocks,

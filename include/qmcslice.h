@@ -233,6 +233,19 @@ qs_status qs_stage_times(qs_plan plan, float* ms, int n);
 qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_dev, const float* x, int64_t N,
                          const float* w, const float* y, int64_t M, float* s, void* stream);
 
+/*
+ * Tuning.  The spread stage has variants 0..2 (one point per thread with 1,
+ * 2 or 4 lane-private grid copies);
+ * they produce bitwise identical results and differ only in speed, which
+ * depends on how the projections cluster.  qs_plan_autotune runs the spread
+ * of the given sources once per variant (timed with CUDA events on `stream`,
+ * best of 3 after a warm-up), keeps the fastest in the plan and writes its
+ * index to *chosen (may be NULL).  Synchronous.  qs_plan_set_variant fixes a
+ * variant directly (QS_ERR_ARG if out of range).
+ */
+qs_status qs_plan_autotune(qs_plan plan, const float* x, int64_t N, const float* w, int* chosen, void* stream);
+qs_status qs_plan_set_variant(qs_plan plan, int spread_variant);
+
 /* Library version string. */
 const char* qs_version(void);
 

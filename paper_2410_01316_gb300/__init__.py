@@ -104,6 +104,22 @@ class QSPlan:
                    "qs_plan_directions")
         return out
 
+    # -- tuning -------------------------------------------------------------
+    SPREAD_VARIANTS = ("point1", "point2", "point4")
+
+    def autotune(self, x, w=None, stream=None) -> str:
+        """Time the spread variants on these sources and keep the fastest."""
+        self._check_points(x, "x")
+        v = ctypes.c_int(-1)
+        _lib.check(self._lib.qs_plan_autotune(self._handle, x.data_ptr(), x.shape[0],
+                                              None if w is None else w.data_ptr(), ctypes.byref(v),
+                                              _stream_handle(stream)), "qs_plan_autotune")
+        return self.SPREAD_VARIANTS[v.value]
+
+    def set_variant(self, name: str) -> None:
+        _lib.check(self._lib.qs_plan_set_variant(self._handle, self.SPREAD_VARIANTS.index(name)),
+                   "qs_plan_set_variant")
+
     # -- stage timing -----------------------------------------------------
     STAGES = ("project_x", "spread_filter", "project_y", "interp", "reduce")
 

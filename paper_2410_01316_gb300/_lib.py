@@ -30,7 +30,8 @@ PROJ = {"auto": 0, "fp32": 1, "fp32_fused": 2, "bf16x3": 3, "tf32": 4}
 # every symbol declared in include/qmcslice.h
 EXPORTS = ("qs_plan_create", "qs_plan_destroy", "qs_plan_info", "qs_plan_directions", "qs_sum",
            "qs_sum_host", "qs_check", "qs_status_string", "qs_last_error", "qs_directions", "qs_version",
-           "qs_set_timing", "qs_stage_times", "qs_project", "qs_sum_noalloc", "qs_grad")
+           "qs_set_timing", "qs_stage_times", "qs_project", "qs_sum_noalloc", "qs_grad",
+           "qs_plan_autotune", "qs_plan_set_variant")
 
 
 class PlanDesc(ctypes.Structure):
@@ -72,6 +73,8 @@ def load() -> ctypes.CDLL:
         lib.qs_last_error.restype = c_char_p
         lib.qs_directions.argtypes = [c_int, c_int, c_int, c_u64, c_vp]
         lib.qs_project.argtypes = [c_vp, c_vp, c_i64, c_vp, c_i64, c_vp]
+        lib.qs_plan_autotune.argtypes = [c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(c_int), c_vp]
+        lib.qs_plan_set_variant.argtypes = [c_vp, c_int]
         lib.qs_grad.argtypes = [c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]
         lib.qs_sum_noalloc.argtypes = [ctypes.POINTER(PlanDesc), c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp]
         lib.qs_set_timing.argtypes = [c_vp, c_int]
@@ -80,7 +83,7 @@ def load() -> ctypes.CDLL:
         lib.qs_version.restype = c_char_p
         for name in ("qs_plan_create", "qs_plan_destroy", "qs_plan_info", "qs_plan_directions", "qs_sum",
                      "qs_sum_host", "qs_check", "qs_directions", "qs_set_timing", "qs_stage_times", "qs_project",
-                     "qs_sum_noalloc", "qs_grad"):
+                     "qs_sum_noalloc", "qs_grad", "qs_plan_autotune", "qs_plan_set_variant"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib

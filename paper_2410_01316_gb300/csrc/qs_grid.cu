@@ -221,7 +221,25 @@ __global__ void __launch_bounds__(1024) weight_scale_kernel(const float* __restr
 // ---------------------------------------------------------------------------
 // Spread + filter: one CTA per slice p.
 // ---------------------------------------------------------------------------
-template <int W, bool FUSED>
+// Projection u of point n on slice p (fused: dot product with the scaled direction).
+template <bool FUSED>
+__device__ __forceinline__ float point_u(const qs_launch& L, const float* urow, const float* x, const float* xi_sm,
+                                         int64_t n)
+{
+    if (FUSED) {
+        const float* xn = x + (size_t)n * L.d;
+        float u = 0.0f;
+        for (int j = 0; j < L.d; ++j) u = fmaf(xi_sm[j], __ldg(&xn[j]), u);
+        return u;
+    }
+    return __ldg(&urow[n]);
+}
+
+// Spread variants (the integer grid makes them bitwise identical): one point
+// per thread, W atomics each, into COPIES lane-private grid copies (copy c
+// shifted by 8 c banks), summed at the end.  More copies cut same-address
+// collisions when projections cluster; one copy keeps occupancy highest.
+template <int W, bool FUSED, int COPIES>
 __global__ void __launch_bounds__(256) spread_filter_kernel(qs_launch L, const float* __restrict__ x,
                                                             const float* __restrict__ w)
 {
@@ -232,7 +250,8 @@ __global__ void __launch_bounds__(256) spread_filter_kernel(qs_launch L, const f
     const int p = blockIdx.x;
     const int G = L.G;
     const int mask = G - 1;
-    for (int i = threadIdx.x; i < G; i += blockDim.x) gridi[i] = 0;
+    const int cstride = G + 8;
+    for (int i = threadIdx.x; i < COPIES * cstride; i += blockDim.x) gridi[i] = 0;
     if (FUSED) {
         for (int j = threadIdx.x; j < L.d; j += blockDim.x) xi_sm[j] = L.xi_s[(size_t)p * L.d + j];
     }
@@ -241,30 +260,30 @@ __global__ void __launch_bounds__(256) spread_filter_kernel(qs_launch L, const f
     __syncthreads();
 
     const float* urow = L.U + (size_t)p * L.ldU;
-    for (int64_t n = threadIdx.x; n < L.N; n += blockDim.x) {
-        float u;
-        if (FUSED) {
-            const float* xn = x + (size_t)n * L.d;
-            u = 0.0f;
-            for (int j = 0; j < L.d; ++j) u = fmaf(xi_sm[j], __ldg(&xn[j]), u);
-        } else {
-            u = __ldg(&urow[n]);
-        }
-        u = qs_check_u(u, L.half_G, L.flag);
-        float wn = w ? __ldg(&w[n]) : 1.0f;
-        if (!isfinite(wn)) {
-            atomicOr(L.flag, QS_FLAG_NONFINITE);
-            wn = 0.0f;
-        }
-        const float ws = wn * scale;
-        int l0;
-        float tap[W];
-        qs_taps<W>(u, L.win, l0, tap);
+    {
+        int* my = gridi + ((threadIdx.x & 31) % COPIES) * cstride;
+        for (int64_t n = threadIdx.x; n < L.N; n += blockDim.x) {
+            float u = qs_check_u(point_u<FUSED>(L, urow, x, xi_sm, n), L.half_G, L.flag);
+            float wn = w ? __ldg(&w[n]) : 1.0f;
+            if (!isfinite(wn)) {
+                atomicOr(L.flag, QS_FLAG_NONFINITE);
+                wn = 0.0f;
+            }
+            const float ws = wn * scale;
+            int l0;
+            float tap[W];
+            qs_taps<W>(u, L.win, l0, tap);
 #pragma unroll
-        for (int j = 0; j < W; ++j) atomicAdd(&gridi[(l0 + j) & mask], __float2int_rn(ws * tap[j]));
+            for (int j = 0; j < W; ++j) atomicAdd(&my[(l0 + j) & mask], __float2int_rn(ws * tap[j]));
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < G; i += blockDim.x) grid[i] = (float)gridi[i] * inv_scale;
+    for (int i = threadIdx.x; i < G; i += blockDim.x) {
+        int v = gridi[i];
+#pragma unroll
+        for (int c = 1; c < COPIES; ++c) v += gridi[c * cstride + i];
+        grid[i] = (float)v * inv_scale;
+    }
     __syncthreads();
 
     const int Gh = G >> 1;
@@ -441,48 +460,107 @@ __global__ void deriv_table_kernel(const double* __restrict__ c, const double* _
 
 // ---------------------------------------------------------------------------
 // Interpolation + per-group compensated slice sums.
-// grid: (ceil(M/256), S); CTA (bx, g) handles targets bx*256.. and slices
-// [g P / S, (g+1) P / S) in increasing order.
+// grid: (ceil(M / (256 TPT)), S); CTA (bx, g) handles the targets
+// bx*256*TPT + i*256 + tid (i < TPT) and the slices [g P / S, (g+1) P / S) in
+// increasing order.  The filtered row of each slice is staged in shared
+// memory (double-buffered cp.async) with its first cells repeated after the
+// end, so the W taps of a target are read without wrapping.
 // ---------------------------------------------------------------------------
-template <int W, bool FUSED, int DMAX>
-__global__ void __launch_bounds__(256) interp_kernel(qs_launch L, const float* __restrict__ y)
+constexpr int IT_THREADS = 256;
+constexpr int ROW_PAD = 16;  // >= QS_MAX_W, keeps rows 64-byte aligned
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 {
-    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Copy the G-cell row `src` into `dst` followed by its first ROW_PAD cells.
+__device__ __forceinline__ void stage_row(float* dst, const float* src, int G)
+{
+    const int n16 = (G + ROW_PAD) >> 2;
+    for (int i = threadIdx.x; i < n16; i += blockDim.x) {
+        const int c = (i << 2) < G ? (i << 2) : (i << 2) - G;
+        cp_async16(dst + (i << 2), src + c);
+    }
+    cp_async_commit();
+}
+
+template <int W, bool FUSED, int DMAX, int TPT>
+__global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const float* __restrict__ y)
+{
+    extern __shared__ float4 rows4[];
+    float* rows = reinterpret_cast<float*>(rows4);
+    const int G = L.G;
+    const int stride = G + ROW_PAD;
     const int g = blockIdx.y;
     const int S = gridDim.y;
-    if (m >= L.M) return;
     const int p0 = (int)(((int64_t)g * L.P) / S);
     const int p1 = (int)(((int64_t)(g + 1) * L.P) / S);
-    float yr[FUSED ? DMAX : 1];
-    if (FUSED) {
+    const int64_t mbase = (int64_t)blockIdx.x * IT_THREADS * TPT + threadIdx.x;
+    const int mask = G - 1;
+
+    float yr[FUSED ? DMAX * TPT : 1];
+    float hi[TPT], lo[TPT];
+    bool live[TPT];
 #pragma unroll
-        for (int j = 0; j < DMAX; ++j) yr[j] = j < L.d ? __ldg(&y[(size_t)m * L.d + j]) : 0.0f;
-    }
-    const int mask = L.G - 1;
-    float hi = 0.0f, lo = 0.0f;
-    for (int p = p0; p < p1; ++p) {
-        float u;
+    for (int i = 0; i < TPT; ++i) {
+        const int64_t m = mbase + (int64_t)i * IT_THREADS;
+        live[i] = m < L.M;
+        hi[i] = 0.0f;
+        lo[i] = 0.0f;
         if (FUSED) {
-            const float* xs = L.xi_s + (size_t)p * L.d;
-            u = 0.0f;
 #pragma unroll
-            for (int j = 0; j < DMAX; ++j)
-                if (j < L.d) u = fmaf(__ldg(&xs[j]), yr[j], u);
-        } else {
-            u = __ldg(&L.U[(size_t)p * L.ldU + m]);
+            for (int j = 0; j < DMAX; ++j) yr[i * DMAX + j] = (live[i] && j < L.d) ? __ldg(&y[(size_t)m * L.d + j]) : 0.0f;
         }
-        u = qs_check_u(u, L.half_G, L.flag);
-        int l0;
-        float tap[W];
-        qs_taps<W>(u, L.win, l0, tap);
-        const float* h = L.H + (size_t)p * L.G;
-        float t = 0.0f;
-#pragma unroll
-        for (int j = 0; j < W; ++j) t = fmaf(__ldg(&h[(l0 + j) & mask]), tap[j], t);
-        qs_two_sum(hi, lo, t);
     }
-    L.part[(size_t)g * L.M + m] = hi;
-    L.part[(size_t)(S + g) * L.M + m] = lo;
+    if (p0 < p1) stage_row(rows, L.H + (size_t)p0 * G, G);
+    for (int p = p0; p < p1; ++p) {
+        const float* row = rows + ((p - p0) & 1) * stride;
+        if (p + 1 < p1) {
+            stage_row(rows + ((p + 1 - p0) & 1) * stride, L.H + (size_t)(p + 1) * G, G);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < TPT; ++i) {
+            if (!live[i]) continue;
+            const int64_t m = mbase + (int64_t)i * IT_THREADS;
+            float u;
+            if (FUSED) {
+                const float* xs = L.xi_s + (size_t)p * L.d;
+                u = 0.0f;
+#pragma unroll
+                for (int j = 0; j < DMAX; ++j)
+                    if (j < L.d) u = fmaf(__ldg(&xs[j]), yr[i * DMAX + j], u);
+            } else {
+                u = __ldg(&L.U[(size_t)p * L.ldU + m]);
+            }
+            u = qs_check_u(u, L.half_G, L.flag);
+            int l0;
+            float tap[W];
+            qs_taps<W>(u, L.win, l0, tap);
+            const float* h = row + (l0 & mask);
+            float t = 0.0f;
+#pragma unroll
+            for (int j = 0; j < W; ++j) t = fmaf(h[j], tap[j], t);
+            qs_two_sum(hi[i], lo[i], t);
+        }
+        __syncthreads();  // the buffer just read is refilled two slices later
+    }
+#pragma unroll
+    for (int i = 0; i < TPT; ++i) {
+        if (!live[i]) continue;
+        const int64_t m = mbase + (int64_t)i * IT_THREADS;
+        L.part[(size_t)g * L.M + m] = hi[i];
+        L.part[(size_t)(S + g) * L.M + m] = lo[i];
+    }
 }
 
 // s_m = (1/P) sum over slice groups in increasing order (TwoSum).
@@ -498,11 +576,11 @@ __global__ void reduce_kernel(const float* __restrict__ part, int S, int64_t M, 
     s[m] = (hi + lo) / (float)P;
 }
 
-template <int W>
-cudaError_t launch_spread_w(const qs_launch& L, const float* x, const float* w, bool fused, cudaStream_t st)
+template <int W, bool FUSED, int COPIES>
+cudaError_t launch_spread_v(const qs_launch& L, const float* x, const float* w, cudaStream_t st)
 {
-    const size_t smem = (size_t)L.G * sizeof(float);
-    auto kern = fused ? spread_filter_kernel<W, true> : spread_filter_kernel<W, false>;
+    const size_t smem = (size_t)COPIES * (L.G + 8) * sizeof(int);
+    auto kern = spread_filter_kernel<W, FUSED, COPIES>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -511,21 +589,46 @@ cudaError_t launch_spread_w(const qs_launch& L, const float* x, const float* w, 
     return cudaGetLastError();
 }
 
+template <int W, bool FUSED>
+cudaError_t launch_spread_f(const qs_launch& L, const float* x, const float* w, int variant, cudaStream_t st)
+{
+    switch (variant) {
+        case QS_SPREAD_POINT1: return launch_spread_v<W, FUSED, 1>(L, x, w, st);
+        case QS_SPREAD_POINT2: return launch_spread_v<W, FUSED, 2>(L, x, w, st);
+        case QS_SPREAD_POINT4: return launch_spread_v<W, FUSED, 4>(L, x, w, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int W>
+cudaError_t launch_spread_w(const qs_launch& L, const float* x, const float* w, bool fused, int variant,
+                            cudaStream_t st)
+{
+    return fused ? launch_spread_f<W, true>(L, x, w, variant, st) : launch_spread_f<W, false>(L, x, w, variant, st);
+}
+
 template <int W>
 cudaError_t launch_interp_w(const qs_launch& L, const float* y, bool fused, cudaStream_t st)
 {
-    dim3 grid((unsigned)((L.M + 255) / 256), (unsigned)L.S);
-    if (!fused) {
-        interp_kernel<W, false, 1><<<grid, 256, 0, st>>>(L, y);
-    } else if (L.d <= 4) {
-        interp_kernel<W, true, 4><<<grid, 256, 0, st>>>(L, y);
-    } else if (L.d <= 8) {
-        interp_kernel<W, true, 8><<<grid, 256, 0, st>>>(L, y);
-    } else if (L.d <= 16) {
-        interp_kernel<W, true, 16><<<grid, 256, 0, st>>>(L, y);
-    } else {
-        interp_kernel<W, true, 32><<<grid, 256, 0, st>>>(L, y);
-    }
+    const size_t smem = (size_t)2 * (L.G + ROW_PAD) * sizeof(float);
+    const unsigned gx = (unsigned)((L.M + (int64_t)IT_THREADS * qs_interp_tpt(fused, L.d) - 1) /
+                                   ((int64_t)IT_THREADS * qs_interp_tpt(fused, L.d)));
+    dim3 grid(gx, (unsigned)L.S);
+#define QS_LAUNCH_INTERP(FU, DM, TP)                                                                       \
+    do {                                                                                                   \
+        auto k_ = interp_kernel<W, FU, DM, TP>;                                                            \
+        if (smem > 48 * 1024) {                                                                            \
+            cudaError_t e_ = cudaFuncSetAttribute(k_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+            if (e_ != cudaSuccess) return e_;                                                              \
+        }                                                                                                  \
+        k_<<<grid, IT_THREADS, smem, st>>>(L, y);                                                          \
+    } while (0)
+    if (!fused) QS_LAUNCH_INTERP(false, 1, 4);
+    else if (L.d <= 4) QS_LAUNCH_INTERP(true, 4, 2);
+    else if (L.d <= 8) QS_LAUNCH_INTERP(true, 8, 2);
+    else if (L.d <= 16) QS_LAUNCH_INTERP(true, 16, 1);
+    else QS_LAUNCH_INTERP(true, 32, 1);
+#undef QS_LAUNCH_INTERP
     return cudaGetLastError();
 }
 
@@ -617,10 +720,10 @@ cudaError_t qs_launch_spread(const qs_launch& L, int W, const float* x, const fl
                              cudaStream_t st)
 {
     switch (W) {
-        case 6: return launch_spread_w<6>(L, x, w, fused, st);
-        case 8: return launch_spread_w<8>(L, x, w, fused, st);
-        case 10: return launch_spread_w<10>(L, x, w, fused, st);
-        case 12: return launch_spread_w<12>(L, x, w, fused, st);
+        case 6: return launch_spread_w<6>(L, x, w, fused, L.spread_variant, st);
+        case 8: return launch_spread_w<8>(L, x, w, fused, L.spread_variant, st);
+        case 10: return launch_spread_w<10>(L, x, w, fused, L.spread_variant, st);
+        case 12: return launch_spread_w<12>(L, x, w, fused, L.spread_variant, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -25,6 +25,14 @@ constexpr int QS_MAX_TERMS = QS_MAX_HALF + 1;  // terms per even / odd part
 constexpr int QS_MAX_G = 16384;                // grid cells per slice (64 KB shared)
 constexpr int QS_FUSED_MAX_D = 32;             // largest d of the fused form
 
+// Spread kernel variants (see spread_filter_kernel); chosen per plan by timing.
+enum {
+    QS_SPREAD_POINT1 = 0,  // point per thread, one grid
+    QS_SPREAD_POINT2 = 1,  // point per thread, two lane-private grid copies
+    QS_SPREAD_POINT4 = 2,  // point per thread, four copies
+    QS_SPREAD_NVARIANTS = 3
+};
+
 // Tap polynomials.  For tap j of the first half (0 <= j < m), with the
 // centred fractional offset s in [-1/2, 1/2]:
 //   psi(s + m - 1/2 - j)         = E_j(s^2) + s O_j(s^2)
@@ -49,6 +57,7 @@ struct qs_launch {
     int S;                // number of slice groups of the interpolation
     unsigned int* flag;   // device error flag
     float* wscale;        // [0] = 2^30 / sum|w| (fixed-point scale of the grids), [1] = its inverse
+    int spread_variant;   // QS_SPREAD_* (all variants give bitwise identical grids)
     qs_window win;
 };
 
@@ -64,6 +73,7 @@ struct qs_plan_s {
     int S_max;            // slice-group capacity of the partial buffer
     size_t U_elems;
     qs_window win;
+    int spread_variant;   // fixed by qs_set_spread_variant or the first timed tuning
     // device buffers
     float* d_dirs;        // P x d
     float* d_dirs_s;      // P x d scaled by G tau
@@ -148,6 +158,12 @@ __device__ __forceinline__ float qs_check_u(float u, float half_G, unsigned int*
         return 0.0f;
     }
     return u;
+}
+
+// Targets per thread of the interpolation kernel (256 threads per CTA).
+__host__ __device__ inline int qs_interp_tpt(bool fused, int d)
+{
+    return !fused ? 4 : (d <= 8 ? 2 : 1);
 }
 
 // ---------------------------------------------------------------------------

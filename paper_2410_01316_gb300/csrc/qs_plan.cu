@@ -267,7 +267,9 @@ cudaError_t dalloc(T** ptr, size_t count)
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
-qs_launch make_launch(const qs_plan p, int64_t N, int64_t M)
+// targets_per_cta: targets covered by one CTA of the interpolation kernel that
+// will consume the launch (256 x targets per thread; 256 for the gradients).
+qs_launch make_launch(const qs_plan p, int64_t N, int64_t M, int64_t targets_per_cta)
 {
     qs_launch L;
     memset(&L, 0, sizeof(L));
@@ -287,10 +289,11 @@ qs_launch make_launch(const qs_plan p, int64_t N, int64_t M)
     L.part = p->d_part;
     L.flag = p->d_flag;
     L.wscale = p->d_wscale;
+    L.spread_variant = p->spread_variant;
     L.win = p->win;
     // slice groups of the interpolation: enough CTAs to fill the device,
     // chosen from M and P only so results do not depend on the GPU model
-    const int64_t blocks_m = (M + 255) / 256;
+    const int64_t blocks_m = (M + targets_per_cta - 1) / targets_per_cta;
     int64_t S = (1024 + blocks_m - 1) / (blocks_m > 0 ? blocks_m : 1);
     if (S < 1) S = 1;
     if (S > p->S_max) S = p->S_max;
@@ -634,8 +637,8 @@ qs_status qs_sum(qs_plan p, const float* x, int64_t N, const float* w, const flo
         e = cudaMemsetAsync(s, 0, (size_t)M * sizeof(float), st);
         return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_sum: memset");
     }
-    qs_launch L = make_launch(p, N, M);
     const bool fused = p->proj == QS_PROJ_FP32_FUSED;
+    qs_launch L = make_launch(p, N, M, 256 * qs_interp_tpt(fused, p->desc.d));
     const bool tm = p->timing != 0;
 #define QS_MARK(i)                                              \
     do {                                                        \
@@ -741,7 +744,7 @@ qs_status qs_grad(qs_plan p, const float* x, int64_t N, const float* w, const fl
         if (N == 0) {
             e = cudaMemsetAsync(gy, 0, (size_t)M * d * sizeof(float), st);
         } else {
-            qs_launch L = make_launch(p, N, M);
+            qs_launch L = make_launch(p, N, M, 256);
             e = qs_launch_weight_scale(L, w, st);
             if (e == cudaSuccess) e = qs_launch_spread_grad(L, p->W, x, w, 1, p->d_Dd, p->d_H2, st);
             if (e == cudaSuccess) e = qs_launch_interp_grad(L, p->W, y, p->d_H2, p->d_dirs, p->d_gpart, st);
@@ -756,7 +759,10 @@ qs_status qs_grad(qs_plan p, const float* x, int64_t N, const float* w, const fl
             if (gx) e = cudaMemsetAsync(gx, 0, (size_t)N * d * sizeof(float), st);
             if (e == cudaSuccess && gw) e = cudaMemsetAsync(gw, 0, (size_t)N * sizeof(float), st);
         } else {
-            qs_launch L = make_launch(p, M, N);
+            // gw uses the (fused) interpolation kernel, gx the gradient kernel: each
+            // gets the slice-group count matching its CTA shape
+            qs_launch L = make_launch(p, M, N, 256);
+            qs_launch Lw = make_launch(p, M, N, 256 * qs_interp_tpt(true, p->desc.d));
             e = qs_launch_weight_scale(L, v, st);
             if (e == cudaSuccess) {
                 if (gx)
@@ -766,11 +772,66 @@ qs_status qs_grad(qs_plan p, const float* x, int64_t N, const float* w, const fl
             }
             if (e == cudaSuccess && gx) e = qs_launch_interp_grad(L, p->W, x, p->d_H2, p->d_dirs, p->d_gpart, st);
             if (e == cudaSuccess && gx) e = qs_launch_reduce_grad(p->d_gpart, L.S, N, d, scale, w, gx, st);
-            if (e == cudaSuccess && gw) e = qs_launch_interp(L, p->W, x, true, st);
-            if (e == cudaSuccess && gw) e = qs_launch_reduce(L, gw, st);
+            if (e == cudaSuccess && gw) e = qs_launch_interp(Lw, p->W, x, true, st);
+            if (e == cudaSuccess && gw) e = qs_launch_reduce(Lw, gw, st);
         }
         if (e != cudaSuccess) return cuda_fail(e, "qs_grad: gradients in x / w");
     }
+    return QS_OK;
+}
+
+qs_status qs_plan_set_variant(qs_plan p, int v)
+{
+    if (!p) return fail(QS_ERR_ARG, "qs_plan_set_variant: NULL plan");
+    if (v < 0 || v >= QS_SPREAD_NVARIANTS) return fail(QS_ERR_ARG, "qs_plan_set_variant: variant %d out of range", v);
+    p->spread_variant = v;
+    return QS_OK;
+}
+
+qs_status qs_plan_autotune(qs_plan p, const float* x, int64_t N, const float* w, int* chosen, void* stream)
+{
+    if (!p) return fail(QS_ERR_ARG, "qs_plan_autotune: NULL plan");
+    if (N <= 0 || N > (p->desc.max_n > p->desc.max_m ? p->desc.max_n : p->desc.max_m) || !x)
+        return fail(QS_ERR_ARG, "qs_plan_autotune: need 0 < N <= max(max_n, max_m) sources");
+    DeviceGuard g(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool fused = p->proj == QS_PROJ_FP32_FUSED;
+    qs_launch L = make_launch(p, N, 1, 256);
+    cudaError_t e = cudaSuccess;
+    if (!fused) e = project(p, x, N, st);
+    if (e == cudaSuccess) e = qs_launch_weight_scale(L, w, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_plan_autotune: setup");
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return fail(QS_ERR_CUDA, "qs_plan_autotune: event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(QS_ERR_CUDA, "qs_plan_autotune: event");
+    }
+    int best = 0;
+    float best_ms = 3.4e38f;
+    for (int v = 0; v < QS_SPREAD_NVARIANTS && e == cudaSuccess; ++v) {
+        L.spread_variant = v;
+        e = qs_launch_spread(L, p->W, x, w, fused, st);  // warm-up
+        float vbest = 3.4e38f;
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+            cudaEventRecord(e0, st);
+            e = qs_launch_spread(L, p->W, x, w, fused, st);
+            cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < vbest) vbest = ms;
+        }
+        if (vbest < best_ms) {
+            best_ms = vbest;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_plan_autotune: timing");
+    p->spread_variant = best;
+    if (chosen) *chosen = best;
     return QS_OK;
 }
 

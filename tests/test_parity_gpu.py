@@ -184,3 +184,24 @@ def test_mnist_laplace_full_size_sampled_targets():
     idx = np.random.default_rng(77).choice(prob.M, 128, replace=False)
     ref = _oracle(prob, y=prob.y[idx])
     assert _err(s[idx], ref, prob) < TOL_FP32
+
+
+@pytest.mark.parametrize("proj", ["fp32_fused", "fp32"])
+@pytest.mark.parametrize("window", [6, 8, 12])
+def test_spread_variants_are_bitwise_identical(proj, window):
+    import torch
+
+    prob = W.tiny(d=5, N=3001, M=500, P=20, kernel="negdist", kparam=0.0, n_ft=256, seed=21)
+    x, w, y = (torch.from_numpy(a).cuda() for a in (prob.x, prob.w, prob.y))
+    outs = []
+    with _plan(prob, proj, window) as plan:
+        for v in plan.SPREAD_VARIANTS:
+            plan.set_variant(v)
+            outs.append(plan.sum(x, w, y).cpu().numpy())
+        plan.check()
+        chosen = plan.autotune(x, w)
+        assert chosen in plan.SPREAD_VARIANTS
+        outs.append(plan.sum(x, w, y).cpu().numpy())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    assert _err(outs[0].astype(np.float64), _oracle(prob), prob) < TOL_FP32
