@@ -428,6 +428,116 @@ def run_mmd_flow(args, rank, world, local_rank):
     plan.close()
 
 
+def batch256_problems(n=256, seed=20241004):
+    """256 Gauss problems: N, M log-uniform in [1e3, 1e5], d in {3, 16, 64},
+    N_ft in {256, 512, 1024}, P = 256 (Fibonacci for d = 3, else orthogonal),
+    sigma by the median rule."""
+    from paper_2410_01316_gb300 import workloads as W
+
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        N = int(np.exp(rng.uniform(np.log(1e3), np.log(1e5))))
+        M = int(np.exp(rng.uniform(np.log(1e3), np.log(1e5))))
+        d = int(rng.choice([3, 16, 64]))
+        n_ft = int(rng.choice([256, 512, 1024]))
+        x = W.gaussian(rng, N, d)
+        y = W.gaussian(rng, M, d)
+        w = rng.standard_normal(N).astype(np.float32)
+        sigma = W.median_pair_distance(x, y, 1000, seed + 7 * i)
+        xi = W.directions_fibonacci(256) if d == 3 else W.directions_orthogonal(rng, 256, d)
+        out.append(W.Problem(f"batch{i}", d, "gauss", sigma, 256, n_ft, x, w, y, xi, W.radius(x, y)))
+    return out
+
+
+def run_batch(args, rank, world, local_rank):
+    """One persistent, graph-captured launch over 256 independent problems."""
+    import torch
+
+    from paper_2410_01316_gb300 import QSBatch, QSPlan
+    from paper_2410_01316_gb300 import build as qbuild
+
+    qbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    probs = batch256_problems()
+    plans = [QSPlan(p.d, p.kernel, p.P, p.n_ft, p.R, p.kparam, dirs=p.xi, proj="fp32_fused", max_n=p.N,
+                    max_m=p.M) for p in probs]
+    data = [(torch.from_numpy(p.x).to(dev), torch.from_numpy(p.w).to(dev), torch.from_numpy(p.y).to(dev),
+             torch.empty(p.M, dtype=torch.float32, device=dev)) for p in probs]
+    ps = sum(p.point_slices for p in probs)
+    batch = QSBatch(plans)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    # tune the interpolation tiling (results are bitwise identical across tilings)
+    best = None
+    with torch.cuda.stream(stream):
+        for tpt in (1, 2, 4):
+            batch.set_tiling(tpt)
+            batch.sum(data, stream=stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            batch.sum(data, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            if best is None or t < best[1]:
+                best = (tpt, t)
+        batch.set_tiling(best[0])
+        g = torch.cuda.CUDAGraph()
+        batch.sum(data, stream=stream)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=stream):
+            batch.sum(data, stream=stream)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(smi_gpu_id(dev))
+    sampler.start()
+    time.sleep(0.3)
+    ms = []
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    batch.check()
+    # the same problems as 256 separate qs_sum calls on one stream
+    seq = []
+    for rep in range(2):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for pl, (x, w, y, out) in zip(plans, data):
+            pl.sum(x, w, y, out=out)
+        e1.record()
+        e1.synchronize()
+        seq.append(e0.elapsed_time(e1))
+    t = sum(ms) / len(ms)
+    line = {"metric": METRIC, "value": ps / (t / 1e3) / 1e9, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch256: 256 Gauss problems, N, M log-uniform in [1e3, 1e5], d in {3,16,64}, "
+                                   "N_ft in {256,512,1024}, P=256, one persistent graph-captured launch",
+                       "point_slices": ps, "interp_targets_per_thread": best[0],
+                       "sequential_qs_sum_ms": min(seq),
+                       "speedup_vs_sequential": min(seq) / t,
+                       "l2": "flushed between steps"},
+            "clocks": clocks, "gpu_launches": args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for pl in plans:
+        pl.close()
+
+
 def launches_per_step(plan) -> int:
     # [split x,] projection x, weight bound, spread+filter, [split y,] projection y,
     # interpolation, reduction
@@ -542,6 +652,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "mmd_flow16":
         run_mmd_flow(args, rank, world, local)
+    elif args.workload == "batch256":
+        run_batch(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1 and _PG is not None:

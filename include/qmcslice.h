@@ -74,7 +74,7 @@ typedef enum {
 typedef enum {
     QS_PROJ_AUTO = 0,       /* library choice */
     QS_PROJ_FP32 = 1,       /* FP32 SIMT GEMM into a P x N workspace */
-    QS_PROJ_FP32_FUSED = 2, /* FP32 dot products inside spread / interpolation (d <= 32) */
+    QS_PROJ_FP32_FUSED = 2, /* FP32 dot products inside spread / interpolation (d <= 64) */
     QS_PROJ_BF16X3 = 3,     /* tensor-core GEMM, x = hi + lo split in BF16, three products */
     QS_PROJ_TF32 = 4        /* tensor-core GEMM in TF32 */
 } qs_proj;
@@ -216,7 +216,7 @@ qs_status qs_stage_times(qs_plan plan, float* ms, int n);
  *
  * desc: as for qs_plan_create; dirs, seed, dirs_host, max_n and max_m are
  *       ignored and proj must be QS_PROJ_AUTO or QS_PROJ_FP32_FUSED (FP32 dot
- *       products inside the spread and interpolation; d <= 32).
+ *       products inside the spread and interpolation; d <= 64).
  * dirs_dev: P x d FP32 directions in device memory (caller-owned).
  * x, w, y, s: as for qs_sum (device memory, w may be NULL).
  * Sizes: P * 2 n_ft grid values, the tables and the slice partial sums must
@@ -232,6 +232,44 @@ qs_status qs_stage_times(qs_plan plan, float* ms, int n);
  */
 qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_dev, const float* x, int64_t N,
                          const float* w, const float* y, int64_t M, float* s, void* stream);
+
+/*
+ * Batched sums.  Many independent problems, each with its own plan (its own
+ * d <= 64, P, N_ft, kernel and directions; all plans must share the window
+ * width), run in ONE persistent launch that drains a queue of
+ * (problem, slice) spread items followed by (problem, target block)
+ * interpolation items, largest problems first.  Projections are FP32 dot
+ * products inside the items.  Each target's slice sum is formed in slice
+ * order by one thread, so results do not depend on the tiling.
+ *
+ * qs_batch_create: plans are borrowed (they must outlive the batch); their
+ *   workspaces hold the intermediate grids.  Allocates the batch's
+ *   descriptor table (pinned host + device).
+ * qs_sum_batched: probs[k] is the problem of plans[k] (device pointers as for
+ *   qs_sum; w may be NULL).  Asynchronous on `stream`.  The problem table is
+ *   uploaded from the batch's pinned staging; outside graph capture the call
+ *   first waits until the previous call's upload has executed.  A captured
+ *   call replays with the table of the call that was captured.
+ * qs_batch_check: synchronises `stream` and returns the worst data-error
+ *   status of the batch's plans (clearing their flags).
+ * qs_batch_set_tiling: largest number of targets per thread of the
+ *   interpolation items (1, 2 or 4; the default 4 is capped by d so that a
+ *   block's coordinates fit a 64 KB shared tile).
+ */
+typedef struct qs_batch_s* qs_batch;
+typedef struct {
+    const float* x;  /* N x d sources */
+    int64_t N;
+    const float* w;  /* N weights or NULL */
+    const float* y;  /* M x d targets */
+    int64_t M;
+    float* s;        /* M outputs */
+} qs_problem;
+qs_status qs_batch_create(qs_batch* out, const qs_plan* plans, int nprob);
+qs_status qs_batch_destroy(qs_batch batch);
+qs_status qs_sum_batched(qs_batch batch, const qs_problem* probs, void* stream);
+qs_status qs_batch_check(qs_batch batch, void* stream);
+qs_status qs_batch_set_tiling(qs_batch batch, int targets_per_thread);
 
 /*
  * Tuning.  The spread stage has variants 0..2 (one point per thread with 1,

@@ -17,7 +17,7 @@ import numpy as np
 from . import _lib
 from ._lib import QSError
 
-__all__ = ["QSPlan", "QSError", "KernelSumFn", "directions", "kernel_sum", "version"]
+__all__ = ["QSPlan", "QSBatch", "QSError", "KernelSumFn", "directions", "kernel_sum", "version"]
 
 
 def version() -> str:
@@ -216,6 +216,50 @@ class QSPlan:
     def status(self, stream=None) -> int:
         """Synchronise and return the device error status without raising."""
         return int(self._lib.qs_check(self._handle, _stream_handle(stream)))
+
+
+class QSBatch:
+    """Many independent problems (one QSPlan each) summed in one persistent launch."""
+
+    def __init__(self, plans):
+        self._lib = _lib.load()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._handle.value for p in self.plans])
+        self._handle = ctypes.c_void_p()
+        _lib.check(self._lib.qs_batch_create(ctypes.byref(self._handle), arr, len(self.plans)), "qs_batch_create")
+        self._probs = (_lib.Problem * len(self.plans))()
+
+    def close(self):
+        if getattr(self, "_handle", None) and self._handle.value:
+            self._lib.qs_batch_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tiling(self, targets_per_thread: int) -> None:
+        _lib.check(self._lib.qs_batch_set_tiling(self._handle, targets_per_thread), "qs_batch_set_tiling")
+
+    def sum(self, problems, stream=None):
+        """problems: list of (x, w, y, out) CUDA tensors (w may be None), one per plan."""
+        if len(problems) != len(self.plans):
+            raise ValueError("one problem per plan")
+        for k, (x, w, y, out) in enumerate(problems):
+            pl = self.plans[k]
+            pl._check_points(x, "x")
+            pl._check_points(y, "y")
+            pl._check_points(out, "out", rows=y.shape[0])
+            if w is not None:
+                pl._check_points(w, "w", rows=x.shape[0])
+            self._probs[k] = _lib.Problem(x.data_ptr(), x.shape[0], None if w is None else w.data_ptr(),
+                                          y.data_ptr(), y.shape[0], out.data_ptr())
+        _lib.check(self._lib.qs_sum_batched(self._handle, self._probs, _stream_handle(stream)), "qs_sum_batched")
+
+    def check(self, stream=None) -> None:
+        _lib.check(self._lib.qs_batch_check(self._handle, _stream_handle(stream)), "qs_batch_check")
 
 
 def _make_fn():

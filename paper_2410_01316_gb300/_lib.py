@@ -31,7 +31,8 @@ PROJ = {"auto": 0, "fp32": 1, "fp32_fused": 2, "bf16x3": 3, "tf32": 4}
 EXPORTS = ("qs_plan_create", "qs_plan_destroy", "qs_plan_info", "qs_plan_directions", "qs_sum",
            "qs_sum_host", "qs_check", "qs_status_string", "qs_last_error", "qs_directions", "qs_version",
            "qs_set_timing", "qs_stage_times", "qs_project", "qs_sum_noalloc", "qs_grad",
-           "qs_plan_autotune", "qs_plan_set_variant")
+           "qs_plan_autotune", "qs_plan_set_variant", "qs_batch_create", "qs_batch_destroy", "qs_sum_batched",
+           "qs_batch_check", "qs_batch_set_tiling")
 
 
 class PlanDesc(ctypes.Structure):
@@ -40,6 +41,10 @@ class PlanDesc(ctypes.Structure):
         ("seed", c_u64), ("dirs_host", c_vp), ("n_ft", c_int), ("window", c_int),
         ("oversampling", c_dbl), ("radius", c_dbl), ("proj", c_int), ("max_n", c_i64), ("max_m", c_i64),
     ]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("x", c_vp), ("N", c_i64), ("w", c_vp), ("y", c_vp), ("M", c_i64), ("s", c_vp)]
 
 
 class QSError(RuntimeError):
@@ -73,6 +78,11 @@ def load() -> ctypes.CDLL:
         lib.qs_last_error.restype = c_char_p
         lib.qs_directions.argtypes = [c_int, c_int, c_int, c_u64, c_vp]
         lib.qs_project.argtypes = [c_vp, c_vp, c_i64, c_vp, c_i64, c_vp]
+        lib.qs_batch_create.argtypes = [ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_int]
+        lib.qs_batch_destroy.argtypes = [c_vp]
+        lib.qs_sum_batched.argtypes = [c_vp, ctypes.POINTER(Problem), c_vp]
+        lib.qs_batch_check.argtypes = [c_vp, c_vp]
+        lib.qs_batch_set_tiling.argtypes = [c_vp, c_int]
         lib.qs_plan_autotune.argtypes = [c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(c_int), c_vp]
         lib.qs_plan_set_variant.argtypes = [c_vp, c_int]
         lib.qs_grad.argtypes = [c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]
@@ -83,7 +93,9 @@ def load() -> ctypes.CDLL:
         lib.qs_version.restype = c_char_p
         for name in ("qs_plan_create", "qs_plan_destroy", "qs_plan_info", "qs_plan_directions", "qs_sum",
                      "qs_sum_host", "qs_check", "qs_directions", "qs_set_timing", "qs_stage_times", "qs_project",
-                     "qs_sum_noalloc", "qs_grad", "qs_plan_autotune", "qs_plan_set_variant"):
+                     "qs_sum_noalloc", "qs_grad", "qs_plan_autotune", "qs_plan_set_variant",
+                     "qs_batch_create", "qs_batch_destroy", "qs_sum_batched", "qs_batch_check",
+                     "qs_batch_set_tiling"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib

@@ -1,0 +1,443 @@
+// Batched sums: many independent problems (each with its own plan: d, P,
+// N_ft, kernel, directions) of uneven N and M in one persistent launch.
+//
+// Work items, dequeued in order from one 64-bit counter:
+//   [0, n_spread)        (problem k, slice p): spread + FFT filter of slice p,
+//                        writing the problem's filtered grid row H_k[p]
+//   [n_spread, n_items)  (problem k, target block b): interpolation of a block
+//                        of targets over all P_k slices, writing s directly
+// Problems are queued largest first.  A target-block item waits until all
+// P_k spread items of its problem have published their rows (a per-problem
+// counter, incremented after a fence).  Those items were dequeued earlier,
+// so they are held by running CTAs and will finish: the wait cannot
+// deadlock, whatever the grid size.  The wait is bounded by a clock budget;
+// on expiry the item sets the problem's timeout flag and is skipped.
+// Rows written in this launch are read back through L2 only (cp.async.cg).
+//
+// Projections are computed in FP32 inside the items (the fused form), for
+// any d <= QS_BATCH_MAX_D.  Each target's slice sum runs in slice order with
+// TwoSum in one thread, so the result does not depend on the tiling chosen
+// by the tuner.
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "qs_device.cuh"
+#include "qs_internal.cuh"
+
+using namespace qsdev;
+
+namespace {
+
+constexpr int BT = 256;                  // threads per CTA
+constexpr int YTILE_BYTES = 64 * 1024;   // shared tile of target coordinates
+
+struct BatchDesc {
+    const float* x;
+    const float* w;
+    const float* y;
+    float* s;
+    int64_t N, M;
+    int d, P, G, tpt;
+    float half_G;
+    const float* xi_s;
+    const float* D;
+    const float2* tw;
+    float* H;
+    unsigned int* flag;
+    int64_t spread_begin, interp_begin, interp_blocks;
+};
+
+__device__ int find_item(const BatchDesc* __restrict__ descs, int nprob, int64_t item, bool interp)
+{
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {  // last k with begin_k <= item
+        const int mid = (lo + hi + 1) >> 1;
+        const int64_t b = interp ? descs[mid].interp_begin : descs[mid].spread_begin;
+        if (b <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int W>
+__device__ void batch_spread(const BatchDesc& D, int p, const qs_window& win, unsigned char* smem)
+{
+    __shared__ float xi_sm[QS_BATCH_MAX_D];
+    __shared__ float red[BT / 32];
+    __shared__ float s_scale[2];
+    int* gridi = reinterpret_cast<int*>(smem);
+    float* grid = reinterpret_cast<float*>(smem);
+    const int G = D.G, mask = G - 1, d = D.d;
+    for (int i = threadIdx.x; i < G; i += BT) gridi[i] = 0;
+    for (int j = threadIdx.x; j < d; j += BT) xi_sm[j] = __ldg(&D.xi_s[(size_t)p * d + j]);
+    // fixed-point scale 2^30 / sum|w| (as in the single-problem spread)
+    float acc = 0.0f;
+    if (D.w)
+        for (int64_t n = threadIdx.x; n < D.N; n += BT) acc += fabsf(__ldg(&D.w[n]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float B = 0.0f;
+        for (int i = 0; i < BT / 32; ++i) B += red[i];
+        if (!D.w) B = (float)D.N;
+        float sc = 0.0f, inv = 0.0f;
+        if (!isfinite(B)) {
+            atomicOr(D.flag, QS_FLAG_NONFINITE);
+        } else if (B > 0.0f) {
+            sc = 1073741824.0f / B;
+            inv = B / 1073741824.0f;
+            if (!isfinite(sc)) sc = inv = 0.0f;
+        }
+        s_scale[0] = sc;
+        s_scale[1] = inv;
+    }
+    __syncthreads();
+    const float scale = s_scale[0];
+    for (int64_t n = threadIdx.x; n < D.N; n += BT) {
+        const float* xn = D.x + (size_t)n * d;
+        float u = 0.0f;
+        for (int j = 0; j < d; ++j) u = fmaf(xi_sm[j], __ldg(&xn[j]), u);
+        u = qs_check_u(u, D.half_G, D.flag);
+        float wn = D.w ? __ldg(&D.w[n]) : 1.0f;
+        if (!isfinite(wn)) {
+            atomicOr(D.flag, QS_FLAG_NONFINITE);
+            wn = 0.0f;
+        }
+        const float ws = wn * scale;
+        int l0;
+        float tap[W];
+        qs_taps<W>(u, win, l0, tap);
+#pragma unroll
+        for (int j = 0; j < W; ++j) atomicAdd(&gridi[(l0 + j) & mask], __float2int_rn(ws * tap[j]));
+    }
+    __syncthreads();
+    const float inv_scale = s_scale[1];
+    for (int i = threadIdx.x; i < G; i += BT) grid[i] = (float)gridi[i] * inv_scale;
+    __syncthreads();
+    const int Gh = G >> 1;
+    const int log2n = 31 - __clz(Gh);
+    float2* z = reinterpret_cast<float2*>(grid);
+    fft_inplace<false>(z, Gh, log2n, D.tw, G);
+    real_filter<false>(z, Gh, D.D, D.tw);
+    __syncthreads();
+    fft_inplace<true>(z, Gh, log2n, D.tw, G);
+    float4* dst = reinterpret_cast<float4*>(D.H + (size_t)p * G);
+    const float4* src = reinterpret_cast<const float4*>(grid);
+    for (int i = threadIdx.x; i < (G >> 2); i += BT) dst[i] = src[i];
+}
+
+template <int W>
+__device__ void batch_interp(const BatchDesc& D, int64_t b, const qs_window& win, unsigned char* smem)
+{
+    const int d = D.d, G = D.G, mask = G - 1, tpt = D.tpt;
+    const int TB = BT * tpt;
+    const int64_t m0 = b * TB;
+    float* ytile = reinterpret_cast<float*>(smem);                  // [d][TB]
+    float* rows = reinterpret_cast<float*>(smem + YTILE_BYTES);     // 2 x (G + ROW_PAD)
+    const int stride = G + ROW_PAD;
+    const int64_t nload = (int64_t)TB * d;
+    for (int64_t i = threadIdx.x; i < nload; i += BT) {
+        const int t = (int)(i / d), j = (int)(i - (int64_t)t * d);
+        const int64_t m = m0 + t;
+        ytile[j * TB + t] = m < D.M ? __ldg(&D.y[(size_t)m * d + j]) : 0.0f;
+    }
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    const int P = D.P;
+    stage_row(rows, D.H, G);
+    for (int p = 0; p < P; ++p) {
+        const float* row = rows + (p & 1) * stride;
+        if (p + 1 < P) {
+            stage_row(rows + ((p + 1) & 1) * stride, D.H + (size_t)(p + 1) * G, G);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const float* xs = D.xi_s + (size_t)p * d;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (i >= tpt) break;
+            const int t = threadIdx.x + i * BT;
+            if (m0 + t >= D.M) continue;
+            float u = 0.0f;
+            for (int j = 0; j < d; ++j) u = fmaf(__ldg(&xs[j]), ytile[j * TB + t], u);
+            u = qs_check_u(u, D.half_G, D.flag);
+            int l0;
+            float tap[W];
+            qs_taps<W>(u, win, l0, tap);
+            const float* h = row + (l0 & mask);
+            float v = 0.0f;
+#pragma unroll
+            for (int j = 0; j < W; ++j) v = fmaf(h[j], tap[j], v);
+            qs_two_sum(hi[i], lo[i], v);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (i >= tpt) break;
+        const int64_t m = m0 + threadIdx.x + i * BT;
+        if (m < D.M) D.s[m] = (hi[i] + lo[i]) / (float)P;
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(BT, 2)
+    batched_kernel(const BatchDesc* __restrict__ descs, int nprob, int64_t n_spread, int64_t n_items,
+                   unsigned long long* __restrict__ counter, unsigned int* __restrict__ done, qs_window win,
+                   long long wait_cycles)
+{
+    extern __shared__ float4 smem4[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(smem4);
+    __shared__ long long s_item;
+    __shared__ int s_ok;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ULL);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= n_items) return;
+        if (item < n_spread) {
+            const int k = find_item(descs, nprob, item, false);
+            const BatchDesc D = descs[k];
+            batch_spread<W>(D, (int)(item - D.spread_begin), win, smem);
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(&done[k], 1u);
+        } else {
+            const int k = find_item(descs, nprob, item, true);
+            const BatchDesc D = descs[k];
+            if (threadIdx.x == 0) {
+                const long long t0 = clock64();
+                int ok = 1;
+                while (atomicAdd(&done[k], 0u) < (unsigned)D.P) {
+                    if (clock64() - t0 > wait_cycles) {
+                        ok = 0;
+                        atomicOr(D.flag, QS_FLAG_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+                __threadfence();
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (s_ok) batch_interp<W>(D, item - D.interp_begin, win, smem);
+        }
+        __syncthreads();
+    }
+}
+
+qs_status bfail(qs_status st, const char* fmt, ...)
+{
+    char msg[384];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof(msg), fmt, ap);
+    va_end(ap);
+    qs_set_error_message(msg);
+    return st;
+}
+
+}  // namespace
+
+struct qs_batch_s {
+    int device;
+    int sm_count;
+    int nprob;
+    int W;
+    int tpt_cap;            // largest targets-per-thread of interpolation items (1, 2 or 4)
+    qs_window win;
+    std::vector<qs_plan> plans;
+    BatchDesc* h_desc;      // pinned host staging of the descriptors
+    cudaEvent_t uploaded;   // recorded after each upload of h_desc
+    BatchDesc* d_desc;
+    unsigned long long* d_counter;
+    unsigned int* d_done;
+};
+
+extern "C" qs_status qs_batch_create(qs_batch* out, const qs_plan* plans, int nprob)
+{
+    if (!out || !plans || nprob < 1) return bfail(QS_ERR_ARG, "qs_batch_create: bad arguments");
+    *out = nullptr;
+    const int dev = plans[0] ? plans[0]->device : -1;
+    for (int k = 0; k < nprob; ++k) {
+        const qs_plan p = plans[k];
+        if (!p) return bfail(QS_ERR_ARG, "qs_batch_create: plan %d is NULL", k);
+        if (p->device != dev) return bfail(QS_ERR_ARG, "qs_batch_create: plans on different devices");
+        if (p->W != plans[0]->W) return bfail(QS_ERR_UNSUPPORTED, "qs_batch_create: plans must share the window width");
+        if (p->desc.d > QS_BATCH_MAX_D)
+            return bfail(QS_ERR_UNSUPPORTED, "qs_batch_create: d = %d exceeds %d", p->desc.d, QS_BATCH_MAX_D);
+        for (int j = 0; j < k; ++j)
+            if (plans[j] == p) return bfail(QS_ERR_ARG, "qs_batch_create: plan %d repeated (plans hold the grids)", k);
+    }
+    qs_batch b = new (std::nothrow) qs_batch_s;
+    if (!b) return bfail(QS_ERR_OOM, "qs_batch_create: host allocation");
+    b->device = dev;
+    b->sm_count = plans[0]->sm_count;
+    b->nprob = nprob;
+    b->W = plans[0]->W;
+    b->tpt_cap = 4;
+    b->win = plans[0]->win;
+    b->plans.assign(plans, plans + nprob);
+    b->h_desc = nullptr;
+    b->d_desc = nullptr;
+    b->d_counter = nullptr;
+    b->d_done = nullptr;
+    b->uploaded = nullptr;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(dev);
+    cudaError_t e = cudaMallocHost((void**)&b->h_desc, sizeof(BatchDesc) * nprob);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_desc, sizeof(BatchDesc) * nprob);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_done, sizeof(unsigned int) * nprob);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        qs_batch_destroy(b);
+        return bfail(QS_ERR_OOM, "qs_batch_create: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return QS_OK;
+}
+
+extern "C" qs_status qs_batch_destroy(qs_batch b)
+{
+    if (!b) return QS_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    if (b->h_desc) cudaFreeHost(b->h_desc);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_counter) cudaFree(b->d_counter);
+    if (b->d_done) cudaFree(b->d_done);
+    if (b->uploaded) cudaEventDestroy(b->uploaded);
+    cudaSetDevice(prev);
+    delete b;
+    return QS_OK;
+}
+
+extern "C" qs_status qs_batch_set_tiling(qs_batch b, int tpt_cap)
+{
+    if (!b || (tpt_cap != 1 && tpt_cap != 2 && tpt_cap != 4)) return bfail(QS_ERR_ARG, "qs_batch_set_tiling: bad value");
+    b->tpt_cap = tpt_cap;
+    return QS_OK;
+}
+
+extern "C" qs_status qs_sum_batched(qs_batch b, const qs_problem* probs, void* stream)
+{
+    if (!b || !probs) return bfail(QS_ERR_ARG, "qs_sum_batched: NULL argument");
+    const int n = b->nprob;
+    // queue order: largest problems first
+    std::vector<int> order(n);
+    for (int k = 0; k < n; ++k) {
+        const qs_problem& q = probs[k];
+        const qs_plan p = b->plans[k];
+        if (q.N < 0 || q.M < 0 || q.N > p->desc.max_n || q.M > p->desc.max_m)
+            return bfail(QS_ERR_ARG, "qs_sum_batched: problem %d sizes outside its plan's limits", k);
+        if ((q.N > 0 && !q.x) || (q.M > 0 && (!q.y || !q.s)))
+            return bfail(QS_ERR_ARG, "qs_sum_batched: problem %d has a NULL data pointer", k);
+        order[k] = k;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        const double wa = (double)(probs[a].N + probs[a].M) * b->plans[a]->desc.P;
+        const double wc = (double)(probs[c].N + probs[c].M) * b->plans[c]->desc.P;
+        return wa > wc;
+    });
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return bfail(QS_ERR_CUDA, "qs_sum_batched: stream query");
+    if (cap == cudaStreamCaptureStatusNone && cudaEventSynchronize(b->uploaded) != cudaSuccess)
+        return bfail(QS_ERR_CUDA, "qs_sum_batched: previous upload");
+    int64_t spread_items = 0, interp_items = 0;
+    int maxG = 32;
+    for (int i = 0; i < n; ++i) {
+        const int k = order[i];
+        const qs_problem& q = probs[k];
+        const qs_plan p = b->plans[k];
+        BatchDesc& D = b->h_desc[i];
+        D.x = q.x;
+        D.w = q.w;
+        D.y = q.y;
+        D.s = q.s;
+        D.N = q.N;
+        D.M = q.M;
+        D.d = p->desc.d;
+        D.P = p->desc.P;
+        D.G = p->G;
+        int tpt = YTILE_BYTES / (BT * 4 * D.d);
+        if (tpt > b->tpt_cap) tpt = b->tpt_cap;
+        if (tpt < 1) tpt = 1;
+        if (tpt == 3) tpt = 2;
+        D.tpt = tpt;
+        D.half_G = 0.5f * (float)p->G;
+        D.xi_s = p->d_dirs_s;
+        D.D = p->d_D;
+        D.tw = p->d_tw;
+        D.H = p->d_H;
+        D.flag = p->d_flag;
+        // an empty source set still needs zero grids; no targets needs nothing
+        D.spread_begin = spread_items;
+        spread_items += q.M > 0 ? D.P : 0;
+        D.interp_begin = interp_items;  // made absolute below
+        D.interp_blocks = q.M > 0 ? (q.M + (int64_t)BT * tpt - 1) / ((int64_t)BT * tpt) : 0;
+        interp_items += D.interp_blocks;
+        if (p->G > maxG) maxG = p->G;
+    }
+    for (int i = 0; i < n; ++i) b->h_desc[i].interp_begin += spread_items;
+    const int64_t n_items = spread_items + interp_items;
+    if (n_items == 0) return QS_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != b->device) cudaSetDevice(b->device);
+    cudaError_t e = cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(BatchDesc) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && cap == cudaStreamCaptureStatusNone) e = cudaEventRecord(b->uploaded, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_done, 0, sizeof(unsigned int) * n, st);
+    const size_t smem = (size_t)YTILE_BYTES + (size_t)2 * (maxG + ROW_PAD) * sizeof(float);
+    const long long wait_cycles = 4000000000LL;  // ~2 s at 2 GHz
+    const unsigned grid = (unsigned)(b->sm_count * 2);
+#define QS_BATCH_LAUNCH(WW)                                                                                   \
+    do {                                                                                                      \
+        if (e == cudaSuccess)                                                                                 \
+            e = cudaFuncSetAttribute(batched_kernel<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e == cudaSuccess) {                                                                               \
+            batched_kernel<WW><<<grid, BT, smem, st>>>(b->d_desc, n, spread_items, n_items, b->d_counter,   \
+                                                       b->d_done, b->win, wait_cycles);                      \
+            e = cudaGetLastError();                                                                           \
+        }                                                                                                     \
+    } while (0)
+    switch (b->W) {
+        case 6: QS_BATCH_LAUNCH(6); break;
+        case 8: QS_BATCH_LAUNCH(8); break;
+        case 10: QS_BATCH_LAUNCH(10); break;
+        case 12: QS_BATCH_LAUNCH(12); break;
+        default: e = cudaErrorInvalidValue;
+    }
+#undef QS_BATCH_LAUNCH
+    if (prev != b->device) cudaSetDevice(prev);
+    if (e != cudaSuccess) return bfail(QS_ERR_CUDA, "qs_sum_batched: %s", cudaGetErrorString(e));
+    return QS_OK;
+}
+
+extern "C" qs_status qs_batch_check(qs_batch b, void* stream)
+{
+    if (!b) return bfail(QS_ERR_ARG, "qs_batch_check: NULL batch");
+    qs_status worst = QS_OK;
+    for (int k = 0; k < b->nprob; ++k) {
+        const qs_status s = qs_check(b->plans[k], stream);
+        if (s != QS_OK && (worst == QS_OK || s == QS_ERR_CUDA || s == QS_ERR_TIMEOUT)) worst = s;
+    }
+    return worst;
+}

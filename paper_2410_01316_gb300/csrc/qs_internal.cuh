@@ -23,7 +23,9 @@ constexpr int QS_MAX_W = 12;
 constexpr int QS_MAX_HALF = QS_MAX_W / 2;
 constexpr int QS_MAX_TERMS = QS_MAX_HALF + 1;  // terms per even / odd part
 constexpr int QS_MAX_G = 16384;                // grid cells per slice (64 KB shared)
-constexpr int QS_FUSED_MAX_D = 32;             // largest d of the fused form
+constexpr int QS_FUSED_MAX_D = 64;             // largest d of the fused form
+constexpr int QS_GRAD_MAX_D = 32;              // largest d of the gradients
+constexpr int QS_BATCH_MAX_D = 64;             // largest d of a batched problem
 
 // Spread kernel variants (see spread_filter_kernel); chosen per plan by timing.
 enum {

@@ -9,7 +9,7 @@
 // plan, because plan creation allocates its workspace.
 //
 // What it does: the same sum as qs_sum with the fused FP32 projection
-// (d <= 32), but every intermediate -- the filter table, the twiddles, the
+// (d <= 64), but every intermediate -- the filter table, the twiddles, the
 // scaled directions, the per-slice filtered grids, the slice partial sums,
 // the weight scale and the error flag -- lives in one file-scope device
 // array of QS_NOALLOC_SCRATCH_BYTES (16 MiB).  Every GPU that loads the

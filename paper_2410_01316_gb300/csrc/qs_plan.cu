@@ -503,7 +503,7 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     // slice-group partials: sized for targets up to max(max_n, max_m), since the
     // gradients evaluate at x as well as at y
     QS_ALLOC(p->d_part, (size_t)2 * p->S_max * (maxnm > 0 ? maxnm : 1));
-    if (d <= QS_FUSED_MAX_D) {
+    if (d <= QS_GRAD_MAX_D) {
         // largest S(M) * M over M <= max(max_n, max_m), S as in make_launch
         size_t sm = 1;
         for (int64_t b = 1; b <= (maxnm + 255) / 256; ++b) {
@@ -732,7 +732,7 @@ qs_status qs_grad(qs_plan p, const float* x, int64_t N, const float* w, const fl
     if ((N > 0 && !x) || (M > 0 && !y)) return fail(QS_ERR_ARG, "qs_grad: NULL point array");
     if (!gx && !gw && !gy) return QS_OK;
     if (!p->d_gpart)
-        return fail(QS_ERR_UNSUPPORTED, "qs_grad: gradients need d <= %d (the plan has d = %d)", QS_FUSED_MAX_D,
+        return fail(QS_ERR_UNSUPPORTED, "qs_grad: gradients need d <= %d (the plan has d = %d)", QS_GRAD_MAX_D,
                     p->desc.d);
     DeviceGuard g(p->device);
     cudaStream_t st = (cudaStream_t)stream;
