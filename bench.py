@@ -369,7 +369,7 @@ def run_mmd_flow(args, rank, world, local_rank):
     N, M, d, P, n_ft = x.shape[0], y0.shape[0], st["d"], st["P"], st["n_ft"]
     xi = W.make_directions("orthogonal", P, d, st["seed"] + 11)
     R = 1.25 * 2 * float(max(x.norm(dim=1).max(), y0.norm(dim=1).max()))
-    plan = QSPlan(d, "negdist", P, n_ft, R, dirs=xi, proj="fp32_fused", max_n=N + M, max_m=N + M)
+    plan = QSPlan(d, "negdist", P, n_ft, R, dirs=xi, proj="fp32", max_n=N + M, max_m=N + M)
     z = torch.cat([y0, x]).contiguous()          # sources; z[:M] are the moving particles
     y = z[:M]
     wz = torch.cat([torch.full((M,), 1.0 / (M * M)), torch.full((N,), -1.0 / (M * N))]).float().to(dev)

@@ -72,7 +72,7 @@ typedef enum {
 
 /* Precision / form of the projection step a = tau X Xi^T. */
 typedef enum {
-    QS_PROJ_AUTO = 0,       /* library choice */
+    QS_PROJ_AUTO = 0,       /* fused for d <= 4, FP32 for d < 64, BF16x3 from d = 64 */
     QS_PROJ_FP32 = 1,       /* FP32 SIMT GEMM into a P x N workspace */
     QS_PROJ_FP32_FUSED = 2, /* FP32 dot products inside spread / interpolation (d <= 64) */
     QS_PROJ_BF16X3 = 3,     /* tensor-core GEMM, x = hi + lo split in BF16, three products */

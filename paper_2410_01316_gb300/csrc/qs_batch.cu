@@ -2,22 +2,28 @@
 // N_ft, kernel, directions) of uneven N and M in one persistent launch.
 //
 // Work items, dequeued in order from one 64-bit counter:
-//   [0, n_spread)        (problem k, slice p): spread + FFT filter of slice p,
+//   projection items     (problem k, x or y, 128-slice x 128-point tile): the
+//                        FP32 SIMT projection tile U = G tau Xi X^T into the
+//                        batch's per-problem projection buffers
+//   spread items         (problem k, slice p): spread + FFT filter of slice p,
 //                        writing the problem's filtered grid row H_k[p]
-//   [n_spread, n_items)  (problem k, target block b): interpolation of a block
+//   interpolation items  (problem k, target block b): interpolation of a block
 //                        of targets over all P_k slices, writing s directly
-// Problems are queued largest first.  A target-block item waits until all
-// P_k spread items of its problem have published their rows (a per-problem
-// counter, incremented after a fence).  Those items were dequeued earlier,
-// so they are held by running CTAs and will finish: the wait cannot
-// deadlock, whatever the grid size.  The wait is bounded by a clock budget;
-// on expiry the item sets the problem's timeout flag and is skipped.
-// Rows written in this launch are read back through L2 only (cp.async.cg).
+// Problems are queued largest first within each phase.  A spread item waits
+// for its problem's x-projection tiles; an interpolation item waits for all
+// P_k spread items and the y-projection tiles of its problem (per-problem
+// counters, incremented after a fence).  Every awaited item was dequeued
+// earlier, so it is held by a running CTA and will finish: no wait can
+// deadlock, whatever the grid size.  Waits are bounded by a clock budget; on
+// expiry the item sets the problem's timeout flag and is skipped.  Data
+// written in this launch is read back through L2 only (ld.global.cg /
+// cp.async.cg).
 //
-// Projections are computed in FP32 inside the items (the fused form), for
-// any d <= QS_BATCH_MAX_D.  Each target's slice sum runs in slice order with
-// TwoSum in one thread, so the result does not depend on the tiling chosen
-// by the tuner.
+// Problems with d <= 4 skip the projection items and form their dot products
+// inside the spread and interpolation items (the fused form is cheaper when
+// a point has so few coordinates).  Each target's slice sum runs in slice
+// order with TwoSum in one thread, so the result does not depend on the
+// tiling chosen by the tuner.
 #include <cuda_runtime.h>
 
 #include <math.h>
@@ -37,7 +43,9 @@ using namespace qsdev;
 namespace {
 
 constexpr int BT = 256;                  // threads per CTA
-constexpr int YTILE_BYTES = 64 * 1024;   // shared tile of target coordinates
+constexpr int FUSED_MAX_D = 4;           // problems with d <= 4 use fused projections
+constexpr int YTILE_BYTES = BT * 4 * FUSED_MAX_D * 4;  // coordinate tile of a fused block
+constexpr int GEMM_SMEM = 4 * GT_BK * GT_BM * 4;       // 16 KB
 
 struct BatchDesc {
     const float* x;
@@ -46,25 +54,48 @@ struct BatchDesc {
     float* s;
     int64_t N, M;
     int d, P, G, tpt;
+    int fused, vecx, vecy;
     float half_G;
     const float* xi_s;
     const float* D;
     const float2* tw;
     float* H;
+    float* Ux;            // P x ldUx projections of x (unfused problems)
+    float* Uy;            // P x ldUy projections of y
+    int64_t ldUx, ldUy;
+    int ptiles;           // ceil(P / 128)
+    int64_t nxt, nyt;     // projection tiles of x and y
     unsigned int* flag;
-    int64_t spread_begin, interp_begin, interp_blocks;
+    int64_t proj_begin, spread_begin, interp_begin, interp_blocks;
 };
 
-__device__ int find_item(const BatchDesc* __restrict__ descs, int nprob, int64_t item, bool interp)
+// last problem k whose phase-`ph` range begins at or before `item`
+// (ph: 0 projection, 1 spread, 2 interpolation)
+__device__ int find_item(const BatchDesc* __restrict__ descs, int nprob, int64_t item, int ph)
 {
     int lo = 0, hi = nprob - 1;
-    while (lo < hi) {  // last k with begin_k <= item
+    while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        const int64_t b = interp ? descs[mid].interp_begin : descs[mid].spread_begin;
+        const int64_t b = ph == 0 ? descs[mid].proj_begin : (ph == 1 ? descs[mid].spread_begin : descs[mid].interp_begin);
         if (b <= item) lo = mid;
         else hi = mid - 1;
     }
     return lo;
+}
+
+// Spin (thread 0) until *ctr >= target or the clock budget is spent.
+__device__ bool wait_count(unsigned int* ctr, unsigned int target, long long budget, unsigned int* flag)
+{
+    const long long t0 = clock64();
+    while (atomicAdd(ctr, 0u) < target) {
+        if (clock64() - t0 > budget) {
+            atomicOr(flag, QS_FLAG_TIMEOUT);
+            return false;
+        }
+        __nanosleep(256);
+    }
+    __threadfence();
+    return true;
 }
 
 template <int W>
@@ -103,10 +134,16 @@ __device__ void batch_spread(const BatchDesc& D, int p, const qs_window& win, un
     }
     __syncthreads();
     const float scale = s_scale[0];
+    const float* urow = D.Ux + (size_t)p * D.ldUx;
     for (int64_t n = threadIdx.x; n < D.N; n += BT) {
-        const float* xn = D.x + (size_t)n * d;
-        float u = 0.0f;
-        for (int j = 0; j < d; ++j) u = fmaf(xi_sm[j], __ldg(&xn[j]), u);
+        float u;
+        if (D.fused) {
+            const float* xn = D.x + (size_t)n * d;
+            u = 0.0f;
+            for (int j = 0; j < d; ++j) u = fmaf(xi_sm[j], __ldg(&xn[j]), u);
+        } else {
+            u = __ldcg(&urow[n]);  // written by projection items of this launch
+        }
         u = qs_check_u(u, D.half_G, D.flag);
         float wn = D.w ? __ldg(&D.w[n]) : 1.0f;
         if (!isfinite(wn)) {
@@ -145,11 +182,13 @@ __device__ void batch_interp(const BatchDesc& D, int64_t b, const qs_window& win
     float* ytile = reinterpret_cast<float*>(smem);                  // [d][TB]
     float* rows = reinterpret_cast<float*>(smem + YTILE_BYTES);     // 2 x (G + ROW_PAD)
     const int stride = G + ROW_PAD;
-    const int64_t nload = (int64_t)TB * d;
-    for (int64_t i = threadIdx.x; i < nload; i += BT) {
-        const int t = (int)(i / d), j = (int)(i - (int64_t)t * d);
-        const int64_t m = m0 + t;
-        ytile[j * TB + t] = m < D.M ? __ldg(&D.y[(size_t)m * d + j]) : 0.0f;
+    if (D.fused) {
+        const int64_t nload = (int64_t)TB * d;
+        for (int64_t i = threadIdx.x; i < nload; i += BT) {
+            const int t = (int)(i / d), j = (int)(i - (int64_t)t * d);
+            const int64_t m = m0 + t;
+            ytile[j * TB + t] = m < D.M ? __ldg(&D.y[(size_t)m * d + j]) : 0.0f;
+        }
     }
     float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
     const int P = D.P;
@@ -169,8 +208,13 @@ __device__ void batch_interp(const BatchDesc& D, int64_t b, const qs_window& win
             if (i >= tpt) break;
             const int t = threadIdx.x + i * BT;
             if (m0 + t >= D.M) continue;
-            float u = 0.0f;
-            for (int j = 0; j < d; ++j) u = fmaf(__ldg(&xs[j]), ytile[j * TB + t], u);
+            float u;
+            if (D.fused) {
+                u = 0.0f;
+                for (int j = 0; j < d; ++j) u = fmaf(__ldg(&xs[j]), ytile[j * TB + t], u);
+            } else {
+                u = __ldcg(&D.Uy[(size_t)p * D.ldUy + m0 + t]);
+            }
             u = qs_check_u(u, D.half_G, D.flag);
             int l0;
             float tap[W];
@@ -193,10 +237,11 @@ __device__ void batch_interp(const BatchDesc& D, int64_t b, const qs_window& win
 
 template <int W>
 __global__ void __launch_bounds__(BT, 2)
-    batched_kernel(const BatchDesc* __restrict__ descs, int nprob, int64_t n_spread, int64_t n_items,
+    batched_kernel(const BatchDesc* __restrict__ descs, int nprob, int64_t n_proj, int64_t n_spread, int64_t n_items,
                    unsigned long long* __restrict__ counter, unsigned int* __restrict__ done, qs_window win,
                    long long wait_cycles)
 {
+    // done[0..n): spread rows published, [n..2n): x tiles, [2n..3n): y tiles
     extern __shared__ float4 smem4[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(smem4);
     __shared__ long long s_item;
@@ -206,29 +251,42 @@ __global__ void __launch_bounds__(BT, 2)
         __syncthreads();
         const int64_t item = s_item;
         if (item >= n_items) return;
-        if (item < n_spread) {
-            const int k = find_item(descs, nprob, item, false);
+        if (item < n_proj) {
+            const int k = find_item(descs, nprob, item, 0);
             const BatchDesc D = descs[k];
-            batch_spread<W>(D, (int)(item - D.spread_begin), win, smem);
+            int64_t j = item - D.proj_begin;
+            const bool isx = j < D.nxt;
+            if (!isx) j -= D.nxt;
+            const int p0 = (int)(j % D.ptiles) * GT_BM;
+            const int64_t n0 = (j / D.ptiles) * GT_BN;
+            float* sm = reinterpret_cast<float*>(smem);
+            if (isx) {
+                if (D.vecx) gemm_tile_fp32<true>(D.x, D.N, D.d, D.xi_s, D.P, D.Ux, D.ldUx, p0, n0, sm);
+                else gemm_tile_fp32<false>(D.x, D.N, D.d, D.xi_s, D.P, D.Ux, D.ldUx, p0, n0, sm);
+            } else {
+                if (D.vecy) gemm_tile_fp32<true>(D.y, D.M, D.d, D.xi_s, D.P, D.Uy, D.ldUy, p0, n0, sm);
+                else gemm_tile_fp32<false>(D.y, D.M, D.d, D.xi_s, D.P, D.Uy, D.ldUy, p0, n0, sm);
+            }
             __threadfence();
             __syncthreads();
-            if (threadIdx.x == 0) atomicAdd(&done[k], 1u);
+            if (threadIdx.x == 0) atomicAdd(&done[(isx ? 1 : 2) * nprob + k], 1u);
+        } else if (item < n_spread) {
+            const int k = find_item(descs, nprob, item, 1);
+            const BatchDesc D = descs[k];
+            if (threadIdx.x == 0) s_ok = wait_count(&done[nprob + k], (unsigned)D.nxt, wait_cycles, D.flag);
+            __syncthreads();
+            if (s_ok) {
+                batch_spread<W>(D, (int)(item - D.spread_begin), win, smem);
+                __threadfence();
+                __syncthreads();
+                if (threadIdx.x == 0) atomicAdd(&done[k], 1u);
+            }
         } else {
-            const int k = find_item(descs, nprob, item, true);
+            const int k = find_item(descs, nprob, item, 2);
             const BatchDesc D = descs[k];
             if (threadIdx.x == 0) {
-                const long long t0 = clock64();
-                int ok = 1;
-                while (atomicAdd(&done[k], 0u) < (unsigned)D.P) {
-                    if (clock64() - t0 > wait_cycles) {
-                        ok = 0;
-                        atomicOr(D.flag, QS_FLAG_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(256);
-                }
-                __threadfence();
-                s_ok = ok;
+                s_ok = wait_count(&done[k], (unsigned)D.P, wait_cycles, D.flag) &&
+                       wait_count(&done[2 * nprob + k], (unsigned)D.nyt, wait_cycles, D.flag);
             }
             __syncthreads();
             if (s_ok) batch_interp<W>(D, item - D.interp_begin, win, smem);
@@ -258,12 +316,16 @@ struct qs_batch_s {
     int tpt_cap;            // largest targets-per-thread of interpolation items (1, 2 or 4)
     qs_window win;
     std::vector<qs_plan> plans;
+    std::vector<float*> Ux, Uy;     // per-problem projection buffers (d > 4)
+    std::vector<int64_t> ldUx, ldUy;
     BatchDesc* h_desc;      // pinned host staging of the descriptors
     cudaEvent_t uploaded;   // recorded after each upload of h_desc
     BatchDesc* d_desc;
     unsigned long long* d_counter;
-    unsigned int* d_done;
+    unsigned int* d_done;   // 3 counters per problem
 };
+
+extern "C" qs_status qs_batch_destroy(qs_batch b);
 
 extern "C" qs_status qs_batch_create(qs_batch* out, const qs_plan* plans, int nprob)
 {
@@ -289,21 +351,34 @@ extern "C" qs_status qs_batch_create(qs_batch* out, const qs_plan* plans, int np
     b->tpt_cap = 4;
     b->win = plans[0]->win;
     b->plans.assign(plans, plans + nprob);
+    b->Ux.assign(nprob, nullptr);
+    b->Uy.assign(nprob, nullptr);
+    b->ldUx.assign(nprob, 0);
+    b->ldUy.assign(nprob, 0);
     b->h_desc = nullptr;
+    b->uploaded = nullptr;
     b->d_desc = nullptr;
     b->d_counter = nullptr;
     b->d_done = nullptr;
-    b->uploaded = nullptr;
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(dev);
     cudaError_t e = cudaMallocHost((void**)&b->h_desc, sizeof(BatchDesc) * nprob);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_desc, sizeof(BatchDesc) * nprob);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_done, sizeof(unsigned int) * nprob);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_done, sizeof(unsigned int) * 3 * nprob);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming);
+    for (int k = 0; k < nprob && e == cudaSuccess; ++k) {
+        const qs_plan p = plans[k];
+        if (p->desc.d <= FUSED_MAX_D) continue;
+        b->ldUx[k] = ((p->desc.max_n > 0 ? p->desc.max_n : 1) + 127) / 128 * 128;
+        b->ldUy[k] = ((p->desc.max_m > 0 ? p->desc.max_m : 1) + 127) / 128 * 128;
+        e = cudaMalloc((void**)&b->Ux[k], sizeof(float) * (size_t)p->desc.P * b->ldUx[k]);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&b->Uy[k], sizeof(float) * (size_t)p->desc.P * b->ldUy[k]);
+    }
     cudaSetDevice(prev);
     if (e != cudaSuccess) {
+        cudaGetLastError();
         qs_batch_destroy(b);
         return bfail(QS_ERR_OOM, "qs_batch_create: %s", cudaGetErrorString(e));
     }
@@ -323,6 +398,10 @@ extern "C" qs_status qs_batch_destroy(qs_batch b)
     if (b->d_counter) cudaFree(b->d_counter);
     if (b->d_done) cudaFree(b->d_done);
     if (b->uploaded) cudaEventDestroy(b->uploaded);
+    for (float* u : b->Ux)
+        if (u) cudaFree(u);
+    for (float* u : b->Uy)
+        if (u) cudaFree(u);
     cudaSetDevice(prev);
     delete b;
     return QS_OK;
@@ -335,11 +414,12 @@ extern "C" qs_status qs_batch_set_tiling(qs_batch b, int tpt_cap)
     return QS_OK;
 }
 
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 extern "C" qs_status qs_sum_batched(qs_batch b, const qs_problem* probs, void* stream)
 {
     if (!b || !probs) return bfail(QS_ERR_ARG, "qs_sum_batched: NULL argument");
     const int n = b->nprob;
-    // queue order: largest problems first
     std::vector<int> order(n);
     for (int k = 0; k < n; ++k) {
         const qs_problem& q = probs[k];
@@ -350,6 +430,7 @@ extern "C" qs_status qs_sum_batched(qs_batch b, const qs_problem* probs, void* s
             return bfail(QS_ERR_ARG, "qs_sum_batched: problem %d has a NULL data pointer", k);
         order[k] = k;
     }
+    // queue order: largest problems first
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
         const double wa = (double)(probs[a].N + probs[a].M) * b->plans[a]->desc.P;
         const double wc = (double)(probs[c].N + probs[c].M) * b->plans[c]->desc.P;
@@ -360,7 +441,7 @@ extern "C" qs_status qs_sum_batched(qs_batch b, const qs_problem* probs, void* s
     if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return bfail(QS_ERR_CUDA, "qs_sum_batched: stream query");
     if (cap == cudaStreamCaptureStatusNone && cudaEventSynchronize(b->uploaded) != cudaSuccess)
         return bfail(QS_ERR_CUDA, "qs_sum_batched: previous upload");
-    int64_t spread_items = 0, interp_items = 0;
+    int64_t proj_items = 0, spread_items = 0, interp_items = 0;
     int maxG = 32;
     for (int i = 0; i < n; ++i) {
         const int k = order[i];
@@ -376,27 +457,40 @@ extern "C" qs_status qs_sum_batched(qs_batch b, const qs_problem* probs, void* s
         D.d = p->desc.d;
         D.P = p->desc.P;
         D.G = p->G;
-        int tpt = YTILE_BYTES / (BT * 4 * D.d);
-        if (tpt > b->tpt_cap) tpt = b->tpt_cap;
-        if (tpt < 1) tpt = 1;
-        if (tpt == 3) tpt = 2;
-        D.tpt = tpt;
+        D.fused = D.d <= FUSED_MAX_D ? 1 : 0;
+        D.vecx = (D.d % 4 == 0) && aligned16(q.x) && aligned16(p->d_dirs_s);
+        D.vecy = (D.d % 4 == 0) && aligned16(q.y) && aligned16(p->d_dirs_s);
+        D.tpt = b->tpt_cap;
         D.half_G = 0.5f * (float)p->G;
         D.xi_s = p->d_dirs_s;
         D.D = p->d_D;
         D.tw = p->d_tw;
         D.H = p->d_H;
+        D.Ux = b->Ux[k];
+        D.Uy = b->Uy[k];
+        D.ldUx = b->ldUx[k];
+        D.ldUy = b->ldUy[k];
+        D.ptiles = (D.P + GT_BM - 1) / GT_BM;
+        D.nxt = D.fused ? 0 : (int64_t)D.ptiles * ((q.N + GT_BN - 1) / GT_BN);
+        D.nyt = D.fused ? 0 : (int64_t)D.ptiles * ((q.M + GT_BN - 1) / GT_BN);
+        if (q.M == 0) D.nxt = D.nyt = 0;  // nothing to compute for this problem
         D.flag = p->d_flag;
-        // an empty source set still needs zero grids; no targets needs nothing
-        D.spread_begin = spread_items;
+        D.proj_begin = proj_items;
+        proj_items += D.nxt + D.nyt;
+        D.spread_begin = spread_items;  // made absolute below
         spread_items += q.M > 0 ? D.P : 0;
-        D.interp_begin = interp_items;  // made absolute below
-        D.interp_blocks = q.M > 0 ? (q.M + (int64_t)BT * tpt - 1) / ((int64_t)BT * tpt) : 0;
+        D.interp_begin = interp_items;
+        D.interp_blocks = q.M > 0 ? (q.M + (int64_t)BT * D.tpt - 1) / ((int64_t)BT * D.tpt) : 0;
         interp_items += D.interp_blocks;
         if (p->G > maxG) maxG = p->G;
     }
-    for (int i = 0; i < n; ++i) b->h_desc[i].interp_begin += spread_items;
-    const int64_t n_items = spread_items + interp_items;
+    for (int i = 0; i < n; ++i) {
+        b->h_desc[i].spread_begin += proj_items;
+        b->h_desc[i].interp_begin += proj_items + spread_items;
+    }
+    const int64_t n_proj = proj_items;
+    const int64_t n_spread_end = proj_items + spread_items;
+    const int64_t n_items = n_spread_end + interp_items;
     if (n_items == 0) return QS_OK;
     int prev = 0;
     cudaGetDevice(&prev);
@@ -404,8 +498,12 @@ extern "C" qs_status qs_sum_batched(qs_batch b, const qs_problem* probs, void* s
     cudaError_t e = cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(BatchDesc) * n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && cap == cudaStreamCaptureStatusNone) e = cudaEventRecord(b->uploaded, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_done, 0, sizeof(unsigned int) * n, st);
-    const size_t smem = (size_t)YTILE_BYTES + (size_t)2 * (maxG + ROW_PAD) * sizeof(float);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_done, 0, sizeof(unsigned int) * 3 * n, st);
+    // shared memory: the union of a projection tile, a spread grid, and an
+    // interpolation block (fused coordinate tile + two staged rows)
+    size_t smem = (size_t)YTILE_BYTES + (size_t)2 * (maxG + ROW_PAD) * sizeof(float);
+    if ((size_t)maxG * 4 > smem) smem = (size_t)maxG * 4;
+    if ((size_t)GEMM_SMEM > smem) smem = GEMM_SMEM;
     const long long wait_cycles = 4000000000LL;  // ~2 s at 2 GHz
     const unsigned grid = (unsigned)(b->sm_count * 2);
 #define QS_BATCH_LAUNCH(WW)                                                                                   \
@@ -413,7 +511,7 @@ extern "C" qs_status qs_sum_batched(qs_batch b, const qs_problem* probs, void* s
         if (e == cudaSuccess)                                                                                 \
             e = cudaFuncSetAttribute(batched_kernel<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e == cudaSuccess) {                                                                               \
-            batched_kernel<WW><<<grid, BT, smem, st>>>(b->d_desc, n, spread_items, n_items, b->d_counter,   \
+            batched_kernel<WW><<<grid, BT, smem, st>>>(b->d_desc, n, n_proj, n_spread_end, n_items, b->d_counter, \
                                                        b->d_done, b->win, wait_cycles);                      \
             e = cudaGetLastError();                                                                           \
         }                                                                                                     \

@@ -128,4 +128,104 @@ __device__ __forceinline__ void stage_row(float* dst, const float* src, int G)
 }
 
 
+// ---------------------------------------------------------------------------
+// One 128-slice x 128-point tile of the FP32 projection GEMM
+//     U[p][n] = sum_j A[p][j] X[n][j]   (A = G tau Xi, X points, both K-major)
+// by a CTA of 256 threads: 8-deep k slabs double-buffered in shared memory
+// (`smem`: 2 x 8 x 256 floats = 16 KB), 8 x 8 outputs per thread.  Rows
+// p >= P are not stored; columns n0..n0+127 are stored (U needs ldU >=
+// round_up(N, 128)).
+// ---------------------------------------------------------------------------
+constexpr int GT_BM = 128;
+constexpr int GT_BN = 128;
+constexpr int GT_BK = 8;
+
+template <bool VEC>
+__device__ __forceinline__ void gemm_load_slab(const float* __restrict__ A, int P, const float* __restrict__ X,
+                                               int64_t N, int d, int p0, int64_t n0, int k0, int lrow, int lk,
+                                               float (&ra)[4], float (&rb)[4])
+{
+    const int gp = p0 + lrow;
+    const int64_t gn = n0 + lrow;
+    const int kk = k0 + lk;
+    if (VEC && kk + 3 < d) {
+        float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va;
+        if (gp < P) va = __ldg(reinterpret_cast<const float4*>(A + (size_t)gp * d + kk));
+        if (gn < N) vb = __ldg(reinterpret_cast<const float4*>(X + (size_t)gn * d + kk));
+        ra[0] = va.x; ra[1] = va.y; ra[2] = va.z; ra[3] = va.w;
+        rb[0] = vb.x; rb[1] = vb.y; rb[2] = vb.z; rb[3] = vb.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            ra[i] = (gp < P && kk + i < d) ? __ldg(A + (size_t)gp * d + kk + i) : 0.0f;
+            rb[i] = (gn < N && kk + i < d) ? __ldg(X + (size_t)gn * d + kk + i) : 0.0f;
+        }
+    }
+}
+
+template <bool VEC>
+__device__ inline void gemm_tile_fp32(const float* __restrict__ X, int64_t N, int d, const float* __restrict__ A,
+                                      int P, float* __restrict__ U, int64_t ldU, int p0, int64_t n0, float* smem)
+{
+    float(*As)[GT_BK][GT_BM] = reinterpret_cast<float(*)[GT_BK][GT_BM]>(smem);
+    float(*Bs)[GT_BK][GT_BN] = reinterpret_cast<float(*)[GT_BK][GT_BN]>(smem + 2 * GT_BK * GT_BM);
+    const int tid = threadIdx.x;
+    const int tx = tid & 15;
+    const int ty = tid >> 4;
+    const int lrow = tid >> 1;
+    const int lk = (tid & 1) * 4;
+
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+
+    float ra[4], rb[4];
+    const int nk = (d + GT_BK - 1) / GT_BK;
+    gemm_load_slab<VEC>(A, P, X, N, d, p0, n0, 0, lrow, lk, ra, rb);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        As[0][lk + i][lrow] = ra[i];
+        Bs[0][lk + i][lrow] = rb[i];
+    }
+    __syncthreads();
+
+    for (int kt = 0; kt < nk; ++kt) {
+        const int cur = kt & 1;
+        if (kt + 1 < nk) gemm_load_slab<VEC>(A, P, X, N, d, p0, n0, (kt + 1) * GT_BK, lrow, lk, ra, rb);
+#pragma unroll
+        for (int k = 0; k < GT_BK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][k][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][k][64 + tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (kt + 1 < nk) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                As[cur ^ 1][lk + i][lrow] = ra[i];
+                Bs[cur ^ 1][lk + i][lrow] = rb[i];
+            }
+        }
+        __syncthreads();
+    }
+
+    // rows: p0 + ty*4 + i (i < 4) and p0 + 64 + ty*4 + (i - 4); columns likewise
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int p = p0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+        if (p >= P) continue;
+        float* row = U + (size_t)p * ldU + n0;
+        *reinterpret_cast<float4*>(row + tx * 4) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        *reinterpret_cast<float4*>(row + 64 + tx * 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    }
+}
+
 }  // namespace qsdev

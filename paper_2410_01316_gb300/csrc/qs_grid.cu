@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) spread_filter_kernel(qs_launch L, const f
 // MODE 1: H2 <- derivative filter (table Dd).  MODE 2: L.H <- plain filter
 // (table L.D) and H2 <- derivative filter from the same spread grid.
 // ---------------------------------------------------------------------------
-template <int W, int MODE>
+template <int W, int MODE, bool FUSED>
 __global__ void __launch_bounds__(256) spread_grad_kernel(qs_launch L, const float* __restrict__ x,
                                                           const float* __restrict__ w, const float* __restrict__ Dd,
                                                           float* __restrict__ H2)
@@ -218,14 +218,21 @@ __global__ void __launch_bounds__(256) spread_grad_kernel(qs_launch L, const flo
     const int G = L.G;
     const int mask = G - 1;
     for (int i = threadIdx.x; i < G; i += blockDim.x) gridi[i] = 0;
-    for (int j = threadIdx.x; j < L.d; j += blockDim.x) xi_sm[j] = L.xi_s[(size_t)p * L.d + j];
+    if (FUSED)
+        for (int j = threadIdx.x; j < L.d; j += blockDim.x) xi_sm[j] = L.xi_s[(size_t)p * L.d + j];
     const float scale = __ldg(&L.wscale[0]);
     const float inv_scale = __ldg(&L.wscale[1]);
+    const float* urow = L.U + (size_t)p * L.ldU;
     __syncthreads();
     for (int64_t n = threadIdx.x; n < L.N; n += blockDim.x) {
-        const float* xn = x + (size_t)n * L.d;
-        float u = 0.0f;
-        for (int j = 0; j < L.d; ++j) u = fmaf(xi_sm[j], __ldg(&xn[j]), u);
+        float u;
+        if (FUSED) {
+            const float* xn = x + (size_t)n * L.d;
+            u = 0.0f;
+            for (int j = 0; j < L.d; ++j) u = fmaf(xi_sm[j], __ldg(&xn[j]), u);
+        } else {
+            u = __ldg(&urow[n]);
+        }
         u = qs_check_u(u, L.half_G, L.flag);
         float wn = w ? __ldg(&w[n]) : 1.0f;
         if (!isfinite(wn)) {
@@ -275,7 +282,7 @@ __global__ void __launch_bounds__(256) spread_grad_kernel(qs_launch L, const flo
 //   q_{m,p} = sum_l h'_p[l] psi(u_{m,p} - l),  acc_m += q_{m,p} xi_p
 // per slice group, compensated per component.  part: [2][S][M][d].
 // ---------------------------------------------------------------------------
-template <int W, int DMAX>
+template <int W, int DMAX, bool FUSED>
 __global__ void __launch_bounds__(256) interp_grad_kernel(qs_launch L, const float* __restrict__ y,
                                                           const float* __restrict__ Hd, const float* __restrict__ xi,
                                                           float* __restrict__ part)
@@ -287,20 +294,25 @@ __global__ void __launch_bounds__(256) interp_grad_kernel(qs_launch L, const flo
     const int d = L.d;
     const int p0 = (int)(((int64_t)g * L.P) / S);
     const int p1 = (int)(((int64_t)(g + 1) * L.P) / S);
-    float yr[DMAX], hi[DMAX], lo[DMAX];
+    float yr[FUSED ? DMAX : 1], hi[DMAX], lo[DMAX];
 #pragma unroll
     for (int j = 0; j < DMAX; ++j) {
-        yr[j] = j < d ? __ldg(&y[(size_t)m * d + j]) : 0.0f;
+        if (FUSED) yr[j] = j < d ? __ldg(&y[(size_t)m * d + j]) : 0.0f;
         hi[j] = 0.0f;
         lo[j] = 0.0f;
     }
     const int mask = L.G - 1;
     for (int p = p0; p < p1; ++p) {
-        const float* xs = L.xi_s + (size_t)p * d;
-        float u = 0.0f;
+        float u;
+        if (FUSED) {
+            const float* xs = L.xi_s + (size_t)p * d;
+            u = 0.0f;
 #pragma unroll
-        for (int j = 0; j < DMAX; ++j)
-            if (j < d) u = fmaf(__ldg(&xs[j]), yr[j], u);
+            for (int j = 0; j < DMAX; ++j)
+                if (j < d) u = fmaf(__ldg(&xs[j]), yr[j], u);
+        } else {
+            u = __ldg(&L.U[(size_t)p * L.ldU + m]);
+        }
         u = qs_check_u(u, L.half_G, L.flag);
         int l0;
         float tap[W];
@@ -511,11 +523,12 @@ cudaError_t launch_interp_w(const qs_launch& L, const float* y, bool fused, cuda
 }
 
 template <int W>
-cudaError_t launch_spread_grad_w(const qs_launch& L, const float* x, const float* w, int mode, const float* Dd,
-                                 float* H2, cudaStream_t st)
+cudaError_t launch_spread_grad_w(const qs_launch& L, const float* x, const float* w, int mode, bool fused,
+                                 const float* Dd, float* H2, cudaStream_t st)
 {
     const size_t smem = (size_t)L.G * sizeof(float) * (mode == 2 ? 2 : 1);
-    auto kern = mode == 2 ? spread_grad_kernel<W, 2> : spread_grad_kernel<W, 1>;
+    auto kern = mode == 2 ? (fused ? spread_grad_kernel<W, 2, true> : spread_grad_kernel<W, 2, false>)
+                          : (fused ? spread_grad_kernel<W, 1, true> : spread_grad_kernel<W, 1, false>);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -524,20 +537,28 @@ cudaError_t launch_spread_grad_w(const qs_launch& L, const float* x, const float
     return cudaGetLastError();
 }
 
-template <int W>
-cudaError_t launch_interp_grad_w(const qs_launch& L, const float* y, const float* Hd, const float* xi, float* part,
-                                 cudaStream_t st)
+template <int W, bool FUSED>
+void launch_interp_grad_f(const qs_launch& L, const float* y, const float* Hd, const float* xi, float* part,
+                          cudaStream_t st)
 {
     dim3 grid((unsigned)((L.M + 255) / 256), (unsigned)L.S);
-    if (L.d > QS_GRAD_MAX_D) return cudaErrorInvalidValue;
     if (L.d <= 4)
-        interp_grad_kernel<W, 4><<<grid, 256, 0, st>>>(L, y, Hd, xi, part);
+        interp_grad_kernel<W, 4, FUSED><<<grid, 256, 0, st>>>(L, y, Hd, xi, part);
     else if (L.d <= 8)
-        interp_grad_kernel<W, 8><<<grid, 256, 0, st>>>(L, y, Hd, xi, part);
+        interp_grad_kernel<W, 8, FUSED><<<grid, 256, 0, st>>>(L, y, Hd, xi, part);
     else if (L.d <= 16)
-        interp_grad_kernel<W, 16><<<grid, 256, 0, st>>>(L, y, Hd, xi, part);
+        interp_grad_kernel<W, 16, FUSED><<<grid, 256, 0, st>>>(L, y, Hd, xi, part);
     else
-        interp_grad_kernel<W, 32><<<grid, 256, 0, st>>>(L, y, Hd, xi, part);
+        interp_grad_kernel<W, 32, FUSED><<<grid, 256, 0, st>>>(L, y, Hd, xi, part);
+}
+
+template <int W>
+cudaError_t launch_interp_grad_w(const qs_launch& L, const float* y, const float* Hd, const float* xi, float* part,
+                                 bool fused, cudaStream_t st)
+{
+    if (L.d > QS_GRAD_MAX_D) return cudaErrorInvalidValue;
+    if (fused) launch_interp_grad_f<W, true>(L, y, Hd, xi, part, st);
+    else launch_interp_grad_f<W, false>(L, y, Hd, xi, part, st);
     return cudaGetLastError();
 }
 
@@ -549,26 +570,26 @@ cudaError_t qs_launch_deriv_table(const double* c, const double* psihat, int n_f
     return cudaGetLastError();
 }
 
-cudaError_t qs_launch_spread_grad(const qs_launch& L, int W, const float* x, const float* w, int mode,
+cudaError_t qs_launch_spread_grad(const qs_launch& L, int W, const float* x, const float* w, int mode, bool fused,
                                   const float* Dd, float* H2, cudaStream_t st)
 {
     switch (W) {
-        case 6: return launch_spread_grad_w<6>(L, x, w, mode, Dd, H2, st);
-        case 8: return launch_spread_grad_w<8>(L, x, w, mode, Dd, H2, st);
-        case 10: return launch_spread_grad_w<10>(L, x, w, mode, Dd, H2, st);
-        case 12: return launch_spread_grad_w<12>(L, x, w, mode, Dd, H2, st);
+        case 6: return launch_spread_grad_w<6>(L, x, w, mode, fused, Dd, H2, st);
+        case 8: return launch_spread_grad_w<8>(L, x, w, mode, fused, Dd, H2, st);
+        case 10: return launch_spread_grad_w<10>(L, x, w, mode, fused, Dd, H2, st);
+        case 12: return launch_spread_grad_w<12>(L, x, w, mode, fused, Dd, H2, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t qs_launch_interp_grad(const qs_launch& L, int W, const float* y, const float* Hd, const float* xi,
-                                  float* part, cudaStream_t st)
+                                  float* part, bool fused, cudaStream_t st)
 {
     switch (W) {
-        case 6: return launch_interp_grad_w<6>(L, y, Hd, xi, part, st);
-        case 8: return launch_interp_grad_w<8>(L, y, Hd, xi, part, st);
-        case 10: return launch_interp_grad_w<10>(L, y, Hd, xi, part, st);
-        case 12: return launch_interp_grad_w<12>(L, y, Hd, xi, part, st);
+        case 6: return launch_interp_grad_w<6>(L, y, Hd, xi, part, fused, st);
+        case 8: return launch_interp_grad_w<8>(L, y, Hd, xi, part, fused, st);
+        case 10: return launch_interp_grad_w<10>(L, y, Hd, xi, part, fused, st);
+        case 12: return launch_interp_grad_w<12>(L, y, Hd, xi, part, fused, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -177,10 +177,10 @@ cudaError_t qs_launch_project_fp32(const float* X, int64_t N, int d, const float
                                    float* U, int64_t ldU, cudaStream_t st);
 void qs_set_error_message(const char* msg);
 cudaError_t qs_launch_deriv_table(const double* c, const double* psihat, int n_ft, int G, float* Dd, cudaStream_t st);
-cudaError_t qs_launch_spread_grad(const qs_launch& L, int W, const float* x, const float* w, int mode,
+cudaError_t qs_launch_spread_grad(const qs_launch& L, int W, const float* x, const float* w, int mode, bool fused,
                                   const float* Dd, float* H2, cudaStream_t st);
 cudaError_t qs_launch_interp_grad(const qs_launch& L, int W, const float* y, const float* Hd, const float* xi,
-                                  float* part, cudaStream_t st);
+                                  float* part, bool fused, cudaStream_t st);
 cudaError_t qs_launch_reduce_grad(const float* part, int S, int64_t M, int d, float scale, const float* fac,
                                   float* out, cudaStream_t st);
 bool qs_make_tmap(void* map_out, const void* base, int elem_bytes, int d, int64_t rows, int ldk, int box_rows);

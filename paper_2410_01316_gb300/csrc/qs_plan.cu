@@ -417,8 +417,11 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     if (D.dirs == QS_DIR_FIBONACCI && D.d != 3)
         return fail(QS_ERR_ARG, "qs_plan_create: Fibonacci directions need d = 3");
 
+    // AUTO: the fused form re-reads d coordinates per point and slice with a
+    // strided pattern and only pays off for very small d; the SIMT GEMM is
+    // cheapest below d = 64 and the BF16x3 tensor-core GEMM from there on
     qs_proj proj = D.proj;
-    if (proj == QS_PROJ_AUTO) proj = D.d <= 16 ? QS_PROJ_FP32_FUSED : QS_PROJ_FP32;
+    if (proj == QS_PROJ_AUTO) proj = D.d <= 4 ? QS_PROJ_FP32_FUSED : (D.d < 64 ? QS_PROJ_FP32 : QS_PROJ_BF16X3);
     if (proj == QS_PROJ_FP32_FUSED && D.d > QS_FUSED_MAX_D)
         return fail(QS_ERR_UNSUPPORTED, "qs_plan_create: fused projection needs d <= %d", QS_FUSED_MAX_D);
     if (proj != QS_PROJ_FP32 && proj != QS_PROJ_FP32_FUSED && proj != QS_PROJ_BF16X3 && proj != QS_PROJ_TF32)
@@ -738,6 +741,8 @@ qs_status qs_grad(qs_plan p, const float* x, int64_t N, const float* w, const fl
     cudaStream_t st = (cudaStream_t)stream;
     const int d = p->desc.d;
     const float scale = (float)(p->tau / (double)p->desc.P);
+    // unfused plans project sources and targets with their GEMM into U first
+    const bool fused = p->proj == QS_PROJ_FP32_FUSED;
     cudaError_t e = cudaSuccess;
     // dL/dy_m = (tau/P) v_m sum_p xi_p sum_n w_n g'(b_{m,p} - a_{n,p}): sources x, targets y
     if (gy && M > 0) {
@@ -746,8 +751,10 @@ qs_status qs_grad(qs_plan p, const float* x, int64_t N, const float* w, const fl
         } else {
             qs_launch L = make_launch(p, N, M, 256);
             e = qs_launch_weight_scale(L, w, st);
-            if (e == cudaSuccess) e = qs_launch_spread_grad(L, p->W, x, w, 1, p->d_Dd, p->d_H2, st);
-            if (e == cudaSuccess) e = qs_launch_interp_grad(L, p->W, y, p->d_H2, p->d_dirs, p->d_gpart, st);
+            if (e == cudaSuccess && !fused) e = project(p, x, N, st);
+            if (e == cudaSuccess) e = qs_launch_spread_grad(L, p->W, x, w, 1, fused, p->d_Dd, p->d_H2, st);
+            if (e == cudaSuccess && !fused) e = project(p, y, M, st);
+            if (e == cudaSuccess) e = qs_launch_interp_grad(L, p->W, y, p->d_H2, p->d_dirs, p->d_gpart, fused, st);
             if (e == cudaSuccess) e = qs_launch_reduce_grad(p->d_gpart, L.S, M, d, scale, v, gy, st);
         }
         if (e != cudaSuccess) return cuda_fail(e, "qs_grad: gradient in y");
@@ -762,17 +769,20 @@ qs_status qs_grad(qs_plan p, const float* x, int64_t N, const float* w, const fl
             // gw uses the (fused) interpolation kernel, gx the gradient kernel: each
             // gets the slice-group count matching its CTA shape
             qs_launch L = make_launch(p, M, N, 256);
-            qs_launch Lw = make_launch(p, M, N, 256 * qs_interp_tpt(true, p->desc.d));
+            qs_launch Lw = make_launch(p, M, N, 256 * qs_interp_tpt(fused, p->desc.d));
             e = qs_launch_weight_scale(L, v, st);
+            if (e == cudaSuccess && !fused) e = project(p, y, M, st);
             if (e == cudaSuccess) {
                 if (gx)
-                    e = qs_launch_spread_grad(L, p->W, y, v, gw ? 2 : 1, p->d_Dd, p->d_H2, st);
+                    e = qs_launch_spread_grad(L, p->W, y, v, gw ? 2 : 1, fused, p->d_Dd, p->d_H2, st);
                 else
-                    e = qs_launch_spread(L, p->W, y, v, true, st);
+                    e = qs_launch_spread(L, p->W, y, v, fused, st);
             }
-            if (e == cudaSuccess && gx) e = qs_launch_interp_grad(L, p->W, x, p->d_H2, p->d_dirs, p->d_gpart, st);
+            if (e == cudaSuccess && !fused) e = project(p, x, N, st);
+            if (e == cudaSuccess && gx)
+                e = qs_launch_interp_grad(L, p->W, x, p->d_H2, p->d_dirs, p->d_gpart, fused, st);
             if (e == cudaSuccess && gx) e = qs_launch_reduce_grad(p->d_gpart, L.S, N, d, scale, w, gx, st);
-            if (e == cudaSuccess && gw) e = qs_launch_interp(Lw, p->W, x, true, st);
+            if (e == cudaSuccess && gw) e = qs_launch_interp(Lw, p->W, x, fused, st);
             if (e == cudaSuccess && gw) e = qs_launch_reduce(Lw, gw, st);
         }
         if (e != cudaSuccess) return cuda_fail(e, "qs_grad: gradients in x / w");

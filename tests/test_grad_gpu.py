@@ -30,7 +30,7 @@ def _cuda(a):
 
 
 @pytest.mark.parametrize("kernel,kp,d", [("gauss", 1.2, 3), ("laplace", 0.8, 8), ("negdist", 0.0, 16)])
-@pytest.mark.parametrize("proj", ["fp32_fused", "bf16x3"])
+@pytest.mark.parametrize("proj", ["fp32_fused", "fp32", "bf16x3"])
 def test_grad_matches_oracle(kernel, kp, d, proj):
     prob = W.tiny(d=d, N=1500, M=700, P=40, kernel=kernel, kparam=kp, n_ft=256, seed=40 + d)
     v = np.random.default_rng(3).standard_normal(prob.M).astype(np.float32)
