@@ -461,7 +461,7 @@ def run_batch(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     probs = batch256_problems()
-    plans = [QSPlan(p.d, p.kernel, p.P, p.n_ft, p.R, p.kparam, dirs=p.xi, proj="fp32_fused", max_n=p.N,
+    plans = [QSPlan(p.d, p.kernel, p.P, p.n_ft, p.R, p.kparam, dirs=p.xi, proj="auto", max_n=p.N,
                     max_m=p.M) for p in probs]
     data = [(torch.from_numpy(p.x).to(dev), torch.from_numpy(p.w).to(dev), torch.from_numpy(p.y).to(dev),
              torch.empty(p.M, dtype=torch.float32, device=dev)) for p in probs]
