@@ -283,7 +283,7 @@ def run_ours(args, rank, world, local_rank):
         peaks, peak_src = _peaks()
         props = torch.cuda.get_device_properties(dev)
         sm_count = props.multi_processor_count
-        roof = roofline(prob, plan, stages, clocks, peaks, peak_src, sm_count)
+        roof, stage_roofs = roofline(prob, plan, stages, clocks, peaks, peak_src, sm_count)
         err = None
         err_desc = None
         if not args.no_error_check:
@@ -300,6 +300,9 @@ def run_ours(args, rank, world, local_rank):
                        "spread_variant": spread_variant,
                        "device_status": int(status)},
             "roofline": roof,
+            "stage_rooflines": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()
+                                    if kk in ("bound", "achieved", "peak", "unit", "frac", "ms")}
+                                for k, v in stage_roofs.items()},
             "clocks": clocks,
             "e2e": {"value": ps_step * args.steps * world / e2e_t / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -546,35 +549,62 @@ def launches_per_step(plan) -> int:
     return 6 if plan.proj == "fp32" else 4
 
 
+def stage_rooflines(prob, plan, stages, clocks, peaks, peak_src, sm_count):
+    """Roofline entry per stage, from the in-stream stage events (ms)."""
+    mhz = clocks.get("sm_mhz") or 2070.0
+    smem_lanes = 32.0 * sm_count * mhz * 1e6  # one conflict-free 32-lane shared wavefront per SM per clock
+    fp32_peak = sm_count * 128 * 2 * mhz * 1e6 / 1e12
+    N, M, P, d, W, G = prob.N, prob.M, prob.P, prob.d, prob.window, plan.G
+    out = {}
+
+    def add(name, bound, achieved, peak, unit, what, source):
+        out[name] = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": achieved / peak if peak else None, "traffic": None, "algorithmic": what,
+                     "peak_source": source, "ms": stages[name]}
+
+    for name, rows in (("project_x", N), ("project_y", M)):
+        t = stages.get(name, 0.0) / 1e3
+        if t <= 0:
+            continue
+        if plan.proj == "bf16x3":
+            fl = 6.0 * rows * P * d
+            add(name, "tensor", fl / t / 1e12, peaks["bf16_tflops"], "TFLOP/s",
+                f"6 N P d = {fl:.3e} BF16 flop (three products per FP32 product)",
+                f"bf16_tflops burst ({peak_src})")
+        elif plan.proj == "tf32":
+            fl = 2.0 * rows * P * d
+            add(name, "tensor", fl / t / 1e12, peaks["bf16_tflops"] * 1.1 / 2.25, "TFLOP/s",
+                f"2 N P d = {fl:.3e} TF32 flop", f"bf16_tflops ({peak_src}) x 1.1/2.25 nominal TF32:BF16")
+        else:
+            fl = 2.0 * rows * P * d
+            add(name, "alu", fl / t / 1e12, fp32_peak, "TFLOP/s", f"2 N P d = {fl:.3e} FP32 flop",
+                f"{sm_count} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz")
+    for name, rows in (("prep_x", N), ("prep_y", M)):
+        t = stages.get(name, 0.0) / 1e3
+        if t <= 0:
+            continue
+        by = rows * d * 8.0  # read FP32, write BF16 hi + lo (or TF32)
+        add(name, "hbm", by / t / 1e9, peaks["hbm_gbs"], "GB/s", f"8 B per coordinate = {by:.3e} B",
+            f"hbm_gbs ({peak_src})")
+    t = stages.get("spread_filter", 0.0) / 1e3
+    if t > 0:
+        ops = float(N) * P * W
+        add("spread_filter", "alu", ops / t / 1e9, smem_lanes / 1e9, "Gop/s",
+            f"N P W = {ops:.3e} shared-memory atomic adds (grid accumulation)",
+            f"shared-memory pipe: 32 lanes x {sm_count} SMs x {mhz:.0f} MHz")
+    t = stages.get("interp", 0.0) / 1e3
+    if t > 0:
+        ops = float(M) * P * W
+        add("interp", "alu", ops / t / 1e9, smem_lanes / 1e9, "Gop/s",
+            f"M P W = {ops:.3e} shared-memory tap reads", f"shared-memory pipe: 32 lanes x {sm_count} SMs x {mhz:.0f} MHz")
+    return out
+
+
 def roofline(prob, plan, stages, clocks, peaks, peak_src, sm_count):
-    """Roofline of the dominant kernel of the step, from the in-stream events."""
-    dom = max(stages, key=lambda k: stages[k])
-    t = stages[dom] / 1e3
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
-    if dom in ("project_x", "project_y"):
-        rows = prob.N if dom == "project_x" else prob.M
-        flops = 2.0 * rows * prob.P * prob.d
-        if plan.proj == "fp32":
-            peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
-            return {"kernel": f"projection GEMM ({dom}, FP32 SIMT)", "bound": "alu", "achieved": flops / t / 1e12,
-                    "peak": peak, "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None,
-                    "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (sampled median)",
-                    "algorithmic": f"2 N P d = {flops:.3e} flop per launch"}
-    # grid stages: algorithmic bytes = projections read + grid written / read
-    G = plan.G
-    if dom == "spread_filter":
-        byts = 4.0 * prob.N * prob.P + 4.0 * prob.N + 4.0 * prob.P * G
-        what = "4 B per source-slice (projection) + 4 N (weights) + 4 G per slice (filtered grid)"
-    elif dom == "interp":
-        byts = 4.0 * prob.M * prob.P + 4.0 * prob.P * G + 8.0 * prob.M * 1
-        what = "4 B per target-slice (projection) + 4 G per slice (filtered grid) + partials"
-    else:
-        byts = 4.0 * prob.M * 2
-        what = "partials"
-    peak = peaks["hbm_gbs"]
-    return {"kernel": dom, "bound": "hbm", "achieved": byts / t / 1e9, "peak": peak, "unit": "GB/s",
-            "frac": byts / t / 1e9 / peak, "traffic": None, "peak_source": f"hbm_gbs ({peak_src})",
-            "algorithmic": what}
+    """Roofline of the dominant kernel of the step (the longest stage)."""
+    rl = stage_rooflines(prob, plan, stages, clocks, peaks, peak_src, sm_count)
+    dom = max(rl, key=lambda k: rl[k]["ms"])
+    return rl[dom], rl
 
 
 def error_vs_oracle(prob, s, n_targets: int):

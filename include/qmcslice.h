@@ -191,10 +191,12 @@ qs_status qs_directions(qs_dirs kind, int d, int P, uint64_t seed, float* out_ho
 /*
  * Stage timing for benchmarks.  While enabled, qs_sum records a CUDA event on
  * its stream between consecutive stages.  qs_stage_times waits for the events
- * of the most recent qs_sum call on this plan and writes up to n stage
+ * of the most recent qs_sum call on this plan and writes up to n (<= 7) stage
  * durations in milliseconds:
- *   [0] projection of x   [1] spread + FFT filter   [2] projection of y
- *   [3] interpolation      [4] slice reduction
+ *   [0] operand split of x (tensor-core forms)   [1] projection GEMM of x
+ *   [2] weight bound + spread + FFT filter        [3] operand split of y
+ *   [4] projection GEMM of y                       [5] interpolation
+ *   [6] slice reduction
  * Stages the plan's form does not run report 0.  Enabling creates the events
  * (host-side driver objects, no device memory).  Do not enable while a stream
  * that the plan uses is being captured into a CUDA graph.

@@ -121,15 +121,15 @@ class QSPlan:
                    "qs_plan_set_variant")
 
     # -- stage timing -----------------------------------------------------
-    STAGES = ("project_x", "spread_filter", "project_y", "interp", "reduce")
+    STAGES = ("prep_x", "project_x", "spread_filter", "prep_y", "project_y", "interp", "reduce")
 
     def set_timing(self, enable: bool) -> None:
         _lib.check(self._lib.qs_set_timing(self._handle, 1 if enable else 0), "qs_set_timing")
 
     def stage_times(self) -> dict:
         """Stage durations (ms) of the most recent timed sum, from CUDA events."""
-        ms = (ctypes.c_float * 5)()
-        _lib.check(self._lib.qs_stage_times(self._handle, ms, 5), "qs_stage_times")
+        ms = (ctypes.c_float * len(self.STAGES))()
+        _lib.check(self._lib.qs_stage_times(self._handle, ms, len(self.STAGES)), "qs_stage_times")
         return dict(zip(self.STAGES, [float(v) for v in ms]))
 
     # -- sums -------------------------------------------------------------

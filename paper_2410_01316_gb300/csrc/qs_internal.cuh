@@ -11,6 +11,9 @@
 
 #include "qmcslice.h"
 
+// stages timed by qs_set_timing / qs_stage_times
+#define QS_NUM_STAGES 7
+
 // device error flag bits (qs_check maps them to qs_status)
 #define QS_FLAG_RANGE 1u
 #define QS_FLAG_NONFINITE 2u
@@ -109,7 +112,7 @@ struct qs_plan_s {
     // stage timing (qs_set_timing)
     int timing;
     int timed_calls;
-    cudaEvent_t ev[6];
+    cudaEvent_t ev[8];  // QS_NUM_STAGES + 1
 };
 
 // ---------------------------------------------------------------------------

@@ -247,7 +247,7 @@ double tau_rule(qs_kernel kernel, double kparam, double R)
 void free_plan(qs_plan p)
 {
     if (!p) return;
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < QS_NUM_STAGES + 1; ++i)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
     void* bufs[] = {p->d_dirs, p->d_dirs_s, p->d_c, p->d_psihat, p->d_D, p->d_tw, p->d_U, p->d_H,
                     p->d_part, p->d_flag, p->d_wscale, p->d_x, p->d_w, p->d_y, p->d_s, p->d_xi_hi, p->d_xi_lo,
@@ -301,23 +301,35 @@ qs_launch make_launch(const qs_plan p, int64_t N, int64_t M, int64_t targets_per
     return L;
 }
 
+// Operand preparation of the tensor-core forms (BF16 hi/lo split or TF32
+// rounding of the points into the plan's staging); nothing for FP32.
+cudaError_t project_prep(const qs_plan p, const float* X, int64_t rows, cudaStream_t st)
+{
+    const int d = p->desc.d;
+    switch (p->proj) {
+        case QS_PROJ_BF16X3: return qs_launch_split_bf16(X, rows, d, p->ldk, p->d_xs_hi, p->d_xs_lo, st);
+        case QS_PROJ_TF32: return qs_launch_round_tf32(X, rows, d, p->ldk, (float*)p->d_xs_hi, st);
+        default: return cudaSuccess;
+    }
+}
+
+// The projection GEMM U = G tau X Xi^T (after project_prep for the tensor-core forms).
+cudaError_t project_gemm(const qs_plan p, const float* X, int64_t rows, cudaStream_t st)
+{
+    const int d = p->desc.d, P = p->desc.P;
+    switch (p->proj) {
+        case QS_PROJ_FP32: return qs_launch_project_fp32(X, rows, d, p->d_dirs_s, P, p->d_U, p->ldU, st);
+        case QS_PROJ_BF16X3: return qs_launch_project_tc(0, p->tmaps, rows, d, P, p->d_U, p->ldU, p->d_flag, st);
+        case QS_PROJ_TF32: return qs_launch_project_tc(1, p->tmaps, rows, d, P, p->d_U, p->ldU, p->d_flag, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 // U = G tau X Xi^T for the plan's projection form.
 cudaError_t project(const qs_plan p, const float* X, int64_t rows, cudaStream_t st)
 {
-    const int d = p->desc.d, P = p->desc.P;
-    cudaError_t e;
-    switch (p->proj) {
-        case QS_PROJ_FP32: return qs_launch_project_fp32(X, rows, d, p->d_dirs_s, P, p->d_U, p->ldU, st);
-        case QS_PROJ_BF16X3:
-            e = qs_launch_split_bf16(X, rows, d, p->ldk, p->d_xs_hi, p->d_xs_lo, st);
-            if (e != cudaSuccess) return e;
-            return qs_launch_project_tc(0, p->tmaps, rows, d, P, p->d_U, p->ldU, p->d_flag, st);
-        case QS_PROJ_TF32:
-            e = qs_launch_round_tf32(X, rows, d, p->ldk, (float*)p->d_xs_hi, st);
-            if (e != cudaSuccess) return e;
-            return qs_launch_project_tc(1, p->tmaps, rows, d, P, p->d_U, p->ldU, p->d_flag, st);
-        default: return cudaErrorInvalidValue;
-    }
+    cudaError_t e = project_prep(p, X, rows, st);
+    return e == cudaSuccess ? project_gemm(p, X, rows, st) : e;
 }
 
 }  // namespace
@@ -652,26 +664,36 @@ qs_status qs_sum(qs_plan p, const float* x, int64_t N, const float* w, const flo
     } while (0)
     QS_MARK(0);
     if (!fused) {
-        e = project(p, x, N, st);
-        if (e != cudaSuccess) return cuda_fail(e, "qs_sum: projection of x");
+        e = project_prep(p, x, N, st);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_sum: operand split of x");
     }
     QS_MARK(1);
+    if (!fused) {
+        e = project_gemm(p, x, N, st);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_sum: projection of x");
+    }
+    QS_MARK(2);
     e = qs_launch_weight_scale(L, w, st);
     if (e != cudaSuccess) return cuda_fail(e, "qs_sum: weight bound");
     e = qs_launch_spread(L, p->W, x, w, fused, st);
     if (e != cudaSuccess) return cuda_fail(e, "qs_sum: spread");
-    QS_MARK(2);
+    QS_MARK(3);
     if (!fused) {
-        e = project(p, y, M, st);
+        e = project_prep(p, y, M, st);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_sum: operand split of y");
+    }
+    QS_MARK(4);
+    if (!fused) {
+        e = project_gemm(p, y, M, st);
         if (e != cudaSuccess) return cuda_fail(e, "qs_sum: projection of y");
     }
-    QS_MARK(3);
+    QS_MARK(5);
     e = qs_launch_interp(L, p->W, y, fused, st);
     if (e != cudaSuccess) return cuda_fail(e, "qs_sum: interpolation");
-    QS_MARK(4);
+    QS_MARK(6);
     e = qs_launch_reduce(L, s, st);
     if (e != cudaSuccess) return cuda_fail(e, "qs_sum: reduction");
-    QS_MARK(5);
+    QS_MARK(7);
 #undef QS_MARK
     if (tm) p->timed_calls++;
     return QS_OK;
@@ -682,7 +704,7 @@ qs_status qs_set_timing(qs_plan p, int enable)
     if (!p) return fail(QS_ERR_ARG, "qs_set_timing: NULL plan");
     DeviceGuard g(p->device);
     if (enable && !p->ev[0]) {
-        for (int i = 0; i < 6; ++i) {
+        for (int i = 0; i < QS_NUM_STAGES + 1; ++i) {
             cudaError_t e = cudaEventCreate(&p->ev[i]);
             if (e != cudaSuccess) return cuda_fail(e, "qs_set_timing: cudaEventCreate");
         }
@@ -697,15 +719,15 @@ qs_status qs_stage_times(qs_plan p, float* ms, int n)
     if (!p || !ms || n < 0) return fail(QS_ERR_ARG, "qs_stage_times: bad argument");
     if (!p->ev[0] || p->timed_calls == 0) return fail(QS_ERR_ARG, "qs_stage_times: no timed call recorded");
     DeviceGuard g(p->device);
-    cudaError_t e = cudaEventSynchronize(p->ev[5]);
+    cudaError_t e = cudaEventSynchronize(p->ev[QS_NUM_STAGES]);
     if (e != cudaSuccess) return cuda_fail(e, "qs_stage_times: event");
-    for (int i = 0; i < n && i < 5; ++i) {
+    for (int i = 0; i < n && i < QS_NUM_STAGES; ++i) {
         float t = 0.0f;
         e = cudaEventElapsedTime(&t, p->ev[i], p->ev[i + 1]);
         if (e != cudaSuccess) return cuda_fail(e, "qs_stage_times: elapsed");
         ms[i] = t;
     }
-    for (int i = 5; i < n; ++i) ms[i] = 0.0f;
+    for (int i = QS_NUM_STAGES; i < n; ++i) ms[i] = 0.0f;
     return QS_OK;
 }
 

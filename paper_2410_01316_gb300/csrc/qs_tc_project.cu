@@ -5,10 +5,11 @@
 //
 // One CTA computes a 128-point x 256-slice tile.  TMA streams K-major tiles
 // of the points (A, 128 rows) and of the scaled directions (B, 256 rows) into
-// 128-byte-swizzled shared memory; one thread issues tcgen05.mma with the
-// FP32 accumulator in tensor memory (256 columns); all four warps read the
-// accumulator back with tcgen05.ld and store U with one coalesced 128-byte
-// row segment per warp and slice.
+// 64-byte-swizzled shared memory (64-byte k-slabs, two stages, 97 KB per CTA,
+// so two CTAs share an SM and one's epilogue overlaps the other's MMAs); one
+// thread issues tcgen05.mma with the FP32 accumulator in tensor memory (256
+// columns); all four warps read the accumulator back with tcgen05.ld and store
+// U with one coalesced 128-byte row segment per warp and slice.
 //
 // Two precision forms:
 //   BF16x3  x = x_hi + x_lo and xi = xi_hi + xi_lo in BF16 (round to nearest);
@@ -78,16 +79,16 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // Shared-memory matrix descriptor for a K-major operand tile in the
-// 128-byte swizzle layout written by TMA: rows of 128 bytes, groups of 8 rows
-// 1024 bytes apart (stride byte offset), descriptor version 1, layout 2.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+// 64-byte swizzle layout written by TMA: rows of 64 bytes, groups of 8 rows
+// 512 bytes apart (stride byte offset), descriptor version 1, layout 4.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)(512 >> 4) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
+    d |= (uint64_t)4 << 61;
     return d;
 }
 
@@ -144,17 +145,18 @@ template <int KIND>
 struct TcCfg;
 template <>
 struct TcCfg<0> {  // BF16x3
-    static constexpr int ESZ = 2, BK = 64, STAGES = 2, NOPS = 2, KSTEP = 16;
+    static constexpr int ESZ = 2, BK = 32, STAGES = 2, NOPS = 2, KSTEP = 16;
     static constexpr uint32_t IDESC = make_idesc(1, TILE_M, TILE_N);
 };
 template <>
 struct TcCfg<1> {  // TF32
-    static constexpr int ESZ = 4, BK = 32, STAGES = 4, NOPS = 1, KSTEP = 8;
+    static constexpr int ESZ = 4, BK = 16, STAGES = 4, NOPS = 1, KSTEP = 8;
     static constexpr uint32_t IDESC = make_idesc(2, TILE_M, TILE_N);
 };
 
-constexpr int A_BYTES = TILE_M * 128;  // one 128-byte swizzle row per point
-constexpr int B_BYTES = TILE_N * 128;
+constexpr int ROW_BYTES = 64;               // one 64-byte swizzle row per operand row and k-slab
+constexpr int A_BYTES = TILE_M * ROW_BYTES;
+constexpr int B_BYTES = TILE_N * ROW_BYTES;
 
 template <int KIND>
 __host__ __device__ constexpr int stage_bytes()
@@ -170,7 +172,7 @@ __host__ __device__ constexpr int tc_smem_bytes()
 
 // mA0/mA1: points (hi/lo for BF16x3), mB0/mB1: scaled directions.
 template <int KIND>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
     tc_project_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                       const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, int d,
                       int P, float* __restrict__ U, int64_t ldU, unsigned int* flag)
@@ -257,11 +259,11 @@ __global__ void __launch_bounds__(128, 1)
                 const uint32_t off = (uint32_t)(k * C::KSTEP * C::ESZ);  // 32 bytes per step
                 const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
                 if (KIND == 0) {
-                    mma_f16(tmem, sw128_desc(a0 + off), sw128_desc(b0 + off), C::IDESC, acc);
-                    mma_f16(tmem, sw128_desc(a0 + off), sw128_desc(b1 + off), C::IDESC, 1u);
-                    mma_f16(tmem, sw128_desc(a1 + off), sw128_desc(b0 + off), C::IDESC, 1u);
+                    mma_f16(tmem, sw64_desc(a0 + off), sw64_desc(b0 + off), C::IDESC, acc);
+                    mma_f16(tmem, sw64_desc(a0 + off), sw64_desc(b1 + off), C::IDESC, 1u);
+                    mma_f16(tmem, sw64_desc(a1 + off), sw64_desc(b0 + off), C::IDESC, 1u);
                 } else {
-                    mma_tf32(tmem, sw128_desc(a0 + off), sw128_desc(b0 + off), C::IDESC, acc);
+                    mma_tf32(tmem, sw64_desc(a0 + off), sw64_desc(b0 + off), C::IDESC, acc);
                 }
             }
             mma_commit(empty0 + 8 * s);
@@ -348,7 +350,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
 }  // namespace
 
 // 2-D K-major tensor map: `rows` rows of `d` elements with a row stride of
-// ldk elements; box = one 128-byte swizzle row (BK elements) x box_rows rows.
+// ldk elements; box = one 64-byte swizzle row (BK elements) x box_rows rows.
 // Coordinates past d or rows read zeros.
 bool qs_make_tmap(void* map_out, const void* base, int elem_bytes, int d, int64_t rows, int ldk, int box_rows)
 {
@@ -356,11 +358,11 @@ bool qs_make_tmap(void* map_out, const void* base, int elem_bytes, int d, int64_
     if (!enc) return false;
     cuuint64_t gdim[2] = {(cuuint64_t)d, (cuuint64_t)rows};
     cuuint64_t gstride[1] = {(cuuint64_t)ldk * (cuuint64_t)elem_bytes};
-    cuuint32_t box[2] = {(cuuint32_t)(128 / elem_bytes), (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / elem_bytes), (cuuint32_t)box_rows};
     cuuint32_t estride[2] = {1, 1};
     const CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     CUresult r = enc(reinterpret_cast<CUtensorMap*>(map_out), dt, 2, const_cast<void*>(base), gdim, gstride, box,
-                     estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
