@@ -385,12 +385,15 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
     extern __shared__ float4 rows4[];
     float* rows = reinterpret_cast<float*>(rows4);
     const int G = L.G;
-    const int stride = G + ROW_PAD;
+    // per buffer: the filtered row (G + ROW_PAD cells) and, unfused, the
+    // projections of the CTA's 256 TPT targets on that slice
+    constexpr int UCNT = FUSED ? 0 : IT_THREADS * TPT;
+    const int stride = G + ROW_PAD + UCNT;
     const int g = blockIdx.y;
     const int S = gridDim.y;
     const int p0 = (int)(((int64_t)g * L.P) / S);
     const int p1 = (int)(((int64_t)(g + 1) * L.P) / S);
-    const int64_t mbase = (int64_t)blockIdx.x * IT_THREADS * TPT + threadIdx.x;
+    const int64_t m0 = (int64_t)blockIdx.x * IT_THREADS * TPT;
     const int mask = G - 1;
 
     float yr[FUSED ? DMAX * TPT : 1];
@@ -398,7 +401,7 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
     bool live[TPT];
 #pragma unroll
     for (int i = 0; i < TPT; ++i) {
-        const int64_t m = mbase + (int64_t)i * IT_THREADS;
+        const int64_t m = m0 + threadIdx.x + (int64_t)i * IT_THREADS;
         live[i] = m < L.M;
         hi[i] = 0.0f;
         lo[i] = 0.0f;
@@ -407,11 +410,27 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
             for (int j = 0; j < DMAX; ++j) yr[i * DMAX + j] = (live[i] && j < L.d) ? __ldg(&y[(size_t)m * L.d + j]) : 0.0f;
         }
     }
-    if (p0 < p1) stage_row(rows, L.H + (size_t)p0 * G, G);
+    // stage slice p: its filtered row and (unfused) the block's projections;
+    // a projection chunk is copied only if it lies inside the U row
+    auto stage = [&](int p, float* buf) {
+        const int n16 = (G + ROW_PAD) >> 2;
+        const float* src = L.H + (size_t)p * G;
+        for (int i = threadIdx.x; i < n16; i += IT_THREADS) {
+            const int c = (i << 2) < G ? (i << 2) : (i << 2) - G;
+            cp_async16(buf + (i << 2), src + c);
+        }
+        if (!FUSED) {
+            const float* urow = L.U + (size_t)p * L.ldU + m0;
+            for (int i = threadIdx.x; i < UCNT / 4; i += IT_THREADS)
+                if (m0 + 4 * i + 3 < L.ldU) cp_async16(buf + G + ROW_PAD + 4 * i, urow + 4 * i);
+        }
+        cp_async_commit();
+    };
+    if (p0 < p1) stage(p0, rows);
     for (int p = p0; p < p1; ++p) {
         const float* row = rows + ((p - p0) & 1) * stride;
         if (p + 1 < p1) {
-            stage_row(rows + ((p + 1 - p0) & 1) * stride, L.H + (size_t)(p + 1) * G, G);
+            stage(p + 1, rows + ((p + 1 - p0) & 1) * stride);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -420,7 +439,6 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
 #pragma unroll
         for (int i = 0; i < TPT; ++i) {
             if (!live[i]) continue;
-            const int64_t m = mbase + (int64_t)i * IT_THREADS;
             float u;
             if (FUSED) {
                 const float* xs = L.xi_s + (size_t)p * L.d;
@@ -429,7 +447,7 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
                 for (int j = 0; j < DMAX; ++j)
                     if (j < L.d) u = fmaf(__ldg(&xs[j]), yr[i * DMAX + j], u);
             } else {
-                u = __ldg(&L.U[(size_t)p * L.ldU + m]);
+                u = row[G + ROW_PAD + threadIdx.x + i * IT_THREADS];
             }
             u = qs_check_u(u, L.half_G, L.flag);
             int l0;
@@ -446,7 +464,7 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
 #pragma unroll
     for (int i = 0; i < TPT; ++i) {
         if (!live[i]) continue;
-        const int64_t m = mbase + (int64_t)i * IT_THREADS;
+        const int64_t m = m0 + threadIdx.x + (int64_t)i * IT_THREADS;
         L.part[(size_t)g * L.M + m] = hi[i];
         L.part[(size_t)(S + g) * L.M + m] = lo[i];
     }
@@ -499,9 +517,9 @@ cudaError_t launch_spread_w(const qs_launch& L, const float* x, const float* w, 
 template <int W>
 cudaError_t launch_interp_w(const qs_launch& L, const float* y, bool fused, cudaStream_t st)
 {
-    const size_t smem = (size_t)2 * (L.G + ROW_PAD) * sizeof(float);
-    const unsigned gx = (unsigned)((L.M + (int64_t)IT_THREADS * qs_interp_tpt(fused, L.d) - 1) /
-                                   ((int64_t)IT_THREADS * qs_interp_tpt(fused, L.d)));
+    const int tpt = qs_interp_tpt(fused, L.d);
+    const size_t smem = (size_t)2 * (L.G + ROW_PAD + (fused ? 0 : IT_THREADS * tpt)) * sizeof(float);
+    const unsigned gx = (unsigned)((L.M + (int64_t)IT_THREADS * tpt - 1) / ((int64_t)IT_THREADS * tpt));
     dim3 grid(gx, (unsigned)L.S);
 #define QS_LAUNCH_INTERP(FU, DM, TP)                                                                       \
     do {                                                                                                   \

@@ -38,6 +38,12 @@ enum {
     QS_SPREAD_NVARIANTS = 3
 };
 
+// Degree of the tap polynomials: W - 1 from W = 8 on (the tap error is then
+// ~4e-8, limited by the square-root edge of the window anyway), W + 1 below.
+__host__ __device__ constexpr int qs_tap_degree(int W) { return W >= 8 ? W - 1 : W + 1; }
+// Terms of each even / odd part (the degree is odd).
+__host__ __device__ constexpr int qs_tap_terms(int W) { return (qs_tap_degree(W) + 1) / 2; }
+
 // Tap polynomials.  For tap j of the first half (0 <= j < m), with the
 // centred fractional offset s in [-1/2, 1/2]:
 //   psi(s + m - 1/2 - j)         = E_j(s^2) + s O_j(s^2)
@@ -125,7 +131,7 @@ template <int W>
 __device__ __forceinline__ void qs_taps(float u, const qs_window& win, int& l0, float (&tap)[W])
 {
     constexpr int m = W / 2;
-    constexpr int T = m + 1;
+    constexpr int T = qs_tap_terms(W);
     const float fl = ceilf(u - (float)m);
     l0 = (int)fl;
     const float s = (u - fl) - ((float)m - 0.5f);

@@ -105,7 +105,7 @@ void gl24(double* x, double* w)
 void fit(int W, double beta, qs_window& win)
 {
     const int m = W / 2;
-    const int n = W + 2;  // degree W + 1
+    const int n = qs_tap_degree(W) + 1;
     double tm[QS_MAX_W + 2][QS_MAX_W + 2];
     memset(&win, 0, sizeof(win));
     for (int k = 0; k < n; ++k)
@@ -138,7 +138,7 @@ void fit(int W, double beta, qs_window& win)
 
 double tap(const qs_window& win, int W, int j, double s)
 {
-    const int m = W / 2, T = m + 1;
+    const int m = W / 2, T = qs_tap_terms(W);
     const int jj = j < m ? j : W - 1 - j;
     const double ss = j < m ? s : -s;
     double e = 0.0, o = 0.0;

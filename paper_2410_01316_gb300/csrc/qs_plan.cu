@@ -151,13 +151,13 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w)
     }
 }
 
-// Fit the tap polynomials: Chebyshev interpolation of degree W+1 on
-// s in [-1/2, 1/2] for each tap of the first half, conversion to monomials
-// in s, split into even and odd parts.
+// Fit the tap polynomials: Chebyshev interpolation of degree qs_tap_degree(W)
+// on s in [-1/2, 1/2] for each tap of the first half, conversion to
+// monomials in s, split into even and odd parts.
 void fit_window(int W, double beta, qs_window& win)
 {
     const int m = W / 2;
-    const int deg = W + 1;
+    const int deg = qs_tap_degree(W);
     const int n = deg + 1;
     memset(&win, 0, sizeof(win));
     // T_k(2s) as monomials in s: tm[k][i]
@@ -196,7 +196,7 @@ void fit_window(int W, double beta, qs_window& win)
 double window_tap(const qs_window& win, int W, int j, double s)
 {
     const int m = W / 2;
-    const int T = m + 1;
+    const int T = qs_tap_terms(W);
     const int jj = j < m ? j : W - 1 - j;
     const double ss = j < m ? s : -s;
     double e = 0.0, o = 0.0;
