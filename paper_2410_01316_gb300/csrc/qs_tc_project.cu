@@ -304,17 +304,43 @@ __global__ void __launch_bounds__(128, 2)
 
 // BF16 split of an FP32 row-major matrix (rows x d) into hi and lo parts with
 // row stride ldk (padding columns zero): hi = bf16_rn(v), lo = bf16_rn(v - hi).
+// Each thread converts 4 consecutive entries of a row (ldk is a multiple of
+// 8): one 16-byte load when the row has them (d % 4 == 0 and aligned), one
+// 8-byte store per output.
+__device__ __forceinline__ void split4(float4 v, uint2& h, uint2& l)
+{
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y);
+    const __nv_bfloat162 h23 = __floats2bfloat162_rn(v.z, v.w);
+    const float2 f01 = __bfloat1622float2(h01);
+    const float2 f23 = __bfloat1622float2(h23);
+    const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+    const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+    h = make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+    l = make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+}
+
+template <bool VEC>
 __global__ void split_bf16_kernel(const float* __restrict__ X, int64_t rows, int d, int ldk,
                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo)
 {
-    const int64_t total = rows * (int64_t)ldk;
+    const int g4 = ldk >> 2;
+    const int64_t total = rows * (int64_t)g4;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = i / ldk;
-        const int k = (int)(i - r * ldk);
-        const float v = k < d ? __ldg(&X[r * d + k]) : 0.0f;
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        hi[i] = h;
-        lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+        const int64_t r = i / g4;
+        const int k = (int)(i - r * g4) << 2;
+        float4 v;
+        if (VEC && k + 3 < d) {
+            v = __ldg(reinterpret_cast<const float4*>(X + r * d + k));
+        } else {
+            v.x = k < d ? __ldg(&X[r * d + k]) : 0.0f;
+            v.y = k + 1 < d ? __ldg(&X[r * d + k + 1]) : 0.0f;
+            v.z = k + 2 < d ? __ldg(&X[r * d + k + 2]) : 0.0f;
+            v.w = k + 3 < d ? __ldg(&X[r * d + k + 3]) : 0.0f;
+        }
+        uint2 h, l;
+        split4(v, h, l);
+        *reinterpret_cast<uint2*>(hi + r * ldk + k) = h;
+        *reinterpret_cast<uint2*>(lo + r * ldk + k) = l;
     }
 }
 
@@ -370,10 +396,16 @@ bool qs_make_tmap(void* map_out, const void* base, int elem_bytes, int d, int64_
 cudaError_t qs_launch_split_bf16(const float* X, int64_t rows, int d, int ldk, void* hi, void* lo, cudaStream_t st)
 {
     if (rows <= 0) return cudaSuccess;
-    const int64_t total = rows * (int64_t)ldk;
+    const int64_t total = rows * (int64_t)(ldk / 4);
     int64_t blocks = (total + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    split_bf16_kernel<<<(unsigned)blocks, 256, 0, st>>>(X, rows, d, ldk, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo);
+    const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    if (vec)
+        split_bf16_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(X, rows, d, ldk, (__nv_bfloat16*)hi,
+                                                                   (__nv_bfloat16*)lo);
+    else
+        split_bf16_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(X, rows, d, ldk, (__nv_bfloat16*)hi,
+                                                                    (__nv_bfloat16*)lo);
     return cudaGetLastError();
 }
 
