@@ -274,8 +274,9 @@ qs_status qs_batch_check(qs_batch batch, void* stream);
 qs_status qs_batch_set_tiling(qs_batch batch, int targets_per_thread);
 
 /*
- * Tuning.  The spread stage has variants 0..2 (one point per thread with 1,
- * 2 or 4 lane-private grid copies);
+ * Tuning.  The spread stage has variants 0..3 (one point per thread; 0..2:
+ * 1, 2 or 4 lane-private grid copies; 3: a 32-cell window with one column
+ * per thread, centred on a sample of the slice, plus one shared grid);
  * they produce bitwise identical results and differ only in speed, which
  * depends on how the projections cluster.  qs_plan_autotune runs the spread
  * of the given sources once per variant (timed with CUDA events on `stream`,

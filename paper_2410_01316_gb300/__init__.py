@@ -105,7 +105,7 @@ class QSPlan:
         return out
 
     # -- tuning -------------------------------------------------------------
-    SPREAD_VARIANTS = ("point1", "point2", "point4")
+    SPREAD_VARIANTS = ("point1", "point2", "point4", "thread32")
 
     def autotune(self, x, w=None, stream=None) -> str:
         """Time the spread variants on these sources and keep the fastest."""

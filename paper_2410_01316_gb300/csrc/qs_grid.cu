@@ -19,6 +19,8 @@
 // once to B 2^-31, and integer addition makes the grid independent of the
 // order in which threads add.  (FP32 atomicAdd on shared memory is retried
 // under contention; the projections of clustered data hit a few hundred cells.)
+#include <float.h>
+#include <limits.h>
 #include <math.h>
 
 #include "qs_device.cuh"
@@ -129,60 +131,176 @@ __global__ void __launch_bounds__(1024) weight_scale_kernel(const float* __restr
 // Spread + filter: one CTA per slice p.
 // ---------------------------------------------------------------------------
 // Spread variants (the integer grid makes them bitwise identical): one point
-// per thread, W atomics each, into COPIES lane-private grid copies (copy c
-// shifted by 8 c banks), summed at the end.  More copies cut same-address
-// collisions when projections cluster; one copy keeps occupancy highest.
-template <int W, bool FUSED, int COPIES>
+// per thread, W fixed-point contributions each.
+//  - SPREAD_COPIES (PARAM copies): W atomics into one of PARAM lane-private
+//    grid copies (copy c shifted by 16 c banks), summed at the end.
+//  - SPREAD_THREAD (PARAM cells): each thread owns a column of a window of
+//    min(PARAM, G) cells (cell t of thread i at t * 256 + i), updated with plain
+//    loads and stores, no atomics.  The window is centred on a strided sample of
+//    256 of the slice's points; points whose taps leave it use atomics on the
+//    one shared grid.  Columns are summed into that grid before the FFT.
+// Each grid copy is linear, G + 16 cells, holding cell c at index
+// (c + H) mod G with H = G/2 + 8, so the taps of a point at grid coordinate
+// u in [-G/2, G/2] fill indices l0 + H .. l0 + H + W - 1, all inside
+// [2, G + 14): one base address per point, no wrap-around per tap.  The 16
+// overflow cells fold back onto the first 16 before the FFT.  The cyclic
+// shift by H commutes with the filter (a cyclic convolution) and is undone
+// when the filtered row is stored.
+// The spread of a point is short next to the latency of loading its
+// projection, so each thread loads PF points at once before spreading them.
+enum { SPREAD_COPIES = 0, SPREAD_THREAD = 1 };
+constexpr int SPREAD_PAD = 16;
+
+template <int W, bool FUSED>
+__device__ __forceinline__ float spread_u(const qs_launch& L, const float* __restrict__ x, const float* urow,
+                                          const float* xi_sm, int64_t n)
+{
+    float u;
+    if (FUSED) {
+        const float* xn = x + (size_t)n * L.d;
+        u = 0.0f;
+        for (int j = 0; j < L.d; ++j) u = fmaf(xi_sm[j], __ldg(&xn[j]), u);
+    } else {
+        u = __ldg(&urow[n]);
+    }
+    return u;
+}
+
+// One point: validate (rarely taken branch), taps, fixed-point contributions.
+template <int W, int TW>
+__device__ __forceinline__ void spread_point(const qs_launch& L, float u, float wn, float scale, int H, int* my,
+                                             int* mine, int wbase, int wcells)
+{
+    if (!(fabsf(u) <= L.half_G && fabsf(wn) <= FLT_MAX)) {
+        u = qs_check_u(u, L.half_G, L.flag);
+        if (!isfinite(wn)) {
+            atomicOr(L.flag, QS_FLAG_NONFINITE);
+            wn = 0.0f;
+        }
+    }
+    const float ws = wn * scale;
+    int l0;
+    float tap[W];
+    qs_taps<W>(u, L.win, l0, tap);
+    const int k0 = l0 + H;
+    int q[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) q[j] = __float2int_rn(ws * tap[j]);
+    if (TW) {
+        const unsigned rel = (unsigned)(k0 - wbase);
+        if (rel <= (unsigned)(wcells - W)) {
+            int* cell = mine + (rel << 8);
+#pragma unroll
+            for (int j = 0; j < W; ++j) cell[j << 8] += q[j];
+            return;
+        }
+    }
+    int* cell = my + k0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) atomicAdd(&cell[j], q[j]);
+}
+
+template <int W, bool FUSED, int MODE, int PARAM, int PF>
 __global__ void __launch_bounds__(256) spread_filter_kernel(qs_launch L, const float* __restrict__ x,
                                                             const float* __restrict__ w)
 {
+    constexpr int COPIES = MODE == SPREAD_COPIES ? PARAM : 1;
+    constexpr int TW = MODE == SPREAD_THREAD ? PARAM : 0;
+    static_assert(TW == 0 || TW >= W, "the thread window holds a point's taps");
+    static_assert(W / 2 + 7 < SPREAD_PAD, "taps stay inside the padded grid");
     extern __shared__ float4 smem4[];
     int* gridi = reinterpret_cast<int*>(smem4);
     float* grid = reinterpret_cast<float*>(smem4);
     __shared__ float xi_sm[QS_FUSED_MAX_D];
+    __shared__ int s_lo, s_hi;
     const int p = blockIdx.x;
     const int G = L.G;
-    const int mask = G - 1;
-    const int cstride = G + 8;
-    for (int i = threadIdx.x; i < COPIES * cstride; i += blockDim.x) gridi[i] = 0;
+    const int H = (G >> 1) + 8;
+    const int cstride = G + SPREAD_PAD;
+    const int wcells = TW > G ? G : TW;
+    int* twin = gridi + cstride;  // SPREAD_THREAD: wcells x 256 ints after the grid
+    {
+        int4* z4 = reinterpret_cast<int4*>(smem4);
+        const int n4 = (COPIES * cstride + wcells * 256) >> 2;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) z4[i] = make_int4(0, 0, 0, 0);
+    }
     if (FUSED) {
         for (int j = threadIdx.x; j < L.d; j += blockDim.x) xi_sm[j] = L.xi_s[(size_t)p * L.d + j];
     }
+    if (TW && threadIdx.x == 0) {
+        s_lo = INT_MAX;
+        s_hi = INT_MIN;
+    }
     const float scale = __ldg(&L.wscale[0]);
     const float inv_scale = __ldg(&L.wscale[1]);
+    const float* urow = L.U + (size_t)p * L.ldU;
     __syncthreads();
 
-    const float* urow = L.U + (size_t)p * L.ldU;
+    int wbase = 0;
+    if (TW) {
+        // first grid index of a strided sample of the slice's points
+        int lo = INT_MAX, hi = INT_MIN;
+        const int ns = L.N < (int64_t)blockDim.x ? (int)L.N : (int)blockDim.x;
+        if ((int)threadIdx.x < ns) {
+            const int64_t n = (int64_t)threadIdx.x * L.N / ns;
+            float u = spread_u<W, FUSED>(L, x, urow, xi_sm, n);
+            if (!(fabsf(u) <= L.half_G)) u = 0.0f;  // recorded by the spread itself
+            lo = hi = (int)ceilf(u - (float)(W / 2)) + H;
+        }
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if ((threadIdx.x & 31) == 0 && lo <= hi) {
+            atomicMin(&s_lo, lo);
+            atomicMax(&s_hi, hi);
+        }
+        __syncthreads();
+        if (s_lo <= s_hi) wbase = ((s_lo + s_hi + W) >> 1) - (wcells >> 1);
+        wbase = max(0, min(wbase, cstride - wcells));  // window inside the linear grid
+    }
+
     {
         int* my = gridi + ((threadIdx.x & 31) % COPIES) * cstride;
-        for (int64_t n = threadIdx.x; n < L.N; n += blockDim.x) {
-            float u;
-            if (FUSED) {
-                const float* xn = x + (size_t)n * L.d;
-                u = 0.0f;
-                for (int j = 0; j < L.d; ++j) u = fmaf(xi_sm[j], __ldg(&xn[j]), u);
-            } else {
-                u = __ldg(&urow[n]);
-            }
-            u = qs_check_u(u, L.half_G, L.flag);
-            float wn = w ? __ldg(&w[n]) : 1.0f;
-            if (!isfinite(wn)) {
-                atomicOr(L.flag, QS_FLAG_NONFINITE);
-                wn = 0.0f;
-            }
-            const float ws = wn * scale;
-            int l0;
-            float tap[W];
-            qs_taps<W>(u, L.win, l0, tap);
+        int* mine = twin + threadIdx.x;
+        // PF points per thread per pass: their loads are all issued before the
+        // first of them is spread, so PF loads per thread are in flight.
+        int64_t n0 = threadIdx.x;
+        for (; n0 + (int64_t)(PF - 1) * blockDim.x < L.N; n0 += (int64_t)PF * blockDim.x) {
+            float ub[PF], wb[PF];
 #pragma unroll
-            for (int j = 0; j < W; ++j) atomicAdd(&my[(l0 + j) & mask], __float2int_rn(ws * tap[j]));
+            for (int k = 0; k < PF; ++k) {
+                const int64_t n = n0 + (int64_t)k * blockDim.x;
+                ub[k] = spread_u<W, FUSED>(L, x, urow, xi_sm, n);
+                wb[k] = w ? __ldg(&w[n]) : 1.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < PF; ++k) spread_point<W, TW>(L, ub[k], wb[k], scale, H, my, mine, wbase, wcells);
         }
+        for (; n0 < L.N; n0 += blockDim.x)
+            spread_point<W, TW>(L, spread_u<W, FUSED>(L, x, urow, xi_sm, n0), w ? __ldg(&w[n0]) : 1.0f, scale, H,
+                                my, mine, wbase, wcells);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < G; i += blockDim.x) {
-        int v = gridi[i];
+    if (TW) {
+        // warp k sums the 256 columns of cells k, k + 8, ...
+        const int lane = threadIdx.x & 31;
+        for (int t = threadIdx.x >> 5; t < wcells; t += blockDim.x >> 5) {
+            const int* row = twin + (t << 8);
+            int v = 0;
 #pragma unroll
-        for (int c = 1; c < COPIES; ++c) v += gridi[c * cstride + i];
+            for (int i = 0; i < 8; ++i) v += row[lane + 32 * i];
+            v = __reduce_add_sync(0xffffffffu, v);
+            if (lane == 0) gridi[wbase + t] += v;  // one warp per grid index
+        }
+        __syncthreads();
+    }
+    // sum the copies and fold the overflow cells G .. G + 15 onto 0 .. 15
+    for (int i = threadIdx.x; i < G; i += blockDim.x) {
+        int v = 0;
+#pragma unroll
+        for (int c = 0; c < COPIES; ++c) {
+            v += gridi[c * cstride + i];
+            if (i < SPREAD_PAD) v += gridi[c * cstride + G + i];
+        }
         grid[i] = (float)v * inv_scale;
     }
     __syncthreads();
@@ -195,8 +313,10 @@ __global__ void __launch_bounds__(256) spread_filter_kernel(qs_launch L, const f
     __syncthreads();
     fft_inplace<true>(z, Gh, log2n, L.tw, G);
 
+    // undo the shift: cell c sits at index (c + H) mod G, H a multiple of 4
     float4* dst = reinterpret_cast<float4*>(L.H + (size_t)p * G);
-    for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst[i] = smem4[i];
+    const int hq = H >> 2, qmask = (G >> 2) - 1;
+    for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst[i] = smem4[(i + hq) & qmask];
 }
 
 // ---------------------------------------------------------------------------
@@ -209,50 +329,36 @@ __global__ void __launch_bounds__(256) spread_grad_kernel(qs_launch L, const flo
                                                           const float* __restrict__ w, const float* __restrict__ Dd,
                                                           float* __restrict__ H2)
 {
+    // same shifted, padded linear grid as spread_filter_kernel (one copy)
     extern __shared__ float4 smem4[];
     int* gridi = reinterpret_cast<int*>(smem4);
     float* grid = reinterpret_cast<float*>(smem4);
-    float* grid2 = grid + L.G;
+    float* grid2 = grid + L.G + SPREAD_PAD;
     __shared__ float xi_sm[QS_FUSED_MAX_D];
     const int p = blockIdx.x;
     const int G = L.G;
-    const int mask = G - 1;
-    for (int i = threadIdx.x; i < G; i += blockDim.x) gridi[i] = 0;
+    const int H = (G >> 1) + 8;
+    for (int i = threadIdx.x; i < G + SPREAD_PAD; i += blockDim.x) gridi[i] = 0;
     if (FUSED)
         for (int j = threadIdx.x; j < L.d; j += blockDim.x) xi_sm[j] = L.xi_s[(size_t)p * L.d + j];
     const float scale = __ldg(&L.wscale[0]);
     const float inv_scale = __ldg(&L.wscale[1]);
     const float* urow = L.U + (size_t)p * L.ldU;
     __syncthreads();
-    for (int64_t n = threadIdx.x; n < L.N; n += blockDim.x) {
-        float u;
-        if (FUSED) {
-            const float* xn = x + (size_t)n * L.d;
-            u = 0.0f;
-            for (int j = 0; j < L.d; ++j) u = fmaf(xi_sm[j], __ldg(&xn[j]), u);
-        } else {
-            u = __ldg(&urow[n]);
-        }
-        u = qs_check_u(u, L.half_G, L.flag);
-        float wn = w ? __ldg(&w[n]) : 1.0f;
-        if (!isfinite(wn)) {
-            atomicOr(L.flag, QS_FLAG_NONFINITE);
-            wn = 0.0f;
-        }
-        const float ws = wn * scale;
-        int l0;
-        float tap[W];
-        qs_taps<W>(u, L.win, l0, tap);
-#pragma unroll
-        for (int j = 0; j < W; ++j) atomicAdd(&gridi[(l0 + j) & mask], __float2int_rn(ws * tap[j]));
-    }
+    for (int64_t n = threadIdx.x; n < L.N; n += blockDim.x)
+        spread_point<W, 0>(L, spread_u<W, FUSED>(L, x, urow, xi_sm, n), w ? __ldg(&w[n]) : 1.0f, scale, H, gridi,
+                           nullptr, 0, 0);
     __syncthreads();
-    for (int i = threadIdx.x; i < G; i += blockDim.x) grid[i] = (float)gridi[i] * inv_scale;
+    for (int i = threadIdx.x; i < G; i += blockDim.x) {
+        const int v = gridi[i] + (i < SPREAD_PAD ? gridi[G + i] : 0);
+        grid[i] = (float)v * inv_scale;
+    }
     __syncthreads();
     const int Gh = G >> 1;
     const int log2n = 31 - __clz(Gh);
     float2* z = reinterpret_cast<float2*>(grid);
     float2* z2 = reinterpret_cast<float2*>(grid2);
+    const int hq = H >> 2, qmask = (G >> 2) - 1;
     fft_inplace<false>(z, Gh, log2n, L.tw, G);
     if (MODE == 2) {
         for (int i = threadIdx.x; i < Gh; i += blockDim.x) z2[i] = z[i];
@@ -264,16 +370,16 @@ __global__ void __launch_bounds__(256) spread_grad_kernel(qs_launch L, const flo
         fft_inplace<true>(z2, Gh, log2n, L.tw, G);
         float4* dst = reinterpret_cast<float4*>(L.H + (size_t)p * G);
         const float4* src = reinterpret_cast<const float4*>(grid);
-        for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst[i] = src[i];
+        for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst[i] = src[(i + hq) & qmask];
         float4* dst2 = reinterpret_cast<float4*>(H2 + (size_t)p * G);
         const float4* src2 = reinterpret_cast<const float4*>(grid2);
-        for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst2[i] = src2[i];
+        for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst2[i] = src2[(i + hq) & qmask];
     } else {
         real_filter<true>(z, Gh, Dd, L.tw);
         __syncthreads();
         fft_inplace<true>(z, Gh, log2n, L.tw, G);
         float4* dst2 = reinterpret_cast<float4*>(H2 + (size_t)p * G);
-        for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst2[i] = smem4[i];
+        for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst2[i] = smem4[(i + hq) & qmask];
     }
 }
 
@@ -483,11 +589,13 @@ __global__ void reduce_kernel(const float* __restrict__ part, int S, int64_t M, 
     s[m] = (hi + lo) / (float)P;
 }
 
-template <int W, bool FUSED, int COPIES>
+template <int W, bool FUSED, int MODE, int PARAM, int PF>
 cudaError_t launch_spread_v(const qs_launch& L, const float* x, const float* w, cudaStream_t st)
 {
-    const size_t smem = (size_t)COPIES * (L.G + 8) * sizeof(int);
-    auto kern = spread_filter_kernel<W, FUSED, COPIES>;
+    const int copies = MODE == SPREAD_COPIES ? PARAM : 1;
+    const int tw = MODE == SPREAD_THREAD ? (PARAM > L.G ? L.G : PARAM) : 0;
+    const size_t smem = ((size_t)copies * (L.G + SPREAD_PAD) + (size_t)tw * 256) * sizeof(int);
+    auto kern = spread_filter_kernel<W, FUSED, MODE, PARAM, PF>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -500,9 +608,10 @@ template <int W, bool FUSED>
 cudaError_t launch_spread_f(const qs_launch& L, const float* x, const float* w, int variant, cudaStream_t st)
 {
     switch (variant) {
-        case QS_SPREAD_POINT1: return launch_spread_v<W, FUSED, 1>(L, x, w, st);
-        case QS_SPREAD_POINT2: return launch_spread_v<W, FUSED, 2>(L, x, w, st);
-        case QS_SPREAD_POINT4: return launch_spread_v<W, FUSED, 4>(L, x, w, st);
+        case QS_SPREAD_POINT1: return launch_spread_v<W, FUSED, SPREAD_COPIES, 1, 4>(L, x, w, st);
+        case QS_SPREAD_POINT2: return launch_spread_v<W, FUSED, SPREAD_COPIES, 2, 4>(L, x, w, st);
+        case QS_SPREAD_POINT4: return launch_spread_v<W, FUSED, SPREAD_COPIES, 4, 4>(L, x, w, st);
+        case QS_SPREAD_THREAD32: return launch_spread_v<W, FUSED, SPREAD_THREAD, 32, 4>(L, x, w, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -544,7 +653,7 @@ template <int W>
 cudaError_t launch_spread_grad_w(const qs_launch& L, const float* x, const float* w, int mode, bool fused,
                                  const float* Dd, float* H2, cudaStream_t st)
 {
-    const size_t smem = (size_t)L.G * sizeof(float) * (mode == 2 ? 2 : 1);
+    const size_t smem = ((size_t)L.G + SPREAD_PAD + (mode == 2 ? (size_t)L.G : 0)) * sizeof(float);
     auto kern = mode == 2 ? (fused ? spread_grad_kernel<W, 2, true> : spread_grad_kernel<W, 2, false>)
                           : (fused ? spread_grad_kernel<W, 1, true> : spread_grad_kernel<W, 1, false>);
     if (smem > 48 * 1024) {

@@ -35,7 +35,8 @@ enum {
     QS_SPREAD_POINT1 = 0,  // point per thread, one grid
     QS_SPREAD_POINT2 = 1,  // point per thread, two lane-private grid copies
     QS_SPREAD_POINT4 = 2,  // point per thread, four copies
-    QS_SPREAD_NVARIANTS = 3
+    QS_SPREAD_THREAD32 = 3,  // point per thread, thread-private 32-cell window columns + one grid
+    QS_SPREAD_NVARIANTS = 4
 };
 
 // Degree of the tap polynomials: W - 1 from W = 8 on (the tap error is then

@@ -186,12 +186,22 @@ def test_mnist_laplace_full_size_sampled_targets():
     assert _err(s[idx], ref, prob) < TOL_FP32
 
 
-@pytest.mark.parametrize("proj", ["fp32_fused", "fp32"])
+def _variant_problem(case):
+    if case == "grid512":  # the 512-cell window covers the whole grid
+        return W.tiny(d=5, N=3001, M=500, P=20, kernel="negdist", kparam=0.0, n_ft=256, seed=21)
+    if case == "grid4096_spread":  # projections spread over ~1000 cells: many points leave the windows
+        return W.tiny(d=5, N=3001, M=500, P=20, kernel="negdist", kparam=0.0, n_ft=2048, seed=22)
+    # MNIST-shaped: projections cluster within a few dozen cells of G = 2048
+    return W.mnist_laplace(N=3001, M=500, P=20, n_ft=1024, seed=23)
+
+
+@pytest.mark.parametrize("case,proj", [("grid512", "fp32_fused"), ("grid512", "fp32"),
+                                       ("grid4096_spread", "fp32_fused"), ("clustered_d784", "fp32")])
 @pytest.mark.parametrize("window", [6, 8, 12])
-def test_spread_variants_are_bitwise_identical(proj, window):
+def test_spread_variants_are_bitwise_identical(case, proj, window):
     import torch
 
-    prob = W.tiny(d=5, N=3001, M=500, P=20, kernel="negdist", kparam=0.0, n_ft=256, seed=21)
+    prob = _variant_problem(case)
     x, w, y = (torch.from_numpy(a).cuda() for a in (prob.x, prob.w, prob.y))
     outs = []
     with _plan(prob, proj, window) as plan:
