@@ -274,18 +274,25 @@ qs_status qs_batch_check(qs_batch batch, void* stream);
 qs_status qs_batch_set_tiling(qs_batch batch, int targets_per_thread);
 
 /*
- * Tuning.  The spread stage has variants 0..3 (one point per thread; 0..2:
- * 1, 2 or 4 lane-private grid copies; 3: a 32-cell window with one column
- * per thread, centred on a sample of the slice, plus one shared grid);
- * they produce bitwise identical results and differ only in speed, which
- * depends on how the projections cluster.  qs_plan_autotune runs the spread
- * of the given sources once per variant (timed with CUDA events on `stream`,
- * best of 3 after a warm-up), keeps the fastest in the plan and writes its
- * index to *chosen (may be NULL).  Synchronous.  qs_plan_set_variant fixes a
- * variant directly (QS_ERR_ARG if out of range).
+ * Tuning.  The spread stage has variants in two families, fixed by the grid
+ * size G and the window W: the moment family (4: one bin table; 5: a 32-bin
+ * lane-interleaved window plus the table) where its shared memory fits two
+ * CTAs per SM (G <= 2048 for W <= 8, G <= 1024 for W >= 10), the tap family
+ * otherwise (0..2: one point per thread with 1, 2 or 4 lane-private grid
+ * copies; 3: a 32-cell window with one column per thread plus one grid).
+ * Within a family the variants produce bitwise identical results and differ
+ * only in speed, which depends on how the projections cluster.
+ * qs_plan_autotune runs the spread of the given sources once per variant of
+ * the family (timed with CUDA events on `stream`, best of 3 after a warm-up),
+ * keeps the fastest in the plan and writes its index to *chosen (may be
+ * NULL).  Synchronous.  qs_plan_set_variant fixes a variant directly
+ * (QS_ERR_ARG if out of range or of the other family).
  */
 qs_status qs_plan_autotune(qs_plan plan, const float* x, int64_t N, const float* w, int* chosen, void* stream);
 qs_status qs_plan_set_variant(qs_plan plan, int spread_variant);
+/* Variants of the plan's family (bit v of *available set for variant v) and
+ * the variant in use (*current); either pointer may be NULL.  Host only. */
+qs_status qs_plan_variants(qs_plan plan, unsigned int* available, int* current);
 
 /* Library version string. */
 const char* qs_version(void);

@@ -105,7 +105,7 @@ class QSPlan:
         return out
 
     # -- tuning -------------------------------------------------------------
-    SPREAD_VARIANTS = ("point1", "point2", "point4", "thread32")
+    SPREAD_VARIANTS = ("point1", "point2", "point4", "thread32", "moment", "momentwin32")
 
     def autotune(self, x, w=None, stream=None) -> str:
         """Time the spread variants on these sources and keep the fastest."""
@@ -119,6 +119,18 @@ class QSPlan:
     def set_variant(self, name: str) -> None:
         _lib.check(self._lib.qs_plan_set_variant(self._handle, self.SPREAD_VARIANTS.index(name)),
                    "qs_plan_set_variant")
+
+    def spread_variants(self) -> tuple:
+        """Names of the spread variants of this plan's family (bitwise identical to each other)."""
+        mask = ctypes.c_uint(0)
+        _lib.check(self._lib.qs_plan_variants(self._handle, ctypes.byref(mask), None), "qs_plan_variants")
+        return tuple(n for i, n in enumerate(self.SPREAD_VARIANTS) if mask.value >> i & 1)
+
+    def variant(self) -> str:
+        """The spread variant in use."""
+        cur = ctypes.c_int(-1)
+        _lib.check(self._lib.qs_plan_variants(self._handle, None, ctypes.byref(cur)), "qs_plan_variants")
+        return self.SPREAD_VARIANTS[cur.value]
 
     # -- stage timing -----------------------------------------------------
     STAGES = ("prep_x", "project_x", "spread_filter", "prep_y", "project_y", "interp", "reduce")

@@ -32,7 +32,7 @@ EXPORTS = ("qs_plan_create", "qs_plan_destroy", "qs_plan_info", "qs_plan_directi
            "qs_sum_host", "qs_check", "qs_status_string", "qs_last_error", "qs_directions", "qs_version",
            "qs_set_timing", "qs_stage_times", "qs_project", "qs_sum_noalloc", "qs_grad",
            "qs_plan_autotune", "qs_plan_set_variant", "qs_batch_create", "qs_batch_destroy", "qs_sum_batched",
-           "qs_batch_check", "qs_batch_set_tiling")
+           "qs_batch_check", "qs_batch_set_tiling", "qs_plan_variants")
 
 
 class PlanDesc(ctypes.Structure):
@@ -85,6 +85,7 @@ def load() -> ctypes.CDLL:
         lib.qs_batch_set_tiling.argtypes = [c_vp, c_int]
         lib.qs_plan_autotune.argtypes = [c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(c_int), c_vp]
         lib.qs_plan_set_variant.argtypes = [c_vp, c_int]
+        lib.qs_plan_variants.argtypes = [c_vp, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(c_int)]
         lib.qs_grad.argtypes = [c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]
         lib.qs_sum_noalloc.argtypes = [ctypes.POINTER(PlanDesc), c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp]
         lib.qs_set_timing.argtypes = [c_vp, c_int]
@@ -95,7 +96,7 @@ def load() -> ctypes.CDLL:
                      "qs_sum_host", "qs_check", "qs_directions", "qs_set_timing", "qs_stage_times", "qs_project",
                      "qs_sum_noalloc", "qs_grad", "qs_plan_autotune", "qs_plan_set_variant",
                      "qs_batch_create", "qs_batch_destroy", "qs_sum_batched", "qs_batch_check",
-                     "qs_batch_set_tiling"):
+                     "qs_batch_set_tiling", "qs_plan_variants"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib

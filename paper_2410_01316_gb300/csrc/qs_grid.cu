@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(1024) weight_scale_kernel(const float* __restr
 // The spread of a point is short next to the latency of loading its
 // projection, so each thread loads PF points at once before spreading them.
 enum { SPREAD_COPIES = 0, SPREAD_THREAD = 1 };
-constexpr int SPREAD_PAD = 16;
+constexpr int SPREAD_PAD = QS_SPREAD_PAD;
 
 template <int W, bool FUSED>
 __device__ __forceinline__ float spread_u(const qs_launch& L, const float* __restrict__ x, const float* urow,
@@ -198,6 +198,24 @@ __device__ __forceinline__ void spread_point(const qs_launch& L, float u, float 
     int* cell = my + k0;
 #pragma unroll
     for (int j = 0; j < W; ++j) atomicAdd(&cell[j], q[j]);
+}
+
+// Filter the shifted grid of slice p (FFT, c_k / psi^2, inverse FFT) and
+// store it unshifted: cell c sits at index (c + H) mod G, H a multiple of 4.
+__device__ __forceinline__ void filter_store(const qs_launch& L, float* grid, int p, int H)
+{
+    const int G = L.G;
+    const int Gh = G >> 1;
+    const int log2n = 31 - __clz(Gh);
+    float2* z = reinterpret_cast<float2*>(grid);
+    fft_inplace<false>(z, Gh, log2n, L.tw, G);
+    real_filter<false>(z, Gh, L.D, L.tw);
+    __syncthreads();
+    fft_inplace<true>(z, Gh, log2n, L.tw, G);
+    float4* dst = reinterpret_cast<float4*>(L.H + (size_t)p * G);
+    const float4* src = reinterpret_cast<const float4*>(grid);
+    const int hq = H >> 2, qmask = (G >> 2) - 1;
+    for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst[i] = src[(i + hq) & qmask];
 }
 
 template <int W, bool FUSED, int MODE, int PARAM, int PF>
@@ -304,19 +322,219 @@ __global__ void __launch_bounds__(256) spread_filter_kernel(qs_launch L, const f
         grid[i] = (float)v * inv_scale;
     }
     __syncthreads();
+    filter_store(L, grid, p, H);
+}
 
-    const int Gh = G >> 1;
-    const int log2n = 31 - __clz(Gh);
-    float2* z = reinterpret_cast<float2*>(grid);
-    fft_inplace<false>(z, Gh, log2n, L.tw, G);
-    real_filter<false>(z, Gh, L.D, L.tw);
+// ---------------------------------------------------------------------------
+// Moment spread.  Tap j of a point is the polynomial sum_k a_jk t^k in
+// t = 2s in (-1, 1] (s the centred fractional offset of qs_taps), so the
+// taps a bin b = l0 of the grid receives from its points follow from the K
+// fixed-point moments M_bk = sum_n rn(w_n scale t_n^k): cell b + j gets
+// sum_k a_jk M_bk.  Moments 0 and 1 are accumulated as the pair
+// rn(ws (1 + t)/2), rn(ws (1 - t)/2), whose sum and difference give them
+// exactly: with equal weights a constant basis function would make every
+// point's rounding error the same, so that it grows like n instead of sqrt(n).  A point then costs K - 1 products and K conversions
+// instead of W polynomial evaluations, and every variant adds the same
+// integers into the same bins, so the grids are bitwise identical.  With
+// |t| <= 1 each moment stays below 2^30 like a grid cell, and the a_jk of the
+// window are below 1 in magnitude (sum_k |a_jk| ~ 1.2), so the quantisation
+// error matches that of the tap spread.
+// Shared layout: the bin table, (G + 16) bins of K + 1 ints (an odd row
+// stride, so random bins spread over the banks), at the bins' linear grid
+// indices kb = l0 + H; then, for LW > 0, a window of LW bins with the
+// moments of lane i at [bin][k][i] (one bank per lane), centred like the
+// thread window of spread_filter_kernel and summed into the table at the
+// end; the float grid (G + 16) reuses that space.
+// ---------------------------------------------------------------------------
+template <int W, int LW>
+__device__ __forceinline__ void moment_point(const qs_launch& L, float u, float wn, float scale, int H, int* tab,
+                                             int* lanecol, int wbase)
+{
+    constexpr int m = W / 2;
+    constexpr int K = qs_moment_count(W);
+    constexpr int KS = K + 1;
+    if (!(fabsf(u) <= L.half_G && fabsf(wn) <= FLT_MAX)) {
+        u = qs_check_u(u, L.half_G, L.flag);
+        if (!isfinite(wn)) {
+            atomicOr(L.flag, QS_FLAG_NONFINITE);
+            wn = 0.0f;
+        }
+    }
+    const float ws = wn * scale;
+    const float fl = ceilf(u - (float)m);
+    const int kb = (int)fl + H;
+    const float t = 2.0f * ((u - fl) - ((float)m - 0.5f));
+    // moments 0 and 1 as ws (1 + t)/2 and ws (1 - t)/2: a basis function
+    // constant in t would round every equal weight the same way
+    const float hw = 0.5f * ws;
+    int q[K];
+    q[0] = __float2int_rn(fmaf(hw, t, hw));
+    q[1] = __float2int_rn(fmaf(-hw, t, hw));
+    float pk = ws * t;
+#pragma unroll
+    for (int k = 2; k < K; ++k) {
+        pk *= t;
+        q[k] = __float2int_rn(pk);
+    }
+    if constexpr (LW > 0) {
+        const unsigned rel = (unsigned)(kb - wbase);
+        if (rel < (unsigned)LW) {
+            int* c = lanecol + rel * (K * 32);
+#pragma unroll
+            for (int k = 0; k < K; ++k) atomicAdd(&c[k * 32], q[k]);
+            return;
+        }
+    }
+    int* c = tab + kb * KS;
+#pragma unroll
+    for (int k = 0; k < K; ++k) atomicAdd(&c[k], q[k]);
+}
+
+// Spread the N points of slice p into moments and turn them into the float
+// grid at `grid` (shifted layout, fixed-point scale removed); ends with a
+// barrier.  Shared memory as described above.
+template <int W, bool FUSED, int LW, int PF>
+__device__ __forceinline__ void moment_grid(const qs_launch& L, const float* __restrict__ x,
+                                            const float* __restrict__ w, int p, int H, int* tab, float* grid,
+                                            const float* xi_sm, int* s_lohi)
+{
+    constexpr int m = W / 2;
+    constexpr int K = qs_moment_count(W);
+    constexpr int KS = K + 1;
+    constexpr int T = qs_tap_terms(W);
+    static_assert(K == 2 * T, "one moment per polynomial coefficient");
+    const int G = L.G;
+    const int cs = G + SPREAD_PAD;
+    int* lanewin = tab + cs * KS;
+    const float scale = __ldg(&L.wscale[0]);
+    const float inv_scale = __ldg(&L.wscale[1]);
+    const float* urow = L.U + (size_t)p * L.ldU;
+
+    int wbase = 0;
+    if (LW) {
+        int lo = INT_MAX, hi = INT_MIN;
+        const int ns = L.N < (int64_t)blockDim.x ? (int)L.N : (int)blockDim.x;
+        if ((int)threadIdx.x < ns) {
+            const int64_t n = (int64_t)threadIdx.x * L.N / ns;
+            float u = spread_u<W, FUSED>(L, x, urow, xi_sm, n);
+            if (!(fabsf(u) <= L.half_G)) u = 0.0f;  // recorded by the spread itself
+            lo = hi = (int)ceilf(u - (float)m) + H;
+        }
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if ((threadIdx.x & 31) == 0 && lo <= hi) {
+            atomicMin(&s_lohi[0], lo);
+            atomicMax(&s_lohi[1], hi);
+        }
+        __syncthreads();
+        if (s_lohi[0] <= s_lohi[1]) wbase = ((s_lohi[0] + s_lohi[1]) >> 1) - (LW >> 1);
+        wbase = max(0, min(wbase, cs - LW));
+    }
+
+    {
+        int* lanecol = lanewin + (threadIdx.x & 31);
+        int64_t n0 = threadIdx.x;
+        for (; n0 + (int64_t)(PF - 1) * blockDim.x < L.N; n0 += (int64_t)PF * blockDim.x) {
+            float ub[PF], wb[PF];
+#pragma unroll
+            for (int k = 0; k < PF; ++k) {
+                const int64_t n = n0 + (int64_t)k * blockDim.x;
+                ub[k] = spread_u<W, FUSED>(L, x, urow, xi_sm, n);
+                wb[k] = w ? __ldg(&w[n]) : 1.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < PF; ++k) moment_point<W, LW>(L, ub[k], wb[k], scale, H, tab, lanecol, wbase);
+        }
+        for (; n0 < L.N; n0 += blockDim.x)
+            moment_point<W, LW>(L, spread_u<W, FUSED>(L, x, urow, xi_sm, n0), w ? __ldg(&w[n0]) : 1.0f, scale, H,
+                                tab, lanecol, wbase);
+    }
     __syncthreads();
-    fft_inplace<true>(z, Gh, log2n, L.tw, G);
+    if (LW) {
+        // one warp per (bin, moment): sum the 32 lane columns into the table
+        const int lane = threadIdx.x & 31;
+        for (int r = threadIdx.x >> 5; r < LW * K; r += blockDim.x >> 5) {
+            int v = __reduce_add_sync(0xffffffffu, lanewin[r * 32 + lane]);
+            if (lane == 0) tab[(wbase + r / K) * KS + r % K] += v;
+        }
+        __syncthreads();
+    }
+    // per bin: the W tap sums V_bj = sum_k a_jk M_bk, written over the moments
+    // (K >= W); mirrored taps share the even and odd parts
+    float* vtab = reinterpret_cast<float*>(tab);
+    for (int b = threadIdx.x; b < cs; b += blockDim.x) {
+        int* row = tab + b * KS;
+        int mk[K];
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            mk[k] = row[k];
+            any |= mk[k] != 0;
+        }
+        if (!any) continue;  // the row already reads as W zero floats
+        float mh[K];
+        mh[0] = (float)(mk[0] + mk[1]);
+        mh[1] = 0.5f * (float)(mk[0] - mk[1]);
+#pragma unroll
+        for (int k = 2; k < K; ++k) mh[k] = ldexpf((float)mk[k], -k);
+#pragma unroll
+        for (int j = 0; j < m; ++j) {
+            float e = 0.0f, o = 0.0f;
+#pragma unroll
+            for (int i = 0; i < T; ++i) {
+                e = fmaf(L.win.e[j][i], mh[2 * i], e);
+                o = fmaf(L.win.o[j][i], mh[2 * i + 1], o);
+            }
+            vtab[b * KS + j] = e + o;
+            vtab[b * KS + W - 1 - j] = e - o;
+        }
+    }
+    __syncthreads();
+    // cell c = sum_j V_{c-j, j}; the overflow cells G .. G + 15 fold onto 0 .. 15
+    for (int c = threadIdx.x; c < G; c += blockDim.x) {
+        float v = 0.0f;
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+            if (c - j >= 0) v += vtab[(c - j) * KS + j];
+        if (c < SPREAD_PAD) {
+            float f = 0.0f;
+#pragma unroll
+            for (int j = 0; j < W; ++j) f += vtab[(G + c - j) * KS + j];
+            v += f;
+        }
+        grid[c] = v * inv_scale;
+    }
+    __syncthreads();
+}
 
-    // undo the shift: cell c sits at index (c + H) mod G, H a multiple of 4
-    float4* dst = reinterpret_cast<float4*>(L.H + (size_t)p * G);
-    const int hq = H >> 2, qmask = (G >> 2) - 1;
-    for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst[i] = smem4[(i + hq) & qmask];
+template <int W, bool FUSED, int LW, int PF>
+__global__ void __launch_bounds__(512, 2) spread_moment_kernel(qs_launch L, const float* __restrict__ x,
+                                                               const float* __restrict__ w)
+{
+    constexpr int K = qs_moment_count(W);
+    extern __shared__ float4 smem4[];
+    int* tab = reinterpret_cast<int*>(smem4);
+    __shared__ float xi_sm[QS_FUSED_MAX_D];
+    __shared__ int s_lohi[2];
+    const int p = blockIdx.x;
+    const int G = L.G;
+    const int H = (G >> 1) + 8;
+    const int cs = G + SPREAD_PAD;
+    float* grid = reinterpret_cast<float*>(tab + cs * (K + 1));
+    {
+        int4* z4 = reinterpret_cast<int4*>(smem4);
+        const int n4 = (cs * (K + 1) + LW * K * 32) >> 2;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) z4[i] = make_int4(0, 0, 0, 0);
+    }
+    if (FUSED)
+        for (int j = threadIdx.x; j < L.d; j += blockDim.x) xi_sm[j] = L.xi_s[(size_t)p * L.d + j];
+    if (threadIdx.x == 0) {
+        s_lohi[0] = INT_MAX;
+        s_lohi[1] = INT_MIN;
+    }
+    __syncthreads();
+    moment_grid<W, FUSED, LW, PF>(L, x, w, p, H, tab, grid, xi_sm, s_lohi);
+    filter_store(L, grid, p, H);
 }
 
 // ---------------------------------------------------------------------------
@@ -324,6 +542,44 @@ __global__ void __launch_bounds__(256) spread_filter_kernel(qs_launch L, const f
 // MODE 1: H2 <- derivative filter (table Dd).  MODE 2: L.H <- plain filter
 // (table L.D) and H2 <- derivative filter from the same spread grid.
 // ---------------------------------------------------------------------------
+// Filter the shifted grid of slice p for the gradients and store unshifted.
+// MODE 1: H2 <- derivative filter (table Dd).  MODE 2: also L.H <- plain
+// filter, from a copy of the spectrum in grid2.
+template <int MODE>
+__device__ __forceinline__ void grad_filter_store(const qs_launch& L, float* grid, float* grid2, const float* Dd,
+                                                  float* H2, int p, int H)
+{
+    const int G = L.G;
+    const int Gh = G >> 1;
+    const int log2n = 31 - __clz(Gh);
+    float2* z = reinterpret_cast<float2*>(grid);
+    float2* z2 = reinterpret_cast<float2*>(grid2);
+    const int hq = H >> 2, qmask = (G >> 2) - 1;
+    fft_inplace<false>(z, Gh, log2n, L.tw, G);
+    if (MODE == 2) {
+        for (int i = threadIdx.x; i < Gh; i += blockDim.x) z2[i] = z[i];
+        __syncthreads();
+        real_filter<false>(z, Gh, L.D, L.tw);
+        real_filter<true>(z2, Gh, Dd, L.tw);
+        __syncthreads();
+        fft_inplace<true>(z, Gh, log2n, L.tw, G);
+        fft_inplace<true>(z2, Gh, log2n, L.tw, G);
+        float4* dst = reinterpret_cast<float4*>(L.H + (size_t)p * G);
+        const float4* src = reinterpret_cast<const float4*>(grid);
+        for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst[i] = src[(i + hq) & qmask];
+        float4* dst2 = reinterpret_cast<float4*>(H2 + (size_t)p * G);
+        const float4* src2 = reinterpret_cast<const float4*>(grid2);
+        for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst2[i] = src2[(i + hq) & qmask];
+    } else {
+        real_filter<true>(z, Gh, Dd, L.tw);
+        __syncthreads();
+        fft_inplace<true>(z, Gh, log2n, L.tw, G);
+        float4* dst2 = reinterpret_cast<float4*>(H2 + (size_t)p * G);
+        const float4* src = reinterpret_cast<const float4*>(grid);
+        for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst2[i] = src[(i + hq) & qmask];
+    }
+}
+
 template <int W, int MODE, bool FUSED>
 __global__ void __launch_bounds__(256) spread_grad_kernel(qs_launch L, const float* __restrict__ x,
                                                           const float* __restrict__ w, const float* __restrict__ Dd,
@@ -354,33 +610,38 @@ __global__ void __launch_bounds__(256) spread_grad_kernel(qs_launch L, const flo
         grid[i] = (float)v * inv_scale;
     }
     __syncthreads();
-    const int Gh = G >> 1;
-    const int log2n = 31 - __clz(Gh);
-    float2* z = reinterpret_cast<float2*>(grid);
-    float2* z2 = reinterpret_cast<float2*>(grid2);
-    const int hq = H >> 2, qmask = (G >> 2) - 1;
-    fft_inplace<false>(z, Gh, log2n, L.tw, G);
-    if (MODE == 2) {
-        for (int i = threadIdx.x; i < Gh; i += blockDim.x) z2[i] = z[i];
-        __syncthreads();
-        real_filter<false>(z, Gh, L.D, L.tw);
-        real_filter<true>(z2, Gh, Dd, L.tw);
-        __syncthreads();
-        fft_inplace<true>(z, Gh, log2n, L.tw, G);
-        fft_inplace<true>(z2, Gh, log2n, L.tw, G);
-        float4* dst = reinterpret_cast<float4*>(L.H + (size_t)p * G);
-        const float4* src = reinterpret_cast<const float4*>(grid);
-        for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst[i] = src[(i + hq) & qmask];
-        float4* dst2 = reinterpret_cast<float4*>(H2 + (size_t)p * G);
-        const float4* src2 = reinterpret_cast<const float4*>(grid2);
-        for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst2[i] = src2[(i + hq) & qmask];
-    } else {
-        real_filter<true>(z, Gh, Dd, L.tw);
-        __syncthreads();
-        fft_inplace<true>(z, Gh, log2n, L.tw, G);
-        float4* dst2 = reinterpret_cast<float4*>(H2 + (size_t)p * G);
-        for (int i = threadIdx.x; i < (G >> 2); i += blockDim.x) dst2[i] = smem4[(i + hq) & qmask];
+    grad_filter_store<MODE>(L, grid, grid2, Dd, H2, p, H);
+}
+
+// The same from a moment spread (plans whose sums use the moment family, so
+// that the plain grid of MODE 2 equals that of spread_moment_kernel bit for bit).
+template <int W, int MODE, bool FUSED>
+__global__ void __launch_bounds__(512, 2) spread_grad_moment_kernel(qs_launch L, const float* __restrict__ x,
+                                                                    const float* __restrict__ w,
+                                                                    const float* __restrict__ Dd,
+                                                                    float* __restrict__ H2)
+{
+    constexpr int K = qs_moment_count(W);
+    extern __shared__ float4 smem4[];
+    int* tab = reinterpret_cast<int*>(smem4);
+    __shared__ float xi_sm[QS_FUSED_MAX_D];
+    __shared__ int s_lohi[2];
+    const int p = blockIdx.x;
+    const int G = L.G;
+    const int H = (G >> 1) + 8;
+    const int cs = G + SPREAD_PAD;
+    float* grid = reinterpret_cast<float*>(tab + cs * (K + 1));
+    float* grid2 = grid + cs;
+    {
+        int4* z4 = reinterpret_cast<int4*>(smem4);
+        const int n4 = (cs * (K + 1)) >> 2;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) z4[i] = make_int4(0, 0, 0, 0);
     }
+    if (FUSED)
+        for (int j = threadIdx.x; j < L.d; j += blockDim.x) xi_sm[j] = L.xi_s[(size_t)p * L.d + j];
+    __syncthreads();
+    moment_grid<W, FUSED, 0, 4>(L, x, w, p, H, tab, grid, xi_sm, s_lohi);
+    grad_filter_store<MODE>(L, grid, grid2, Dd, H2, p, H);
 }
 
 // ---------------------------------------------------------------------------
@@ -604,6 +865,17 @@ cudaError_t launch_spread_v(const qs_launch& L, const float* x, const float* w, 
     return cudaGetLastError();
 }
 
+template <int W, bool FUSED, int LW>
+cudaError_t launch_moment_v(const qs_launch& L, const float* x, const float* w, cudaStream_t st)
+{
+    const size_t smem = qs_moment_smem(L.G, W, LW > 0);
+    auto kern = spread_moment_kernel<W, FUSED, LW, 4>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<L.P, 512, smem, st>>>(L, x, w);
+    return cudaGetLastError();
+}
+
 template <int W, bool FUSED>
 cudaError_t launch_spread_f(const qs_launch& L, const float* x, const float* w, int variant, cudaStream_t st)
 {
@@ -612,6 +884,8 @@ cudaError_t launch_spread_f(const qs_launch& L, const float* x, const float* w, 
         case QS_SPREAD_POINT2: return launch_spread_v<W, FUSED, SPREAD_COPIES, 2, 4>(L, x, w, st);
         case QS_SPREAD_POINT4: return launch_spread_v<W, FUSED, SPREAD_COPIES, 4, 4>(L, x, w, st);
         case QS_SPREAD_THREAD32: return launch_spread_v<W, FUSED, SPREAD_THREAD, 32, 4>(L, x, w, st);
+        case QS_SPREAD_MOMENT: return launch_moment_v<W, FUSED, 0>(L, x, w, st);
+        case QS_SPREAD_MOMENTWIN32: return launch_moment_v<W, FUSED, QS_MOMENT_WIN>(L, x, w, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -653,6 +927,16 @@ template <int W>
 cudaError_t launch_spread_grad_w(const qs_launch& L, const float* x, const float* w, int mode, bool fused,
                                  const float* Dd, float* H2, cudaStream_t st)
 {
+    if (qs_spread_moments(L.G, W)) {
+        const size_t cs = (size_t)L.G + SPREAD_PAD;
+        const size_t smem = (cs * (qs_moment_count(W) + 1) + cs + (mode == 2 ? (size_t)L.G : 0)) * sizeof(float);
+        auto kern = mode == 2 ? (fused ? spread_grad_moment_kernel<W, 2, true> : spread_grad_moment_kernel<W, 2, false>)
+                              : (fused ? spread_grad_moment_kernel<W, 1, true> : spread_grad_moment_kernel<W, 1, false>);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<L.P, 512, smem, st>>>(L, x, w, Dd, H2);
+        return cudaGetLastError();
+    }
     const size_t smem = ((size_t)L.G + SPREAD_PAD + (mode == 2 ? (size_t)L.G : 0)) * sizeof(float);
     auto kern = mode == 2 ? (fused ? spread_grad_kernel<W, 2, true> : spread_grad_kernel<W, 2, false>)
                           : (fused ? spread_grad_kernel<W, 1, true> : spread_grad_kernel<W, 1, false>);
@@ -746,6 +1030,7 @@ cudaError_t qs_launch_weight_scale(const qs_launch& L, const float* w, cudaStrea
 cudaError_t qs_launch_spread(const qs_launch& L, int W, const float* x, const float* w, bool fused,
                              cudaStream_t st)
 {
+    if (!qs_spread_variant_ok(L.G, W, L.spread_variant)) return cudaErrorInvalidValue;
     switch (W) {
         case 6: return launch_spread_w<6>(L, x, w, fused, L.spread_variant, st);
         case 8: return launch_spread_w<8>(L, x, w, fused, L.spread_variant, st);

@@ -30,13 +30,17 @@ constexpr int QS_FUSED_MAX_D = 64;             // largest d of the fused form
 constexpr int QS_GRAD_MAX_D = 32;              // largest d of the gradients
 constexpr int QS_BATCH_MAX_D = 64;             // largest d of a batched problem
 
-// Spread kernel variants (see spread_filter_kernel); chosen per plan by timing.
+// Spread kernel variants, in two families fixed by (G, W): the moment family
+// where its table fits two CTAs per SM, the tap family otherwise.  Within a
+// family the variants give bitwise identical grids and are chosen by timing.
 enum {
-    QS_SPREAD_POINT1 = 0,  // point per thread, one grid
-    QS_SPREAD_POINT2 = 1,  // point per thread, two lane-private grid copies
-    QS_SPREAD_POINT4 = 2,  // point per thread, four copies
-    QS_SPREAD_THREAD32 = 3,  // point per thread, thread-private 32-cell window columns + one grid
-    QS_SPREAD_NVARIANTS = 4
+    QS_SPREAD_POINT1 = 0,       // taps: point per thread, one grid
+    QS_SPREAD_POINT2 = 1,       // taps: two lane-private grid copies
+    QS_SPREAD_POINT4 = 2,       // taps: four copies
+    QS_SPREAD_THREAD32 = 3,     // taps: thread-private 32-cell window columns + one grid
+    QS_SPREAD_MOMENT = 4,       // moments: one bin table
+    QS_SPREAD_MOMENTWIN32 = 5,  // moments: lane-interleaved 32-bin window + the bin table
+    QS_SPREAD_NVARIANTS = 6
 };
 
 // Degree of the tap polynomials: W - 1 from W = 8 on (the tap error is then
@@ -44,6 +48,28 @@ enum {
 __host__ __device__ constexpr int qs_tap_degree(int W) { return W >= 8 ? W - 1 : W + 1; }
 // Terms of each even / odd part (the degree is odd).
 __host__ __device__ constexpr int qs_tap_terms(int W) { return (qs_tap_degree(W) + 1) / 2; }
+
+constexpr int QS_SPREAD_PAD = 16;    // overflow cells of the linear spread grid
+constexpr int QS_MOMENT_WIN = 32;    // bins of the lane-interleaved moment window
+
+// Moments per point of the moment spread: the tap polynomials' degree + 1.
+__host__ __device__ constexpr int qs_moment_count(int W) { return qs_tap_degree(W) + 1; }
+
+// Shared bytes of the moment spread: the bin table ((G + 16) rows of K + 1
+// ints) and the larger of the lane window and the float grid it becomes.
+inline size_t qs_moment_smem(int G, int W, bool window)
+{
+    const size_t K = (size_t)qs_moment_count(W), cs = (size_t)G + QS_SPREAD_PAD;
+    const size_t lw = window ? (size_t)QS_MOMENT_WIN * K * 32 * 4 : 0, grid = cs * 4;
+    return cs * (K + 1) * 4 + (lw > grid ? lw : grid);
+}
+// The moment family is used when both its variants fit two CTAs per SM.
+inline bool qs_spread_moments(int G, int W) { return qs_moment_smem(G, W, true) <= (size_t)113 * 1024; }
+inline int qs_spread_default(int G, int W) { return qs_spread_moments(G, W) ? QS_SPREAD_MOMENT : QS_SPREAD_POINT1; }
+inline bool qs_spread_variant_ok(int G, int W, int v)
+{
+    return v >= 0 && v < QS_SPREAD_NVARIANTS && (v >= QS_SPREAD_MOMENT) == qs_spread_moments(G, W);
+}
 
 // Tap polynomials.  For tap j of the first half (0 <= j < m), with the
 // centred fractional offset s in [-1/2, 1/2]:

@@ -243,6 +243,7 @@ extern "C" qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_
     L.U = nullptr;
     L.part = reinterpret_cast<float*>(base + o_part);
     L.S = (int)S;
+    L.spread_variant = qs_spread_default(G, W);
     L.flag = reinterpret_cast<unsigned int*>(base + o_flag);
     L.wscale = reinterpret_cast<float*>(base + o_wscale);
 

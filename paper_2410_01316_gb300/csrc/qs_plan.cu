@@ -458,6 +458,7 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     p->proj = proj;
     p->W = W;
     p->G = 2 * D.n_ft;
+    p->spread_variant = qs_spread_default(p->G, W);
     p->beta = 2.30 * W;
     p->tau = tau_rule(D.kernel, D.kparam, D.radius);
     p->S_max = D.P < 64 ? D.P : 64;
@@ -816,7 +817,21 @@ qs_status qs_plan_set_variant(qs_plan p, int v)
 {
     if (!p) return fail(QS_ERR_ARG, "qs_plan_set_variant: NULL plan");
     if (v < 0 || v >= QS_SPREAD_NVARIANTS) return fail(QS_ERR_ARG, "qs_plan_set_variant: variant %d out of range", v);
+    if (!qs_spread_variant_ok(p->G, p->W, v))
+        return fail(QS_ERR_ARG, "qs_plan_set_variant: variant %d is not in this plan's family (%s spread for G = %d, W = %d)",
+                    v, qs_spread_moments(p->G, p->W) ? "moment" : "tap", p->G, p->W);
     p->spread_variant = v;
+    return QS_OK;
+}
+
+qs_status qs_plan_variants(qs_plan p, unsigned int* available, int* current)
+{
+    if (!p) return fail(QS_ERR_ARG, "qs_plan_variants: NULL plan");
+    unsigned int mask = 0;
+    for (int v = 0; v < QS_SPREAD_NVARIANTS; ++v)
+        if (qs_spread_variant_ok(p->G, p->W, v)) mask |= 1u << v;
+    if (available) *available = mask;
+    if (current) *current = p->spread_variant;
     return QS_OK;
 }
 
@@ -839,9 +854,10 @@ qs_status qs_plan_autotune(qs_plan p, const float* x, int64_t N, const float* w,
         cudaEventDestroy(e0);
         return fail(QS_ERR_CUDA, "qs_plan_autotune: event");
     }
-    int best = 0;
+    int best = qs_spread_default(p->G, p->W);
     float best_ms = 3.4e38f;
     for (int v = 0; v < QS_SPREAD_NVARIANTS && e == cudaSuccess; ++v) {
+        if (!qs_spread_variant_ok(p->G, p->W, v)) continue;
         L.spread_variant = v;
         e = qs_launch_spread(L, p->W, x, w, fused, st);  // warm-up
         float vbest = 3.4e38f;
