@@ -224,7 +224,11 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
-    spread_variant = plan.autotune(x, w)
+    if args.spread_variant:
+        plan.set_variant(args.spread_variant)
+        spread_variant = args.spread_variant
+    else:
+        spread_variant = plan.autotune(x, w)
     for _ in range(args.warmup):
         plan.sum(x, w, y, out=s)
     plan.check()
@@ -670,6 +674,7 @@ def main():
     ap.add_argument("--P", type=int, default=0, help="override the number of slices (profiling small cases)")
     ap.add_argument("--N", type=int, default=0, help="override N = M (profiling small cases)")
     ap.add_argument("--no-error-check", action="store_true")
+    ap.add_argument("--spread-variant", default="", help="fix the spread variant instead of timing the family")
     ap.add_argument("--error-targets", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-slices", type=int, default=128)
