@@ -553,6 +553,21 @@ def launches_per_step(plan) -> int:
     return 6 if plan.proj == "fp32" else 4
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the d = 784, N = M = 60000 shape at
+# P = 1024 (profiles/kernels_mnist_laplace_p1024.md); every term streams per slice, so a launch at
+# P slices moves P / 1024 times as much.  Only for that shape and the kernels as captured.
+TRAFFIC_MNIST_P1024 = {"project_x": 398.5e6, "project_y": 399.1e6, "spread_filter": 253.5e6, "interp": 262.3e6}
+
+
+def _traffic(prob, plan, name):
+    if prob.d != 784 or prob.N != 60000 or prob.M != 60000 or plan.proj != "bf16x3" or prob.n_ft != 1024:
+        return None
+    if name == "spread_filter" and plan.variant() != "momentwin32":
+        return None
+    b = TRAFFIC_MNIST_P1024.get(name)
+    return None if b is None else b * prob.P / 1024
+
+
 def stage_rooflines(prob, plan, stages, clocks, peaks, peak_src, sm_count):
     """Roofline entry per stage, from the in-stream stage events (ms)."""
     mhz = clocks.get("sm_mhz") or 2070.0
@@ -563,7 +578,8 @@ def stage_rooflines(prob, plan, stages, clocks, peaks, peak_src, sm_count):
 
     def add(name, bound, achieved, peak, unit, what, source):
         out[name] = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": achieved / peak if peak else None, "traffic": None, "algorithmic": what,
+                     "frac": achieved / peak if peak else None, "traffic": _traffic(prob, plan, name),
+                     "algorithmic": what,
                      "peak_source": source, "ms": stages[name]}
 
     for name, rows in (("project_x", N), ("project_y", M)):
