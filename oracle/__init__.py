@@ -25,7 +25,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KERNEL_IDS = {"gauss": 0, "laplace": 1, "negdist": 2}
+KERNEL_IDS = {"gauss": 0, "laplace": 1, "negdist": 2, "matern": 3, "riesz": 4, "tps": 5}
 
 
 def build(force: bool = False) -> str:
@@ -51,6 +51,22 @@ def _load():
             lib.o_tau.argtypes = [i, d, d]
             lib.o_riesz_const.restype = d
             lib.o_riesz_const.argtypes = [i]
+            lib.o_riesz_const_r.restype = d
+            lib.o_riesz_const_r.argtypes = [i, d]
+            lib.o_tps_const.restype = d
+            lib.o_tps_const.argtypes = [i]
+            lib.o_F2.restype = d
+            lib.o_F2.argtypes = [i, d, d, d]
+            lib.o_f2.restype = d
+            lib.o_f2.argtypes = [i, d, d, i, d]
+            lib.o_fhat2.restype = d
+            lib.o_fhat2.argtypes = [i, d, d, i, d]
+            lib.o_coeffs2.restype = i
+            lib.o_coeffs2.argtypes = [i, d, d, i, d, i, p]
+            lib.o2_exact2.restype = i
+            lib.o2_exact2.argtypes = [i, d, d, i, i64, p, p, i64, p, p, i]
+            lib.o3_sliced2.restype = i
+            lib.o3_sliced2.argtypes = [i, d, d, i, i64, p, p, i64, p, i, p, p, i]
             lib.o_F.restype = d
             lib.o_F.argtypes = [i, d, d]
             lib.o_f.restype = d
@@ -100,30 +116,39 @@ def tau(kernel: str, kparam: float, R: float) -> float:
     return float(_load().o_tau(_kid(kernel), float(kparam), float(R)))
 
 
-def riesz_const(d: int) -> float:
-    """c_d with f(t) = -c_d |t| for F(r) = -r (Table tab:kernels, Riesz r=1)."""
-    return float(_load().o_riesz_const(int(d)))
+def riesz_const(d: int, r: float = 1.0) -> float:
+    """c_{d,r} with f(t) = -c_{d,r} |t|^r for F(x) = -x^r (Table tab:kernels, Riesz row)."""
+    if r == 1.0:
+        return float(_load().o_riesz_const(int(d)))
+    return float(_load().o_riesz_const_r(int(d), float(r)))
 
 
-def F(kernel: str, kparam: float, r: float) -> float:
-    return float(_load().o_F(_kid(kernel), float(kparam), float(r)))
+def tps_const(d: int) -> float:
+    """C_d with f(t) = d t^2 log|t| + C_d t^2 for F(x) = x^2 log x (Table tab:kernels)."""
+    return float(_load().o_tps_const(int(d)))
 
 
-def f(kernel: str, kparam: float, d: int, t: float) -> float:
-    """Closed-form 1D basis function (d=1, d=3, or negative distance)."""
-    return float(_load().o_f(_kid(kernel), float(kparam), int(d), float(t)))
+def F(kernel: str, kparam: float, r: float, nu: float = 0.0) -> float:
+    """Radial basis function (Table tab:kernels); Matern takes beta = kparam, nu (half-integers)."""
+    return float(_load().o_F2(_kid(kernel), float(kparam), float(nu), float(r)))
 
 
-def fhat(kernel: str, kparam: float, d: int, omega: float) -> float:
+def f(kernel: str, kparam: float, d: int, t: float, nu: float = 0.0) -> float:
+    """Closed-form 1D basis function (d=1, d=3, or the negative distance, Riesz and thin plate
+    spline kernels in any d)."""
+    return float(_load().o_f2(_kid(kernel), float(kparam), float(nu), int(d), float(t)))
+
+
+def fhat(kernel: str, kparam: float, d: int, omega: float, nu: float = 0.0) -> float:
     """F_1[f(|.|)](omega) (Table tab:kernels, corrected constants)."""
-    return float(_load().o_fhat(_kid(kernel), float(kparam), int(d), float(omega)))
+    return float(_load().o_fhat2(_kid(kernel), float(kparam), float(nu), int(d), float(omega)))
 
 
-def coeffs(kernel: str, kparam: float, d: int, tau_: float, n_ft: int) -> np.ndarray:
+def coeffs(kernel: str, kparam: float, d: int, tau_: float, n_ft: int, nu: float = 0.0) -> np.ndarray:
     """c_k for k = -n_ft/2 .. n_ft/2-1 (App. C Step 2; App. G)."""
     c = np.zeros(n_ft, dtype=np.float64)
-    _check(_load().o_coeffs(_kid(kernel), float(kparam), int(d), float(tau_), int(n_ft),
-                            _ptr(c)), "coeffs")
+    _check(_load().o_coeffs2(_kid(kernel), float(kparam), float(nu), int(d), float(tau_), int(n_ft),
+                             _ptr(c)), "coeffs")
     return c
 
 
@@ -164,27 +189,28 @@ def o1_grad(x, w, y, v, xi, tau_: float, c: np.ndarray, idx_n=None, idx_m=None,
     return {"x": gx, "w": gw, "y": gy}
 
 
-def o2_exact(kernel: str, kparam: float, x, w, y, threads: int = 0) -> np.ndarray:
+def o2_exact(kernel: str, kparam: float, x, w, y, threads: int = 0, nu: float = 0.0) -> np.ndarray:
     """Exact kernel sum s_m = sum_n w_n F(|x_n - y_m|) (eq. kernel_sum)."""
     x, y, w = _f32(x), _f32(y), _f32(w)
     s = np.zeros(y.shape[0], dtype=np.float64)
-    _check(_load().o2_exact(_kid(kernel), float(kparam), x.shape[1], x.shape[0], _ptr(x), _ptr(w),
-                            y.shape[0], _ptr(y), _ptr(s), int(threads)), "o2_exact")
+    _check(_load().o2_exact2(_kid(kernel), float(kparam), float(nu), x.shape[1], x.shape[0], _ptr(x),
+                             _ptr(w), y.shape[0], _ptr(y), _ptr(s), int(threads)), "o2_exact")
     return s
 
 
-def o3_sliced(kernel: str, kparam: float, x, w, y, xi, threads: int = 0) -> np.ndarray:
+def o3_sliced(kernel: str, kparam: float, x, w, y, xi, threads: int = 0, nu: float = 0.0) -> np.ndarray:
     """Sliced sum with closed-form f, no Fourier step (eq. kernel_sum_sliced)."""
     x, y, w, xi = _f32(x), _f32(y), _f32(w), _f32(xi)
     s = np.zeros(y.shape[0], dtype=np.float64)
-    _check(_load().o3_sliced(_kid(kernel), float(kparam), x.shape[1], x.shape[0], _ptr(x), _ptr(w),
-                             y.shape[0], _ptr(y), xi.shape[0], _ptr(xi), _ptr(s), int(threads)),
+    _check(_load().o3_sliced2(_kid(kernel), float(kparam), float(nu), x.shape[1], x.shape[0], _ptr(x),
+                              _ptr(w), y.shape[0], _ptr(y), xi.shape[0], _ptr(xi), _ptr(s), int(threads)),
            "o3_sliced")
     return s
 
 
 def o1_problem(prob, threads: int = 0, y=None) -> np.ndarray:
     """O1 for a workloads.Problem (optionally on a subset of targets y)."""
+    nu = getattr(prob, "kparam2", 0.0)
     t = tau(prob.kernel, prob.kparam, prob.R)
-    c = coeffs(prob.kernel, prob.kparam, prob.d, t, prob.n_ft)
+    c = coeffs(prob.kernel, prob.kparam, prob.d, t, prob.n_ft, nu=nu)
     return o1_sum(prob.x, prob.w, prob.y if y is None else y, prob.xi, t, c, threads)

@@ -15,6 +15,8 @@
  * Contents (each function names the passage it follows):
  *   o_tau          rescaling factor tau               (App. C "Step 1"; App. G, eq. radius_xy)
  *   o_riesz_const  constant of the sliced Riesz r=1   (Table tab:kernels, Riesz row)
+ *   o_riesz_const_r  the same for any r > -1           (Table tab:kernels, Riesz row)
+ *   o_tps_const    C_d of the sliced thin plate spline (Table tab:kernels, Thin Plate Spline row)
  *   o_f            1D basis function f, closed forms  (Table tab:kernels; Sec. 2, eq. integral_transform)
  *   o_F            radial basis function F            (Table tab:kernels)
  *   o_fhat         1D Fourier transform of f(|.|)     (Table tab:kernels with the corrected constants)
@@ -37,6 +39,17 @@
  *     whose Fourier coefficients are known in closed form.
  *   - The kept frequencies are k = -N_ft/2 .. N_ft/2-1 (App. C, Step 2), and
  *     the one-dimensional sums take the real part.
+ *   - Matern (nu = kp2, beta = kp): f-hat from the same relation, which is the
+ *     last column of Table tab:kernels; tau = min(0.2 / R, 1 / (2 * 5 beta))
+ *     (App. C, Step 1: T = 0.2, g_max = 5 beta).
+ *   - Generalised Riesz F = -x^r (0 < r < 2, r = kp) and the thin plate spline
+ *     F = x^2 log x have no classical Fourier transform (App. A); like the
+ *     negative distance kernel they use the 1-periodic continuation of
+ *     g(t) = f(|t| / tau) on [-1/2, 1/2) with tau = 1/(2R), whose coefficients
+ *     are the integrals c_k = 2 int_0^{1/2} g(t) cos(2 pi k t) dt, computed here
+ *     by Gauss-Legendre quadrature on half-period panels.
+ *   - H_{d/2} in C_d is the harmonic number at d/2 (digamma(d/2 + 1) + Euler's
+ *     constant), so C_3 = 1 and f(t) = 3 t^2 log|t| + t^2 for d = 3.
  */
 #include <math.h>
 #include <stdint.h>
@@ -50,6 +63,9 @@
 #define O_GAUSS 0
 #define O_LAPLACE 1
 #define O_NEGDIST 2
+#define O_MATERN 3
+#define O_RIESZ 4
+#define O_TPS 5
 
 #define O_OK 0
 #define O_EARG (-1)
@@ -67,6 +83,12 @@ static const double O_PI = 3.14159265358979323846264338327950288;
 double o_tau(int kernel, double kparam, double R)
 {
     if (!(R > 0.0)) return -1.0;
+    if (kernel == O_MATERN) {
+        double gmax = 5.0 * kparam;
+        double t1 = 0.2 / R, t2 = 1.0 / (2.0 * gmax);
+        return t1 < t2 ? t1 : t2;
+    }
+    if (kernel == O_RIESZ || kernel == O_TPS) return 1.0 / (2.0 * R);
     if (kernel == O_GAUSS) {
         double gmax = 5.0 * kparam;
         double t1 = 0.3 / R, t2 = 1.0 / (2.0 * gmax);
@@ -88,14 +110,69 @@ double o_riesz_const(int d)
     return exp(0.5 * log(O_PI) + lgamma(0.5 * (d + 1)) - lgamma(0.5 * d));
 }
 
-/* Radial basis function F (Table tab:kernels). */
-double o_F(int kernel, double kparam, double r)
+/* Generalised Riesz F(x) = -x^r (Table tab:kernels):                      */
+/* f(x) = -sqrt(pi) Gamma((d+r)/2) / (Gamma(d/2) Gamma((r+1)/2)) |x|^r.    */
+double o_riesz_const_r(int d, double r)
+{
+    return exp(0.5 * log(O_PI) + lgamma(0.5 * (d + r)) - lgamma(0.5 * d) - lgamma(0.5 * (r + 1.0)));
+}
+
+/* Thin plate spline (Table tab:kernels): C_d = d/2 (H_{d/2} - 2 + log 4), */
+/* H_{d/2} by H_0 = 0, H_{1/2} = 2 - 2 log 2 and H_{x+1} = H_x + 1/(x+1).  */
+double o_tps_const(int d)
+{
+    double h = (d % 2 == 0) ? 0.0 : 2.0 - 2.0 * log(2.0);
+    double x = (d % 2 == 0) ? 0.0 : 0.5;
+    while (x + 0.25 < 0.5 * d) {
+        x += 1.0;
+        h += 1.0 / x;
+    }
+    return 0.5 * d * (h - 2.0 + log(4.0));
+}
+
+/* Matern with nu = p + 1/2 (p = 0, 1, 2, ...): F(x) = e^{-a x} sum_{i<=p}  */
+/* p!/(2p)! (p+i)!/(i!(p-i)!) (2 a x)^{p-i}, a = sqrt(2 nu)/beta.  Writes  */
+/* the coefficients q_j of F(x) = e^{-a x} sum_j q_j x^j; returns p, or -1  */
+/* if nu is not a half-integer (no closed form here).                       */
+static int matern_poly(double beta, double nu, double* a_out, double q[16])
+{
+    double pd = nu - 0.5;
+    int p = (int)llround(pd);
+    if (p < 0 || p > 14 || fabs(pd - p) > 1e-12) return -1;
+    double a = sqrt(2.0 * nu) / beta;
+    for (int j = 0; j < 16; ++j) q[j] = 0.0;
+    double lf_p = lgamma(p + 1.0), lf_2p = lgamma(2.0 * p + 1.0);
+    for (int i = 0; i <= p; ++i) {
+        int j = p - i;
+        double lc = lf_p - lf_2p + lgamma(p + i + 1.0) - lgamma(i + 1.0) - lgamma(j + 1.0);
+        q[j] = exp(lc) * pow(2.0 * a, (double)j);
+    }
+    *a_out = a;
+    return p;
+}
+
+/* Radial basis function F (Table tab:kernels).  Matern: kp = beta, kp2 =  */
+/* nu (half-integers only); Riesz: kp = r.                                  */
+double o_F2(int kernel, double kparam, double kp2, double r)
 {
     if (kernel == O_GAUSS) return exp(-r * r / (2.0 * kparam * kparam));
     if (kernel == O_LAPLACE) return exp(-kparam * r);
     if (kernel == O_NEGDIST) return -r;
+    if (kernel == O_RIESZ) return -pow(r, kparam);
+    if (kernel == O_TPS) return r > 0.0 ? r * r * log(r) : 0.0;
+    if (kernel == O_MATERN) {
+        double a, q[16];
+        int p = matern_poly(kparam, kp2, &a, q);
+        if (p < 0) return NAN;
+        double e = exp(-a * r), acc = 0.0;
+        if (e == 0.0) return 0.0; /* far tail: the polynomial may overflow */
+        for (int j = p; j >= 0; --j) acc = acc * r + q[j];
+        return e * acc;
+    }
     return NAN;
 }
+
+double o_F(int kernel, double kparam, double r) { return o_F2(kernel, kparam, 0.0, r); }
 
 /* One-dimensional basis function f in closed form where one exists:        */
 /*  d = 1: f = F;                                                           */
@@ -103,11 +180,24 @@ double o_F(int kernel, double kparam, double r)
 /*         F(t) = int_0^1 f(ts) ds for d = 3;                                */
 /*  negative distance, any d: f(t) = -c_d |t| (Riesz row, r = 1).           */
 /* Returns NAN where no closed form is implemented.                         */
-double o_f(int kernel, double kparam, int d, double t)
+double o_f2(int kernel, double kparam, double kp2, int d, double t)
 {
     t = fabs(t);
     if (kernel == O_NEGDIST) return -o_riesz_const(d) * t;
-    if (d == 1) return o_F(kernel, kparam, t);
+    if (kernel == O_RIESZ) return -o_riesz_const_r(d, kparam) * pow(t, kparam);
+    if (kernel == O_TPS) return t > 0.0 ? d * t * t * log(t) + o_tps_const(d) * t * t : 0.0;
+    if (d == 1) return o_F2(kernel, kparam, kp2, t);
+    if (d == 3 && kernel == O_MATERN) {
+        /* (t F)' = e^{-a t} (P + t P' - a t P) for F = e^{-a t} P */
+        double a, q[16];
+        int p = matern_poly(kparam, kp2, &a, q);
+        if (p < 0) return NAN;
+        double P0 = 0.0, P1 = 0.0;
+        if (exp(-a * t) == 0.0) return 0.0;
+        for (int j = p; j >= 0; --j) P0 = P0 * t + q[j];
+        for (int j = p; j >= 1; --j) P1 = P1 * t + j * q[j];
+        return exp(-a * t) * (P0 + t * P1 - a * t * P0);
+    }
     if (d == 3) {
         if (kernel == O_GAUSS) {
             double s2 = kparam * kparam;
@@ -118,15 +208,27 @@ double o_f(int kernel, double kparam, int d, double t)
     return NAN;
 }
 
+double o_f(int kernel, double kparam, int d, double t) { return o_f2(kernel, kparam, 0.0, d, t); }
+
 /* F_1[f(|.|)](omega), evaluated in log space (|omega|^{d-1} and Gamma     */
 /* overflow separately for d in the hundreds).                             */
 /*  Gauss:   sqrt(2) pi sigma (2 pi^2 sigma^2 w^2)^{(d-1)/2}                */
 /*           exp(-2 pi^2 sigma^2 w^2) / Gamma(d/2)                          */
 /*  Laplace: Gamma((d+1)/2) 2^d pi^{d-1/2} |w|^{d-1} / (Gamma(d/2) alpha^d) */
 /*           (1 + 4 pi^2 w^2 / alpha^2)^{-(d+1)/2}                          */
-double o_fhat(int kernel, double kparam, int d, double omega)
+/*  Matern:  Gamma(nu + d/2) 2^{d/2} pi^d beta^d |w|^{d-1}                 */
+/*           / (Gamma(d/2) Gamma(nu) nu^{d/2}) (1 + 2 pi^2 beta^2 w^2/nu)^{-(nu+d/2)} */
+double o_fhat2(int kernel, double kparam, double kp2, int d, double omega)
 {
     double aw = fabs(omega);
+    if (kernel == O_MATERN) {
+        double be = kparam, nu = kp2;
+        if (aw == 0.0 && d > 1) return 0.0;
+        double lg = lgamma(nu + 0.5 * d) + 0.5 * d * log(2.0) + d * log(O_PI) + d * log(be)
+                    + (d > 1 ? (d - 1) * log(aw) : 0.0) - lgamma(0.5 * d) - lgamma(nu) - 0.5 * d * log(nu)
+                    - (nu + 0.5 * d) * log1p(2.0 * O_PI * O_PI * be * be * aw * aw / nu);
+        return exp(lg);
+    }
     if (kernel == O_GAUSS) {
         double sig = kparam;
         double q = 2.0 * O_PI * O_PI * sig * sig * aw * aw;
@@ -146,20 +248,95 @@ double o_fhat(int kernel, double kparam, int d, double omega)
     return NAN;
 }
 
+double o_fhat(int kernel, double kparam, int d, double omega) { return o_fhat2(kernel, kparam, 0.0, d, omega); }
+
+/* ---------------------------------------------------------------------- */
+/* 2 int_0^{1/2} g(t) cos(2 pi k t) dt for the periodised kernels, by      */
+/* 20-point Gauss-Legendre on the half-periods of the cosine, the first    */
+/* one graded geometrically towards the |t|^r or t^2 log t point t = 0.    */
+/* ---------------------------------------------------------------------- */
+#define O_GL 20
+static double o_gl_x[O_GL], o_gl_w[O_GL];
+static int o_gl_ready = 0;
+
+static void o_gl_init(void)
+{
+    if (o_gl_ready) return;
+    for (int i = 0; i < O_GL; ++i) {
+        double z = cos(O_PI * (i + 0.75) / (O_GL + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = 0.0;
+            for (int j = 1; j <= O_GL; ++j) {
+                double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+            }
+            dp = O_GL * (z * p0 - p1) / (z * z - 1.0);
+            double dz = p0 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        o_gl_x[i] = z;
+        o_gl_w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+    o_gl_ready = 1;
+}
+
+/* g(t) for t in (0, 1/2], i.e. f(t / tau) */
+static double o_gper(int kernel, double kparam, int d, double tau, double t)
+{
+    return o_f2(kernel, kparam, 0.0, d, t / tau);
+}
+
+static double o_panel(int kernel, double kparam, int d, double tau, int k, double a, double b)
+{
+    double m = 0.5 * (a + b), h = 0.5 * (b - a), acc = 0.0;
+    for (int i = 0; i < O_GL; ++i) {
+        double t = m + h * o_gl_x[i];
+        acc += o_gl_w[i] * o_gper(kernel, kparam, d, tau, t) * cos(2.0 * O_PI * k * t);
+    }
+    return acc * h;
+}
+
+static double o_periodic_coeff(int kernel, double kparam, int d, double tau, int k)
+{
+    int ak = k < 0 ? -k : k;
+    int npan = ak < 1 ? 1 : ak; /* half-periods of cos(2 pi k t) on [0, 1/2] */
+    double hw = 0.5 / npan, acc = 0.0;
+    for (int j = 1; j < npan; ++j) acc += o_panel(kernel, kparam, d, tau, ak, j * hw, (j + 1) * hw);
+    double b = hw; /* first panel, graded: [hw/2^{l+1}, hw/2^l], l = 0..59 */
+    for (int l = 0; l < 60; ++l) {
+        acc += o_panel(kernel, kparam, d, tau, ak, 0.5 * b, b);
+        b *= 0.5;
+    }
+    return 2.0 * acc;
+}
+
 /* Fourier coefficients c_k, k = -nft/2 .. nft/2-1, stored at c[k + nft/2]. */
 /*  Gauss / Laplace (App. C, Step 2): c_k = F_1[g~](k) = tau f-hat(tau k),  */
 /*  with g~(x) = f(|x| / tau) (Poisson summation, g~ ~ 0 outside [-1/2,1/2]).*/
 /*  Negative distance (App. G): g~ is the 1-periodic triangle wave          */
 /*  -(c_d / tau)|t| on [-1/2, 1/2); its coefficients are                    */
 /*  c_0 = -(c_d/tau)/4,  c_k = (c_d/tau) / (pi^2 k^2) for odd k, 0 else.    */
-int o_coeffs(int kernel, double kparam, int d, double tau, int nft, double* c)
+/*  Matern: tau f-hat(tau k) as for Gauss / Laplace.  Riesz and thin plate */
+/*  spline: the integrals of the periodised g~ above (c_{-k} = c_k).        */
+int o_coeffs2(int kernel, double kparam, double kp2, int d, double tau, int nft, double* c)
 {
     if (nft < 2 || (nft & 1) || !(tau > 0.0) || d < 1 || !c) return O_EARG;
     int K = nft / 2;
+    if (kernel == O_RIESZ || kernel == O_TPS) {
+        o_gl_init();
+        for (int k = 0; k <= K; ++k) {
+            double v = o_periodic_coeff(kernel, kparam, d, tau, k);
+            if (k < K) c[k + K] = v;
+            c[K - k] = v;
+        }
+        return O_OK;
+    }
     for (int k = -K; k < K; ++k) {
         double v;
-        if (kernel == O_GAUSS || kernel == O_LAPLACE) {
-            v = tau * o_fhat(kernel, kparam, d, tau * (double)k);
+        if (kernel == O_GAUSS || kernel == O_LAPLACE || kernel == O_MATERN) {
+            v = tau * o_fhat2(kernel, kparam, kp2, d, tau * (double)k);
         } else if (kernel == O_NEGDIST) {
             double amp = o_riesz_const(d) / tau;
             if (k == 0) v = -amp / 4.0;
@@ -171,6 +348,11 @@ int o_coeffs(int kernel, double kparam, int d, double tau, int nft, double* c)
         c[k + K] = v;
     }
     return O_OK;
+}
+
+int o_coeffs(int kernel, double kparam, int d, double tau, int nft, double* c)
+{
+    return o_coeffs2(kernel, kparam, 0.0, d, tau, nft, c);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -442,11 +624,11 @@ int o1_grad(int d, int64_t N, const float* x, const float* w, int64_t M, const f
 /* ---------------------------------------------------------------------- */
 /* O2: exact kernel sum s_m = sum_n w_n F(|x_n - y_m|)  (eq. kernel_sum)    */
 /* ---------------------------------------------------------------------- */
-int o2_exact(int kernel, double kparam, int d, int64_t N, const float* x, const float* w,
-             int64_t M, const float* y, double* s, int nthreads)
+int o2_exact2(int kernel, double kparam, double kp2, int d, int64_t N, const float* x, const float* w,
+              int64_t M, const float* y, double* s, int nthreads)
 {
     if (d < 1 || N < 0 || M < 0 || !s) return O_EARG;
-    if (kernel != O_GAUSS && kernel != O_LAPLACE && kernel != O_NEGDIST) return O_EUNSUPPORTED;
+    if (isnan(o_F2(kernel, kparam, kp2, 0.5))) return O_EUNSUPPORTED;
 #pragma omp parallel for schedule(static) num_threads(n_threads(nthreads))
     for (int64_t m = 0; m < M; ++m) {
         double acc = 0.0;
@@ -456,11 +638,17 @@ int o2_exact(int kernel, double kparam, int d, int64_t N, const float* x, const 
                 double diff = (double)x[(size_t)n * d + j] - (double)y[(size_t)m * d + j];
                 r2 += diff * diff;
             }
-            acc += (w ? (double)w[n] : 1.0) * o_F(kernel, kparam, sqrt(r2));
+            acc += (w ? (double)w[n] : 1.0) * o_F2(kernel, kparam, kp2, sqrt(r2));
         }
         s[m] = acc;
     }
     return O_OK;
+}
+
+int o2_exact(int kernel, double kparam, int d, int64_t N, const float* x, const float* w,
+             int64_t M, const float* y, double* s, int nthreads)
+{
+    return o2_exact2(kernel, kparam, 0.0, d, N, x, w, M, y, s, nthreads);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -468,11 +656,11 @@ int o2_exact(int kernel, double kparam, int d, int64_t N, const float* x, const 
 /*   s_m = (1/P) sum_p sum_n w_n f(|<xi_p, x_n - y_m>|)  (eq. kernel_sum_sliced) */
 /* No Fourier step.  Available where o_f has a closed form.                */
 /* ---------------------------------------------------------------------- */
-int o3_sliced(int kernel, double kparam, int d, int64_t N, const float* x, const float* w,
-              int64_t M, const float* y, int P, const float* xi, double* s, int nthreads)
+int o3_sliced2(int kernel, double kparam, double kp2, int d, int64_t N, const float* x, const float* w,
+               int64_t M, const float* y, int P, const float* xi, double* s, int nthreads)
 {
     if (d < 1 || N < 0 || M < 0 || P < 1 || !s || !xi) return O_EARG;
-    if (isnan(o_f(kernel, kparam, d, 0.5))) return O_EUNSUPPORTED;
+    if (isnan(o_f2(kernel, kparam, kp2, d, 0.5))) return O_EUNSUPPORTED;
 #pragma omp parallel for schedule(static) num_threads(n_threads(nthreads))
     for (int64_t m = 0; m < M; ++m) {
         double tot = 0.0;
@@ -482,11 +670,17 @@ int o3_sliced(int kernel, double kparam, int d, int64_t N, const float* x, const
             double acc = 0.0;
             for (int64_t n = 0; n < N; ++n) {
                 double an = dot_fd(x + (size_t)n * d, xp, d);
-                acc += (w ? (double)w[n] : 1.0) * o_f(kernel, kparam, d, an - bm);
+                acc += (w ? (double)w[n] : 1.0) * o_f2(kernel, kparam, kp2, d, an - bm);
             }
             tot += acc;
         }
         s[m] = tot / (double)P;
     }
     return O_OK;
+}
+
+int o3_sliced(int kernel, double kparam, int d, int64_t N, const float* x, const float* w,
+              int64_t M, const float* y, int P, const float* xi, double* s, int nthreads)
+{
+    return o3_sliced2(kernel, kparam, 0.0, d, N, x, w, M, y, P, xi, s, nthreads);
 }

@@ -165,8 +165,8 @@ def radius(x: np.ndarray, y: np.ndarray) -> float:
 class Problem:
     name: str
     d: int
-    kernel: str            # "gauss" | "laplace" | "negdist"
-    kparam: float          # sigma (gauss), alpha (laplace), unused (negdist)
+    kernel: str            # "gauss" | "laplace" | "negdist" | "matern" | "riesz" | "tps"
+    kparam: float          # sigma (gauss), alpha (laplace), beta (matern), r (riesz), unused otherwise
     P: int
     n_ft: int
     x: np.ndarray          # (N, d) float32
@@ -176,6 +176,7 @@ class Problem:
     R: float               # radius bound used for the rescaling
     window: int = 8
     meta: dict = field(default_factory=dict)
+    kparam2: float = 0.0   # nu (matern), unused otherwise
 
     @property
     def N(self) -> int:
@@ -235,11 +236,21 @@ def mmd_flow16(N: int = 100000, M: int = 100000, P: int = 1024, n_ft: int = 1024
 
 
 def tiny(d: int, N: int, M: int, P: int, kernel: str, kparam: float, n_ft: int,
-         seed: int, dirs: str = "iid", scale: float = 1.0) -> Problem:
+         seed: int, dirs: str = "iid", scale: float = 1.0, kparam2: float = 0.0) -> Problem:
     """Small random problem for unit and parity tests."""
     rng = np.random.default_rng(seed)
     x = gaussian(rng, N, d, scale)
     y = gaussian(rng, M, d, scale)
     w = rng.standard_normal(N).astype(np.float32)
     xi = make_directions(dirs, P, d, seed + 7)
-    return Problem(f"tiny_d{d}", d, kernel, kparam, P, n_ft, x, w, y, xi, radius(x, y))
+    return Problem(f"tiny_d{d}", d, kernel, kparam, P, n_ft, x, w, y, xi, radius(x, y), kparam2=kparam2)
+
+
+def mnist_matern(N: int = 60000, M: int = 60000, P: int = 2048, n_ft: int = 512, d: int = 784,
+                 nu: float = 1.5, seed: int = SEED_BASE + 2) -> Problem:
+    """The MNIST-shaped d=784 inputs with the Matern kernel (nu = 3/2 or 7/2, beta by the median
+    rule, N_ft = 512 as for the paper's Matern runs)."""
+    base = mnist_laplace(N, M, P, 1024, d, seed)
+    med = base.meta["median"]
+    return Problem(f"mnist_matern{int(2 * nu)}", d, "matern", med, P, n_ft, base.x, base.w, base.y, base.xi,
+                   base.R, meta={"median": med}, kparam2=nu)
