@@ -553,19 +553,18 @@ def launches_per_step(plan) -> int:
     return 6 if plan.proj == "fp32" else 4
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of the d = 784, N = M = 60000 shape at
-# P = 1024 (profiles/kernels_mnist_laplace_p1024.md); every term streams per slice, so a launch at
-# P slices moves P / 1024 times as much.  Only for that shape and the kernels as captured.
-TRAFFIC_MNIST_P1024 = {"project_x": 398.5e6, "project_y": 399.1e6, "spread_filter": 253.5e6, "interp": 262.3e6}
+# DRAM bytes (read + write) per launch from one ncu capture of the default workload itself
+# (d = 784, N = M = 60000, P = 2048, N_ft = 1024, BF16x3, momentwin32 spread;
+# profiles/traffic_mnist_laplace.md).  Only for that configuration and the kernels as captured.
+TRAFFIC_MNIST = {"project_x": 639.3e6, "project_y": 636.2e6, "spread_filter": 504.3e6, "interp": 515.7e6}
 
 
 def _traffic(prob, plan, name):
-    if prob.d != 784 or prob.N != 60000 or prob.M != 60000 or plan.proj != "bf16x3" or prob.n_ft != 1024:
+    if (prob.d, prob.N, prob.M, prob.P, prob.n_ft, plan.proj) != (784, 60000, 60000, 2048, 1024, "bf16x3"):
         return None
     if name == "spread_filter" and plan.variant() != "momentwin32":
         return None
-    b = TRAFFIC_MNIST_P1024.get(name)
-    return None if b is None else b * prob.P / 1024
+    return TRAFFIC_MNIST.get(name)
 
 
 def stage_rooflines(prob, plan, stages, clocks, peaks, peak_src, sm_count):

@@ -59,7 +59,11 @@ typedef enum {
 typedef enum {
     QS_GAUSS = 0,   /* F(r) = exp(-r^2 / (2 sigma^2)),  kparam = sigma */
     QS_LAPLACE = 1, /* F(r) = exp(-alpha r),            kparam = alpha */
-    QS_NEGDIST = 2  /* F(r) = -r (Riesz r = 1),          kparam unused  */
+    QS_NEGDIST = 2, /* F(r) = -r (Riesz r = 1),          kparam unused  */
+    QS_MATERN = 3,  /* F(r) = 2^{1-nu}/Gamma(nu) (sqrt(2 nu) r/beta)^nu K_nu(sqrt(2 nu) r/beta),
+                       kparam = beta > 0, kparam2 = nu > 0 */
+    QS_RIESZ = 4,   /* F(r) = -r^q (generalised Riesz), kparam = q in (0, 2) */
+    QS_TPS = 5      /* F(r) = r^2 log r (thin plate spline), kparam unused */
 } qs_kernel;
 
 /* Direction designs (Sec. 4.1, "QMC Sequences"). */
@@ -82,7 +86,7 @@ typedef enum {
 typedef struct {
     int d;                 /* dimension, >= 1 */
     qs_kernel kernel;
-    double kparam;         /* sigma (Gauss), alpha (Laplace); ignored for QS_NEGDIST */
+    double kparam;         /* sigma (Gauss), alpha (Laplace), beta (Matern), q (Riesz); else ignored */
     int P;                 /* number of slices, >= 1 */
     qs_dirs dirs;
     uint64_t seed;         /* seed for QS_DIR_ORTHOGONAL / QS_DIR_IID */
@@ -93,13 +97,18 @@ typedef struct {
     double radius;         /* R >= max|x_n| + max|y_m| (App. G, eq. radius_xy), > 0 */
     qs_proj proj;
     int64_t max_n, max_m;  /* largest N and M the plan will be called with */
+    double kparam2;        /* nu (Matern); else ignored */
 } qs_plan_desc;
 
 /*
- * Create a plan: the rescaling factor tau (App. C Step 1 for Gauss / Laplace:
- * tau = min(T/R, 1/(2 g_max)); App. G for the negative distance: tau =
- * 1/(2R)), the directions, the Fourier coefficients c_k in FP64 on the device
- * (App. C Step 2), the window tables, and all device workspace.  Runs on the
+ * Create a plan: the rescaling factor tau (App. C Step 1 for Gauss / Laplace /
+ * Matern: tau = min(T/R, 1/(2 g_max)) with T = 0.3 / 0.1 / 0.2; App. G for the
+ * negative distance, generalised Riesz and thin plate spline kernels: tau =
+ * 1/(2R)), the directions, the Fourier coefficients c_k in FP64 (App. C Step 2:
+ * closed-form transforms on the device for Gauss / Laplace / Matern / negative
+ * distance; for Riesz and the thin plate spline, which have no classical
+ * transform, the integrals of the periodised 1D function over one period by
+ * host quadrature), the window tables, and all device workspace.  Runs on the
  * current CUDA device and synchronises it.  On success *out holds the plan.
  * Errors: QS_ERR_ARG, QS_ERR_UNSUPPORTED, QS_ERR_OOM, QS_ERR_CUDA.
  */

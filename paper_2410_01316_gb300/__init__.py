@@ -45,7 +45,7 @@ class QSPlan:
 
     def __init__(self, d: int, kernel: str, P: int, n_ft: int, radius: float, kparam: float = 0.0,
                  dirs="orthogonal", seed: int = 0, window: int = 8, proj: str = "auto",
-                 max_n: int = 0, max_m: int = 0, device=None):
+                 max_n: int = 0, max_m: int = 0, device=None, kparam2: float = 0.0):
         import torch
 
         lib = _lib.load()
@@ -69,10 +69,11 @@ class QSPlan:
         desc.radius = float(radius)
         desc.proj = _lib.PROJ[proj]
         desc.max_n, desc.max_m = int(max_n), int(max_m)
+        desc.kparam2 = float(kparam2)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         with torch.cuda.device(self.device):
             _lib.check(lib.qs_plan_create(ctypes.byref(self._handle), ctypes.byref(desc)), "qs_plan_create")
-        self.d, self.kernel, self.kparam, self.P, self.n_ft = d, kernel, kparam, P, n_ft
+        self.d, self.kernel, self.kparam, self.kparam2, self.P, self.n_ft = d, kernel, kparam, kparam2, P, n_ft
         self.window, self.proj, self.max_n, self.max_m, self.radius = window, proj, max_n, max_m, radius
         tau = ctypes.c_double()
         G = ctypes.c_int()
@@ -314,14 +315,15 @@ KernelSumFn = _LazyFn()
 
 
 def kernel_sum(x, w, y, kernel: str, kparam: float = 0.0, P: int = 256, n_ft: int = 512, dirs="orthogonal",
-               seed: int = 0, radius: float | None = None, proj: str = "auto", window: int = 8):
-    """One-shot convenience wrapper: builds a plan sized for these inputs."""
+               seed: int = 0, radius: float | None = None, proj: str = "auto", window: int = 8,
+               kparam2: float = 0.0):
+    """One-shot convenience wrapper: builds a plan sized for these inputs (kparam2 = nu for "matern")."""
     import torch
 
     if radius is None:
         radius = float(x.norm(dim=1).max() + y.norm(dim=1).max()) * (1 + 1e-6)
     with QSPlan(x.shape[1], kernel, P, n_ft, radius, kparam, dirs, seed, window, proj, x.shape[0], y.shape[0],
-                device=x.device.index) as plan:
+                device=x.device.index, kparam2=kparam2) as plan:
         s = plan.sum(x, w, y)
         torch.cuda.current_stream().synchronize()
         plan.check()

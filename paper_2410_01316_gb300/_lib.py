@@ -23,7 +23,7 @@ STATUS = {
     0: "QS_OK", 1: "QS_ERR_ARG", 2: "QS_ERR_RANGE", 3: "QS_ERR_NONFINITE", 4: "QS_ERR_OOM",
     5: "QS_ERR_CUDA", 6: "QS_ERR_UNSUPPORTED", 7: "QS_ERR_TIMEOUT",
 }
-KERNELS = {"gauss": 0, "laplace": 1, "negdist": 2}
+KERNELS = {"gauss": 0, "laplace": 1, "negdist": 2, "matern": 3, "riesz": 4, "tps": 5}
 DIRS = {"user": 0, "fibonacci": 1, "orthogonal": 2, "iid": 3}
 PROJ = {"auto": 0, "fp32": 1, "fp32_fused": 2, "bf16x3": 3, "tf32": 4}
 
@@ -40,6 +40,7 @@ class PlanDesc(ctypes.Structure):
         ("d", c_int), ("kernel", c_int), ("kparam", c_dbl), ("P", c_int), ("dirs", c_int),
         ("seed", c_u64), ("dirs_host", c_vp), ("n_ft", c_int), ("window", c_int),
         ("oversampling", c_dbl), ("radius", c_dbl), ("proj", c_int), ("max_n", c_i64), ("max_m", c_i64),
+        ("kparam2", c_dbl),
     ]
 
 

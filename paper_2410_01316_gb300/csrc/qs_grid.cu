@@ -37,12 +37,23 @@ constexpr double kPi = 3.14159265358979323846264338327950288;
 // Gauss:   f^(w) = sqrt(2) pi sigma (2 pi^2 sigma^2 w^2)^{(d-1)/2} e^{-2 pi^2 sigma^2 w^2} / Gamma(d/2)
 // Laplace: f^(w) = Gamma((d+1)/2) 2^d pi^{d-1/2} |w|^{d-1} / (Gamma(d/2) alpha^d)
 //                  (1 + 4 pi^2 w^2 / alpha^2)^{-(d+1)/2}
-// Both follow from F_1[f](w) = pi^{d/2}/Gamma(d/2) |w|^{d-1} F_d[F](|w|) and
+// Matern:  f^(w) = Gamma(nu + d/2) 2^{d/2} pi^d beta^d |w|^{d-1}
+//                  / (Gamma(d/2) Gamma(nu) nu^{d/2}) (1 + 2 pi^2 beta^2 w^2 / nu)^{-(nu + d/2)}
+// All follow from F_1[f](w) = pi^{d/2}/Gamma(d/2) |w|^{d-1} F_d[F](|w|) and
 // are evaluated in log space (d up to the hundreds).  Negative distance: the
 // 1-periodic triangle wave -(c_d/tau)|t| with closed-form coefficients.
+// (Riesz and the thin plate spline come from the host as a table.)
 // ---------------------------------------------------------------------------
-__device__ double coeff_k(int kernel, double kp, int d, double tau, int k)
+__device__ double coeff_k(int kernel, double kp, double kp2, int d, double tau, int k)
 {
+    if (kernel == QS_MATERN) {
+        const double w = fabs(tau * (double)k), nu = kp2;
+        if (w == 0.0 && d > 1) return 0.0;
+        const double lf = lgamma(nu + 0.5 * d) + 0.5 * d * log(2.0) + d * log(kPi) + d * log(kp)
+                          + (d > 1 ? (d - 1) * log(w) : 0.0) - lgamma(0.5 * d) - lgamma(nu) - 0.5 * d * log(nu)
+                          - (nu + 0.5 * d) * log1p(2.0 * kPi * kPi * kp * kp * w * w / nu);
+        return tau * exp(lf);
+    }
     if (kernel == QS_NEGDIST) {
         const double cd = exp(0.5 * log(kPi) + lgamma(0.5 * (d + 1)) - lgamma(0.5 * d));
         const double amp = cd / tau;
@@ -64,19 +75,24 @@ __device__ double coeff_k(int kernel, double kp, int d, double tau, int k)
     return tau * exp(lf);
 }
 
-__global__ void coeff_kernel(int kernel, double kp, int d, double tau, int n_ft, int G,
-                             const double* __restrict__ psihat, double* __restrict__ c_out,
-                             float* __restrict__ D_out)
+// c_in (n_ft values at k + n_ft/2, or NULL): coefficients computed on the host.
+__global__ void coeff_kernel(int kernel, double kp, double kp2, int d, double tau, int n_ft, int G,
+                             const double* __restrict__ psihat, const double* __restrict__ c_in,
+                             double* __restrict__ c_out, float* __restrict__ D_out)
 {
     const int K = n_ft / 2;
     const int Gh = G / 2;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n_ft) c_out[i] = coeff_k(kernel, kp, d, tau, i - K);
+    auto ck = [&](int k) {
+        if (c_in) return c_in[(k < K ? k : -k) + K];  // c_K = c_{-K} (even)
+        return coeff_k(kernel, kp, kp2, d, tau, k);
+    };
+    if (i < n_ft) c_out[i] = ck(i - K);
     if (i <= Gh) {
         float v = 0.0f;
         if (i <= K) {
             const double ph = psihat[i];
-            double dv = coeff_k(kernel, kp, d, tau, i) / (ph * ph);
+            double dv = ck(i) / (ph * ph);
             // only k = -N_ft/2 is kept of the pair +-N_ft/2; its real part
             // contributes half to each side of the Hermitian spectrum
             if (i == K) dv *= 0.5;
@@ -1013,11 +1029,12 @@ cudaError_t qs_launch_reduce_grad(const float* part, int S, int64_t M, int d, fl
     return cudaGetLastError();
 }
 
-cudaError_t qs_launch_coeffs(int kernel, double kparam, int d, double tau, int n_ft, int G,
-                             const double* psihat, double* c_out, float* D_out, cudaStream_t st)
+cudaError_t qs_launch_coeffs(int kernel, double kparam, double kparam2, int d, double tau, int n_ft, int G,
+                             const double* psihat, const double* c_in, double* c_out, float* D_out, cudaStream_t st)
 {
     const int n = (n_ft > G / 2 + 1 ? n_ft : G / 2 + 1);
-    coeff_kernel<<<(n + 127) / 128, 128, 0, st>>>(kernel, kparam, d, tau, n_ft, G, psihat, c_out, D_out);
+    coeff_kernel<<<(n + 127) / 128, 128, 0, st>>>(kernel, kparam, kparam2, d, tau, n_ft, G, psihat, c_in, c_out,
+                                                   D_out);
     return cudaGetLastError();
 }
 

@@ -207,8 +207,8 @@ __host__ __device__ inline int qs_interp_tpt(bool fused, int d)
 // ---------------------------------------------------------------------------
 // launchers (defined in the .cu files); return cudaSuccess or the launch error
 // ---------------------------------------------------------------------------
-cudaError_t qs_launch_coeffs(int kernel, double kparam, int d, double tau, int n_ft, int G,
-                             const double* psihat, double* c_out, float* D_out, cudaStream_t st);
+cudaError_t qs_launch_coeffs(int kernel, double kparam, double kparam2, int d, double tau, int n_ft, int G,
+                             const double* psihat, const double* c_in, double* c_out, float* D_out, cudaStream_t st);
 cudaError_t qs_launch_project_fp32(const float* X, int64_t N, int d, const float* xi_s, int P,
                                    float* U, int64_t ldU, cudaStream_t st);
 void qs_set_error_message(const char* msg);

@@ -171,10 +171,15 @@ extern "C" qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_
     const qs_plan_desc& D = *desc;
     if (D.d < 1 || D.d > QS_FUSED_MAX_D || D.P < 1)
         return nfail(QS_ERR_ARG, "qs_sum_noalloc: need 1 <= d <= %d and P >= 1", QS_FUSED_MAX_D);
-    if (D.kernel != QS_GAUSS && D.kernel != QS_LAPLACE && D.kernel != QS_NEGDIST)
+    if (D.kernel < QS_GAUSS || D.kernel > QS_TPS)
         return nfail(QS_ERR_ARG, "qs_sum_noalloc: unknown kernel");
+    if (D.kernel == QS_RIESZ || D.kernel == QS_TPS)
+        return nfail(QS_ERR_UNSUPPORTED,
+                     "qs_sum_noalloc: the Riesz and thin plate spline coefficients need a plan (host quadrature)");
     if (D.kernel != QS_NEGDIST && !(D.kparam > 0.0 && isfinite(D.kparam)))
         return nfail(QS_ERR_ARG, "qs_sum_noalloc: kernel parameter must be positive");
+    if (D.kernel == QS_MATERN && !(D.kparam2 > 0.0 && D.kparam2 < 1e6))
+        return nfail(QS_ERR_ARG, "qs_sum_noalloc: Matern nu (kparam2) must be positive");
     if (!(D.radius > 0.0 && isfinite(D.radius))) return nfail(QS_ERR_ARG, "qs_sum_noalloc: radius must be > 0");
     if (D.n_ft < 16 || D.n_ft > QS_MAX_G / 2 || (D.n_ft & (D.n_ft - 1)))
         return nfail(QS_ERR_UNSUPPORTED, "qs_sum_noalloc: n_ft must be a power of two in [16, %d]", QS_MAX_G / 2);
@@ -224,6 +229,7 @@ extern "C" qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_
     switch (D.kernel) {
         case QS_GAUSS: tau = fmin(0.3 / D.radius, 1.0 / (2.0 * 5.0 * D.kparam)); break;
         case QS_LAPLACE: tau = fmin(0.1 / D.radius, 1.0 / (2.0 * 5.0 / D.kparam)); break;
+        case QS_MATERN: tau = fmin(0.2 / D.radius, 1.0 / (2.0 * 5.0 * D.kparam)); break;
         default: tau = 1.0 / (2.0 * D.radius); break;
     }
     qs_launch L;
@@ -282,7 +288,8 @@ extern "C" qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_
                                                                      reinterpret_cast<float*>(base + o_xi));
     e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = qs_launch_coeffs((int)D.kernel, D.kparam, d, tau, D.n_ft, G, reinterpret_cast<const double*>(base + o_psihat),
+        e = qs_launch_coeffs((int)D.kernel, D.kparam, D.kparam2, d, tau, D.n_ft, G,
+                             reinterpret_cast<const double*>(base + o_psihat), nullptr,
                              reinterpret_cast<double*>(base + o_c), reinterpret_cast<float*>(base + o_D), st);
     if (e == cudaSuccess) {
         if (N == 0) {

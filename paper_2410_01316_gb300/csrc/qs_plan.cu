@@ -233,15 +233,90 @@ void window_transform(const qs_window& win, int W, int K, int G, std::vector<dou
     }
 }
 
-// Rescaling factor (App. C Step 1; App. G for the negative distance).
+// Rescaling factor (App. C Step 1: T = 0.3 Gauss, 0.1 Laplace, 0.2 Matern,
+// g_max = 5 sigma, 5 / alpha, 5 beta; App. G for the kernels without a
+// classical Fourier transform: the half period T = R, tau = 1/(2R)).
 double tau_rule(qs_kernel kernel, double kparam, double R)
 {
     switch (kernel) {
         case QS_GAUSS: return fmin(0.3 / R, 1.0 / (2.0 * 5.0 * kparam));
         case QS_LAPLACE: return fmin(0.1 / R, 1.0 / (2.0 * 5.0 / kparam));
-        case QS_NEGDIST: return 1.0 / (2.0 * R);
+        case QS_MATERN: return fmin(0.2 / R, 1.0 / (2.0 * 5.0 * kparam));
+        case QS_NEGDIST:
+        case QS_RIESZ:
+        case QS_TPS: return 1.0 / (2.0 * R);
     }
     return -1.0;
+}
+
+// Fourier coefficients of the 1-periodic g(t) = f(|t| / tau), t in [-1/2, 1/2),
+// for the generalised Riesz kernel (f = -c_{d,q} |t|^q, c_{d,q} =
+// sqrt(pi) Gamma((d+q)/2) / (Gamma(d/2) Gamma((q+1)/2))) and the thin plate
+// spline (f = d t^2 log|t| + C_d t^2, C_d = d/2 (H_{d/2} - 2 + log 4)), both
+// from Table tab:kernels: c_k = 2 int_0^{1/2} g(t) cos(2 pi k t) dt for
+// k = 0 .. n_ft/2, in FP64.  All k share one set of nodes: 16-point
+// Gauss-Legendre on panels of width 1/n_ft (half a period of the highest
+// frequency), the first panel split geometrically towards t = 0 where g is
+// not smooth; cos(2 pi k t) over k by the three-term recurrence, restarted
+// from cos() every 64 steps.  Writes c[k + n_ft/2] for k = -n_ft/2 .. n_ft/2 - 1.
+void periodic_coeffs(qs_kernel kernel, double q, int d, double tau, int n_ft, std::vector<double>& c)
+{
+    const int K = n_ft / 2;
+    double amp = 0.0, cd = 0.0;
+    if (kernel == QS_RIESZ) {
+        amp = -exp(0.5 * log(kPi) + lgamma(0.5 * (d + q)) - lgamma(0.5 * d) - lgamma(0.5 * (q + 1.0)));
+    } else {
+        double h = 0.0, x = 0.0;  // H_x at x = 0 or 1/2, stepped up to d/2
+        if (d & 1) {
+            h = 2.0 - 2.0 * log(2.0);
+            x = 0.5;
+        }
+        for (; x + 0.25 < 0.5 * d; x += 1.0) h += 1.0 / (x + 1.0);
+        cd = 0.5 * d * (h - 2.0 + log(4.0));
+    }
+    auto g = [&](double t) {
+        const double u = t / tau;
+        if (kernel == QS_RIESZ) return amp * pow(u, q);
+        return u > 0.0 ? (double)d * u * u * log(u) + cd * u * u : 0.0;
+    };
+    std::vector<double> gx, gw;
+    gauss_legendre(16, gx, gw);
+    std::vector<double> nodes, vals;
+    auto panel = [&](double a, double b) {
+        const double m = 0.5 * (a + b), hh = 0.5 * (b - a);
+        for (size_t i = 0; i < gx.size(); ++i) {
+            const double t = m + hh * gx[i];
+            nodes.push_back(t);
+            vals.push_back(2.0 * hh * gw[i] * g(t));
+        }
+    };
+    const double h = 0.5 / K;
+    for (int j = 1; j < K; ++j) panel(j * h, (j + 1) * h);
+    for (double b = h; b > h * 1e-18; b *= 0.5) panel(0.5 * b, b);
+    std::vector<double> acc(K + 1, 0.0);
+    for (size_t i = 0; i < nodes.size(); ++i) {
+        const double th = 2.0 * kPi * nodes[i], c1 = cos(th), v = vals[i];
+        acc[0] += v;
+        acc[1] += v * c1;
+        double cprev = 1.0, ccur = c1;  // cos((k-2) th), cos((k-1) th)
+        for (int k = 2; k <= K; ++k) {
+            double cnext;
+            if ((k & 63) == 0) {
+                ccur = cos((k - 1) * th);
+                cnext = cos(k * th);
+            } else {
+                cnext = 2.0 * c1 * ccur - cprev;
+            }
+            acc[k] += v * cnext;
+            cprev = ccur;
+            ccur = cnext;
+        }
+    }
+    c.assign(n_ft, 0.0);
+    for (int k = 0; k <= K; ++k) {
+        if (k < K) c[K + k] = acc[k];
+        c[K - k] = acc[k];
+    }
 }
 
 void free_plan(qs_plan p)
@@ -412,10 +487,15 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     *out = nullptr;
     const qs_plan_desc& D = *desc;
     if (D.d < 1 || D.P < 1) return fail(QS_ERR_ARG, "qs_plan_create: d and P must be >= 1");
-    if (D.kernel != QS_GAUSS && D.kernel != QS_LAPLACE && D.kernel != QS_NEGDIST)
+    if (D.kernel < QS_GAUSS || D.kernel > QS_TPS)
         return fail(QS_ERR_ARG, "qs_plan_create: unknown kernel %d", (int)D.kernel);
-    if (D.kernel != QS_NEGDIST && !(D.kparam > 0.0 && isfinite(D.kparam)))
+    if ((D.kernel == QS_GAUSS || D.kernel == QS_LAPLACE || D.kernel == QS_MATERN) &&
+        !(D.kparam > 0.0 && isfinite(D.kparam)))
         return fail(QS_ERR_ARG, "qs_plan_create: kernel parameter must be positive");
+    if (D.kernel == QS_MATERN && !(D.kparam2 > 0.0 && D.kparam2 < 1e6))
+        return fail(QS_ERR_ARG, "qs_plan_create: Matern nu (kparam2) must be positive");
+    if (D.kernel == QS_RIESZ && !(D.kparam > 0.0 && D.kparam < 2.0))
+        return fail(QS_ERR_ARG, "qs_plan_create: Riesz exponent (kparam) must lie in (0, 2)");
     if (!(D.radius > 0.0 && isfinite(D.radius))) return fail(QS_ERR_ARG, "qs_plan_create: radius must be > 0");
     if (!is_pow2(D.n_ft) || D.n_ft < 16 || D.n_ft > QS_MAX_G / 2)
         return fail(QS_ERR_UNSUPPORTED, "qs_plan_create: n_ft must be a power of two in [16, %d]", QS_MAX_G / 2);
@@ -581,8 +661,24 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
              "copy window transform");
     QS_CHECK(cudaMemcpy(p->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice), "copy twiddles");
     QS_CHECK(cudaMemset(p->d_flag, 0, sizeof(unsigned int)), "clear flag");
-    QS_CHECK(qs_launch_coeffs((int)D.kernel, D.kparam, d, p->tau, D.n_ft, G, p->d_psihat, p->d_c, p->d_D, 0),
-             "coefficient kernel launch");
+    if (D.kernel == QS_RIESZ || D.kernel == QS_TPS) {
+        // no classical transform: the periodised kernel's coefficients by host quadrature
+        std::vector<double> ch;
+        periodic_coeffs(D.kernel, D.kparam, d, p->tau, D.n_ft, ch);
+        double* d_ch = nullptr;
+        QS_CHECK(cudaMalloc(&d_ch, ch.size() * sizeof(double)), "coefficient table");
+        cudaError_t e1 = cudaMemcpy(d_ch, ch.data(), ch.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e1 == cudaSuccess)
+            e1 = qs_launch_coeffs((int)D.kernel, D.kparam, D.kparam2, d, p->tau, D.n_ft, G, p->d_psihat, d_ch,
+                                  p->d_c, p->d_D, 0);
+        if (e1 == cudaSuccess) e1 = cudaDeviceSynchronize();
+        cudaFree(d_ch);
+        QS_CHECK(e1, "coefficient table upload");
+    } else {
+        QS_CHECK(qs_launch_coeffs((int)D.kernel, D.kparam, D.kparam2, d, p->tau, D.n_ft, G, p->d_psihat, nullptr,
+                                  p->d_c, p->d_D, 0),
+                 "coefficient kernel launch");
+    }
     if (p->d_Dd) QS_CHECK(qs_launch_deriv_table(p->d_c, p->d_psihat, D.n_ft, G, p->d_Dd, 0), "derivative table");
     if (tc) {
         const int eb = proj == QS_PROJ_BF16X3 ? 2 : 4;

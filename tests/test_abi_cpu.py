@@ -106,6 +106,20 @@ def test_plan_create_argument_errors_need_no_gpu(lib):
     assert lib.qs_plan_destroy(None) == 0
 
 
+def test_kernel_parameter_errors_need_no_gpu(lib):
+    desc = _lib.PlanDesc()
+    h = ctypes.c_void_p()
+    desc.d, desc.P, desc.dirs = 3, 16, 1
+    desc.n_ft, desc.window, desc.radius, desc.max_n, desc.max_m = 128, 8, 2.0, 10, 10
+    for kernel, kp, kp2 in (("matern", 0.5, 0.0), ("matern", -1.0, 1.5), ("riesz", 0.0, 0.0),
+                            ("riesz", 2.0, 0.0), ("riesz", -0.5, 0.0)):
+        desc.kernel, desc.kparam, desc.kparam2 = _lib.KERNELS[kernel], kp, kp2
+        assert lib.qs_plan_create(ctypes.byref(h), ctypes.byref(desc)) == 1, (kernel, kp, kp2)
+    desc.kernel = 6
+    assert lib.qs_plan_create(ctypes.byref(h), ctypes.byref(desc)) == 1
+    assert not h.value
+
+
 def test_plan_create_without_device_fails_cleanly(lib):
     import torch
 
