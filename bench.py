@@ -59,6 +59,13 @@ def make_problem(name: str, P: int = 0, N: int = 0):
         if N:
             kw["N"] = kw["M"] = N
         return W.mnist_laplace(**kw)
+    if name in ("mnist_matern3", "mnist_matern7"):
+        kw = {"nu": 1.5 if name == "mnist_matern3" else 3.5}
+        if P:
+            kw["P"] = P
+        if N:
+            kw["N"] = kw["M"] = N
+        return W.mnist_matern(**kw)
     if name == "small_gauss":
         return W.small_gauss()
     if name == "gauss64_negdist":
@@ -157,7 +164,7 @@ def oracle_sample_rate(prob, n_slices: int, n_targets: int, threads: int = 0, se
     y = np.ascontiguousarray(prob.y[idx])
     xi = np.ascontiguousarray(prob.xi[:n_slices])
     t = oracle.tau(prob.kernel, prob.kparam, prob.R)
-    c = oracle.coeffs(prob.kernel, prob.kparam, prob.d, t, prob.n_ft)
+    c = oracle.coeffs(prob.kernel, prob.kparam, prob.d, t, prob.n_ft, nu=prob.kparam2)
     t0 = time.perf_counter()
     oracle.o1_sum(prob.x, prob.w, y, xi, t, c, threads)
     dt = time.perf_counter() - t0
@@ -216,7 +223,7 @@ def run_ours(args, rank, world, local_rank):
     prob = make_problem(args.workload, args.P, args.N)
     proj = args.proj
     plan = QSPlan(prob.d, prob.kernel, prob.P, prob.n_ft, prob.R, prob.kparam, dirs=prob.xi, window=prob.window,
-                  proj=proj, max_n=prob.N, max_m=prob.M)
+                  proj=proj, max_n=prob.N, max_m=prob.M, kparam2=prob.kparam2)
     x = torch.from_numpy(prob.x).to(dev)
     y = torch.from_numpy(prob.y).to(dev)
     w = torch.from_numpy(prob.w).to(dev)
@@ -332,7 +339,7 @@ def plain_fp32_compare(prob, x, w, y, flush, args, err_idx_err=True):
 
     steps = max(3, min(args.steps, 5))
     with QSPlan(prob.d, prob.kernel, prob.P, prob.n_ft, prob.R, prob.kparam, dirs=prob.xi, window=prob.window,
-                proj="fp32", max_n=prob.N, max_m=prob.M) as plan:
+                proj="fp32", max_n=prob.N, max_m=prob.M, kparam2=prob.kparam2) as plan:
         s = torch.empty(prob.M, dtype=torch.float32, device=x.device)
         for _ in range(2):
             plan.sum(x, w, y, out=s)
@@ -631,7 +638,7 @@ def error_vs_oracle(prob, s, n_targets: int):
 
     idx = np.random.default_rng(4242).choice(prob.M, min(n_targets, prob.M), replace=False)
     t = oracle.tau(prob.kernel, prob.kparam, prob.R)
-    c = oracle.coeffs(prob.kernel, prob.kparam, prob.d, t, prob.n_ft)
+    c = oracle.coeffs(prob.kernel, prob.kparam, prob.d, t, prob.n_ft, nu=prob.kparam2)
     ref = oracle.o1_sum(prob.x, prob.w, np.ascontiguousarray(prob.y[idx]), prob.xi, t, c)
     sg = s.detach().cpu().numpy().astype(np.float64)[idx]
     norm = float(np.abs(prob.w.astype(np.float64)).sum()) * (prob.R if prob.kernel == "negdist" else 1.0)

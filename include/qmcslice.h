@@ -227,7 +227,9 @@ qs_status qs_stage_times(qs_plan plan, float* ms, int n);
  *
  * desc: as for qs_plan_create; dirs, seed, dirs_host, max_n and max_m are
  *       ignored and proj must be QS_PROJ_AUTO or QS_PROJ_FP32_FUSED (FP32 dot
- *       products inside the spread and interpolation; d <= 64).
+ *       products inside the spread and interpolation; d <= 64).  QS_RIESZ and
+ *       QS_TPS, whose coefficients need host quadrature, return
+ *       QS_ERR_UNSUPPORTED.
  * dirs_dev: P x d FP32 directions in device memory (caller-owned).
  * x, w, y, s: as for qs_sum (device memory, w may be NULL).
  * Sizes: P * 2 n_ft grid values, the tables and the slice partial sums must
