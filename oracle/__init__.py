@@ -65,6 +65,8 @@ def _load():
             lib.o_coeffs2.argtypes = [i, d, d, i, d, i, p]
             lib.o2_exact2.restype = i
             lib.o2_exact2.argtypes = [i, d, d, i, i64, p, p, i64, p, p, i]
+            lib.o_esym.restype = i
+            lib.o_esym.argtypes = [i, i, p, p, p, i]
             lib.o3_sliced2.restype = i
             lib.o3_sliced2.argtypes = [i, d, d, i, i64, p, p, i64, p, i, p, p, i]
             lib.o_F.restype = d
@@ -214,3 +216,14 @@ def o1_problem(prob, threads: int = 0, y=None) -> np.ndarray:
     t = tau(prob.kernel, prob.kparam, prob.R)
     c = coeffs(prob.kernel, prob.kparam, prob.d, t, prob.n_ft, nu=nu)
     return o1_sum(prob.x, prob.w, prob.y if y is None else y, prob.xi, t, c, threads)
+
+
+def esym(xi, grad: bool = True, threads: int = 0):
+    """Symmetric distance energy E_sym = -2 sum_{p,q} (|xi_p - xi_q| + |xi_p + xi_q|) and its
+    gradient (eq. distance-sym; Sec. 2.3 eq. distance-mmd)."""
+    xi = _f32(xi)
+    P, d = xi.shape
+    E = ctypes.c_double(0.0)
+    g = np.zeros((P, d)) if grad else None
+    _check(_load().o_esym(d, P, _ptr(xi), ctypes.byref(E), _ptr(g), int(threads)), "esym")
+    return E.value, g

@@ -25,6 +25,8 @@
  *   o1_grad        gradients of L = sum_m v_m s_m of the same sum
  *   o2_exact       exact kernel sum, O(NM)            (Sec. 1, eq. kernel_sum)
  *   o3_sliced      sliced sum with closed-form f      (Sec. 2.1, eq. kernel_sum_sliced)
+ *   o_esym         symmetric distance energy and its gradient (Sec. 2.3, eq. distance-mmd;
+ *                  App. "Relation between Distance QMC Designs and Orthogonal Points", eq. distance-sym)
  *
  * Readings of the paper taken here (garbled or silent passages):
  *   - f-hat for the Gauss and Laplace kernels is obtained from the relation
@@ -683,4 +685,54 @@ int o3_sliced(int kernel, double kparam, int d, int64_t N, const float* x, const
               int64_t M, const float* y, int P, const float* xi, double* s, int nthreads)
 {
     return o3_sliced2(kernel, kparam, 0.0, d, N, x, w, M, y, P, xi, s, nthreads);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Symmetric distance energy of P points xi_p in R^d (eq. distance-sym):   */
+/*   E_sym = E((xi, -xi)) = -2 sum_{p,q} (|xi_p - xi_q| + |xi_p + xi_q|),   */
+/* the energy of eq. distance-mmd (s = d/2, exponent 1) of the points and  */
+/* their antipodes.  Its gradient in xi_p, from the plain definition (both */
+/* orders of each pair; the p = q pair contributes |2 xi_p|):               */
+/*   dE/dxi_p = -4 [ sum_{q != p} ((xi_p - xi_q)/|xi_p - xi_q|              */
+/*                                 + (xi_p + xi_q)/|xi_p + xi_q|) + xi_p/|xi_p| ]. */
+/* grad (P x d) may be NULL.                                               */
+/* ---------------------------------------------------------------------- */
+int o_esym(int d, int P, const float* xi, double* E, double* grad, int nthreads)
+{
+    if (d < 1 || P < 1 || !xi || !E) return O_EARG;
+    double tot = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : tot) num_threads(n_threads(nthreads))
+    for (int p = 0; p < P; ++p) {
+        const float* a = xi + (size_t)p * d;
+        double acc = 0.0;
+        double* g = grad ? grad + (size_t)p * d : NULL;
+        if (g)
+            for (int j = 0; j < d; ++j) g[j] = 0.0;
+        for (int q = 0; q < P; ++q) {
+            const float* b = xi + (size_t)q * d;
+            double dm = 0.0, dp = 0.0;
+            for (int j = 0; j < d; ++j) {
+                double u = (double)a[j] - (double)b[j], v = (double)a[j] + (double)b[j];
+                dm += u * u;
+                dp += v * v;
+            }
+            dm = sqrt(dm);
+            dp = sqrt(dp);
+            acc += dm + dp;
+            if (!g) continue;
+            if (q == p) {
+                for (int j = 0; j < d; ++j) g[j] += 4.0 * (double)a[j] / dp; /* d|2 a|/da = 2 a/|a| = 4 a/|2 a| */
+                continue;
+            }
+            for (int j = 0; j < d; ++j) {
+                double u = (double)a[j] - (double)b[j], v = (double)a[j] + (double)b[j];
+                g[j] += 2.0 * (u / dm + v / dp);
+            }
+        }
+        if (g)
+            for (int j = 0; j < d; ++j) g[j] *= -2.0;
+        tot += acc;
+    }
+    *E = -2.0 * tot;
+    return O_OK;
 }
