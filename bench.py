@@ -442,6 +442,63 @@ def run_mmd_flow(args, rank, world, local_rank):
     plan.close()
 
 
+def run_design(args, rank, world, local):
+    """Distance QMC design generator (Sec. 4.1 "Distance"; eq. distance-sym) at the paper's largest
+    reported size, d = 200 and P = 5000: Adam steps per second.  One step = Gram matrix + pairwise
+    weights + (B - A) Xi + Adam/renormalise, i.e. 4 P^2 d FP32 flop in two SIMT GEMMs."""
+    import torch
+
+    from paper_2410_01316_gb300 import build as qbuild
+    from paper_2410_01316_gb300 import directions, distance_design, distance_energy
+
+    qbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    d, P = 200, (args.P or 5000)
+    iters = 50
+    x0 = torch.from_numpy(directions("orthogonal", d, P, seed=20241006)).to(dev)
+    e_orth = distance_energy(x0)
+    x = x0.clone()
+    for _ in range(args.warmup):
+        distance_design(x, iters=5)
+    x.copy_(x0)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(smi_gpu_id(dev))
+    sampler.start()
+    time.sleep(0.3)
+    ms, energies = [], []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        energies.append(distance_design(x, iters=iters))
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    t = sum(ms) / 1e3
+    n_it = iters * args.steps
+    flops = 4.0 * P * P * d
+    mhz = clocks.get("sm_mhz") or 2070.0
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sm_count * 128 * 2 * mhz * 1e6 / 1e12
+    achieved = flops * n_it / t / 1e12
+    line = {"metric": "distance QMC design: Adam steps per second", "value": n_it / t, "unit": "steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / n_it,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"distance_design: d={d} P={P}, {iters} Adam steps per timed call "
+                                   f"(workspace allocation included), start = seeded orthogonal design",
+                       "energy_start": e_orth, "energy_after": energies},
+            "roofline": {"kernel": "design step", "bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "algorithmic": f"4 P^2 d = {flops:.3e} FP32 flop per step (two P x P x d contractions)",
+                         "peak_source": f"{sm_count} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"},
+            "clocks": clocks, "gpu_launches": n_it * 5 + args.steps * 4}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def batch256_problems(n=256, seed=20241004):
     """256 Gauss problems: N, M log-uniform in [1e3, 1e5], d in {3, 16, 64},
     N_ft in {256, 512, 1024}, P = 256 (Fibonacci for d = 3, else orthogonal),
@@ -711,6 +768,8 @@ def main():
         run_mmd_flow(args, rank, world, local)
     elif args.workload == "batch256":
         run_batch(args, rank, world, local)
+    elif args.workload == "distance_design":
+        run_design(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1 and _PG is not None:

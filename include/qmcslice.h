@@ -71,7 +71,10 @@ typedef enum {
     QS_DIR_USER = 0,       /* caller supplies P x d unit rows in dirs_host */
     QS_DIR_FIBONACCI = 1,  /* spherical Fibonacci points, d = 3 only */
     QS_DIR_ORTHOGONAL = 2, /* first P columns of ceil(P/d) Haar-orthogonal matrices */
-    QS_DIR_IID = 3         /* iid uniform on the sphere */
+    QS_DIR_IID = 3,        /* iid uniform on the sphere */
+    QS_DIR_DISTANCE = 4    /* distance QMC design: QS_DIR_ORTHOGONAL (seeded) refined by
+                              qs_distance_design (300 steps, lr 0.05/sqrt(d)) at plan creation;
+                              plans only (qs_directions refuses it: it needs the GPU) */
 } qs_dirs;
 
 /* Precision / form of the projection step a = tau X Xi^T. */
@@ -304,6 +307,27 @@ qs_status qs_plan_set_variant(qs_plan plan, int spread_variant);
 /* Variants of the plan's family (bit v of *available set for variant v) and
  * the variant in use (*current); either pointer may be NULL.  Host only. */
 qs_status qs_plan_variants(qs_plan plan, unsigned int* available, int* current);
+
+/*
+ * Distance QMC designs (Sec. 2.3, eq. distance-mmd with s = d/2; Sec. 4.1,
+ * "Distance"; the symmetric energy of eq. distance-sym):
+ *   E_sym(xi) = -2 sum_{p,q} (|xi_p - xi_q| + |xi_p + xi_q|)
+ * over P unit directions in R^d, minimised by Adam (beta1 0.9, beta2 0.999,
+ * step size lr) with every step followed by renormalising the rows.
+ *
+ * qs_distance_design: runs `iters` steps on the P x d FP32 rows in dirs_dev
+ * (device, caller-owned, updated in place; start from any unit rows, e.g.
+ * QS_DIR_ORTHOGONAL); if energy is not NULL it receives E_sym of the result.
+ * qs_distance_energy: E_sym of the rows in dirs_dev and, if grad_dev is not
+ * NULL, its Euclidean gradient dE/dxi (P x d device array, caller-owned).
+ * Both are set-up routines, not part of the sum: they allocate and free a
+ * workspace of about 4 P^2 + 12 P d bytes on the current device, run on
+ * `stream` and return when it is done.  Errors: QS_ERR_ARG (NULL pointer,
+ * d or P < 1, iters < 0, lr <= 0), QS_ERR_UNSUPPORTED (P^2 beyond 2^31),
+ * QS_ERR_OOM, QS_ERR_CUDA.
+ */
+qs_status qs_distance_design(float* dirs_dev, int d, int P, int iters, double lr, double* energy, void* stream);
+qs_status qs_distance_energy(const float* dirs_dev, int d, int P, double* energy, float* grad_dev, void* stream);
 
 /* Library version string. */
 const char* qs_version(void);

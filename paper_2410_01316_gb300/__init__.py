@@ -11,13 +11,15 @@ memory and streams; all arithmetic runs in the CUDA library
 from __future__ import annotations
 
 import ctypes
+import math
 
 import numpy as np
 
 from . import _lib
 from ._lib import QSError
 
-__all__ = ["QSPlan", "QSBatch", "QSError", "KernelSumFn", "directions", "kernel_sum", "version"]
+__all__ = ["QSPlan", "QSBatch", "QSError", "KernelSumFn", "directions", "kernel_sum", "version",
+           "distance_design", "distance_energy"]
 
 
 def version() -> str:
@@ -328,3 +330,43 @@ def kernel_sum(x, w, y, kernel: str, kparam: float = 0.0, P: int = 256, n_ft: in
         torch.cuda.current_stream().synchronize()
         plan.check()
         return s
+
+
+def _dirs_tensor(xi):
+    import torch
+
+    if not (isinstance(xi, torch.Tensor) and xi.is_cuda and xi.dtype == torch.float32 and xi.is_contiguous()
+            and xi.dim() == 2):
+        raise TypeError("xi must be a contiguous float32 CUDA tensor of shape (P, d)")
+    return xi
+
+
+def distance_design(xi, iters: int = 300, lr: float | None = None, stream=None) -> float:
+    """Refine the unit rows of xi (P x d CUDA tensor, in place) towards a distance QMC design:
+    `iters` Adam steps on E_sym = -2 sum_{p,q} (|xi_p - xi_q| + |xi_p + xi_q|) (Sec. 2.3,
+    eq. distance-sym), rows renormalised after each step.  Returns E_sym of the result."""
+    import torch
+
+    xi = _dirs_tensor(xi)
+    P, d = xi.shape
+    lr = 0.05 / math.sqrt(d) if lr is None else lr
+    E = ctypes.c_double(0.0)
+    with torch.cuda.device(xi.device):
+        _lib.check(_lib.load().qs_distance_design(xi.data_ptr(), d, P, int(iters), float(lr), ctypes.byref(E),
+                                                  _stream_handle(stream)), "qs_distance_design")
+    return E.value
+
+
+def distance_energy(xi, grad: bool = False, stream=None):
+    """E_sym of the unit rows of xi and, with grad=True, its gradient (a new P x d tensor)."""
+    import torch
+
+    xi = _dirs_tensor(xi)
+    P, d = xi.shape
+    E = ctypes.c_double(0.0)
+    g = torch.empty_like(xi) if grad else None
+    with torch.cuda.device(xi.device):
+        _lib.check(_lib.load().qs_distance_energy(xi.data_ptr(), d, P, ctypes.byref(E),
+                                                  None if g is None else g.data_ptr(), _stream_handle(stream)),
+                   "qs_distance_energy")
+    return (E.value, g) if grad else E.value

@@ -24,7 +24,7 @@ STATUS = {
     5: "QS_ERR_CUDA", 6: "QS_ERR_UNSUPPORTED", 7: "QS_ERR_TIMEOUT",
 }
 KERNELS = {"gauss": 0, "laplace": 1, "negdist": 2, "matern": 3, "riesz": 4, "tps": 5}
-DIRS = {"user": 0, "fibonacci": 1, "orthogonal": 2, "iid": 3}
+DIRS = {"user": 0, "fibonacci": 1, "orthogonal": 2, "iid": 3, "distance": 4}
 PROJ = {"auto": 0, "fp32": 1, "fp32_fused": 2, "bf16x3": 3, "tf32": 4}
 
 # every symbol declared in include/qmcslice.h
@@ -32,7 +32,8 @@ EXPORTS = ("qs_plan_create", "qs_plan_destroy", "qs_plan_info", "qs_plan_directi
            "qs_sum_host", "qs_check", "qs_status_string", "qs_last_error", "qs_directions", "qs_version",
            "qs_set_timing", "qs_stage_times", "qs_project", "qs_sum_noalloc", "qs_grad",
            "qs_plan_autotune", "qs_plan_set_variant", "qs_batch_create", "qs_batch_destroy", "qs_sum_batched",
-           "qs_batch_check", "qs_batch_set_tiling", "qs_plan_variants")
+           "qs_batch_check", "qs_batch_set_tiling", "qs_plan_variants", "qs_distance_design",
+           "qs_distance_energy")
 
 
 class PlanDesc(ctypes.Structure):
@@ -87,6 +88,8 @@ def load() -> ctypes.CDLL:
         lib.qs_plan_autotune.argtypes = [c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(c_int), c_vp]
         lib.qs_plan_set_variant.argtypes = [c_vp, c_int]
         lib.qs_plan_variants.argtypes = [c_vp, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(c_int)]
+        lib.qs_distance_design.argtypes = [c_vp, c_int, c_int, c_int, c_dbl, ctypes.POINTER(c_dbl), c_vp]
+        lib.qs_distance_energy.argtypes = [c_vp, c_int, c_int, ctypes.POINTER(c_dbl), c_vp, c_vp]
         lib.qs_grad.argtypes = [c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]
         lib.qs_sum_noalloc.argtypes = [ctypes.POINTER(PlanDesc), c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp]
         lib.qs_set_timing.argtypes = [c_vp, c_int]
@@ -97,7 +100,7 @@ def load() -> ctypes.CDLL:
                      "qs_sum_host", "qs_check", "qs_directions", "qs_set_timing", "qs_stage_times", "qs_project",
                      "qs_sum_noalloc", "qs_grad", "qs_plan_autotune", "qs_plan_set_variant",
                      "qs_batch_create", "qs_batch_destroy", "qs_sum_batched", "qs_batch_check",
-                     "qs_batch_set_tiling", "qs_plan_variants"):
+                     "qs_batch_set_tiling", "qs_plan_variants", "qs_distance_design", "qs_distance_energy"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib

@@ -1,0 +1,255 @@
+// Distance QMC designs (Sec. 2.3, eq. distance-mmd with s = d/2, and the
+// symmetric form of eq. distance-sym): P unit directions xi_p minimising
+//   E_sym(xi) = E((xi, -xi)) = -2 sum_{p,q} (|xi_p - xi_q| + |xi_p + xi_q|),
+// the energy of the points together with their antipodes (the sliced
+// integrand is even in xi, so the antipodes come for free).  As in Sec. 4.1
+// the minimiser is found with Adam; each step is followed by renormalising
+// the rows onto the sphere.
+//
+// For unit rows |xi_p -+ xi_q|^2 = 2 -+ 2 c_pq with c = Xi Xi^T, so with
+// a_pq = 1/sqrt(2 - 2c) (0 on the diagonal) and b_pq = 1/sqrt(2 + 2c):
+//   dE/dxi_p = -4 [ xi_p r_p + sum_q (b_pq - a_pq) xi_q ],  r_p = sum_q (a_pq + b_pq),
+// i.e. two P x P x d contractions (the Gram matrix and (B - A) Xi) done by
+// the library's FP32 SIMT GEMM, plus elementwise work.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "qs_internal.cuh"
+
+namespace {
+
+qs_status design_fail(qs_status s, const char* msg)
+{
+    qs_set_error_message(msg);
+    return s;
+}
+
+// Row p of the Gram matrix C (stride ldc) -> weights W = B - A in place,
+// zero in the padding columns P .. ldc-1; r_p; and the row's share of the
+// energy, sum_q (|xi_p - xi_q| + |xi_p + xi_q|), in FP64.  One CTA per row.
+__global__ void __launch_bounds__(256) esym_weights_kernel(float* __restrict__ C, int P, int64_t ldc,
+                                                           float* __restrict__ r, double* __restrict__ e_row)
+{
+    const int p = blockIdx.x;
+    float* row = C + (size_t)p * ldc;
+    float racc = 0.0f;
+    double eacc = 0.0;
+    for (int64_t q = threadIdx.x; q < ldc; q += blockDim.x) {
+        if (q >= P) {
+            row[q] = 0.0f;
+            continue;
+        }
+        const float c = fminf(1.0f, fmaxf(-1.0f, row[q]));
+        const float dm2 = 2.0f - 2.0f * c, dp2 = 2.0f + 2.0f * c;
+        // coincident or antipodal pairs have no gradient direction: weight 0
+        const float a = (q == p || dm2 <= 0.0f) ? 0.0f : rsqrtf(dm2);
+        const float b = dp2 > 0.0f ? rsqrtf(dp2) : 0.0f;
+        row[q] = b - a;
+        racc += a + b;
+        eacc += (q == p ? 0.0 : sqrt((double)dm2)) + sqrt((double)dp2);
+    }
+    __shared__ float rs[8];
+    __shared__ double es[8];
+    for (int o = 16; o > 0; o >>= 1) {
+        racc += __shfl_xor_sync(0xffffffffu, racc, o);
+        eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        rs[threadIdx.x >> 5] = racc;
+        es[threadIdx.x >> 5] = eacc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float rt = 0.0f;
+        double et = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            rt += rs[i];
+            et += es[i];
+        }
+        r[p] = rt;
+        e_row[p] = et;
+    }
+}
+
+// Xi (P x d) -> Xi^T (d x ldt), zero in columns P .. ldt-1.
+__global__ void transpose_pad_kernel(const float* __restrict__ X, int P, int d, int64_t ldt, float* __restrict__ T)
+{
+    __shared__ float tile[32][33];
+    const int p0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int p = p0 + i, j = j0 + threadIdx.x;
+        tile[i][threadIdx.x] = (p < P && j < d) ? X[(size_t)p * d + j] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int j = j0 + i;
+        const int64_t p = p0 + threadIdx.x;
+        if (j < d && p < ldt) T[(size_t)j * ldt + p] = tile[threadIdx.x][i];
+    }
+}
+
+// Gradient -4 (r_p xi_p + Gm_p) (Gm = (B - A) Xi, stride ldg), the Euclidean
+// gradient dE/dxi_p (grad_out, may be NULL); with m, v: one Adam step on row p
+// of xi and its renormalisation.  One CTA per row.
+__global__ void __launch_bounds__(256) esym_step_kernel(float* __restrict__ xi, int d, const float* __restrict__ r,
+                                                        const float* __restrict__ Gm, int64_t ldg,
+                                                        float* __restrict__ grad_out, float* __restrict__ m,
+                                                        float* __restrict__ v, float lr, float b1, float b2,
+                                                        float b1t, float b2t, float eps)
+{
+    const int p = blockIdx.x;
+    float* x = xi + (size_t)p * d;
+    const float rp = r[p];
+    float ss = 0.0f;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const float g = -4.0f * fmaf(rp, x[j], Gm[(size_t)p * ldg + j]);
+        if (grad_out) grad_out[(size_t)p * d + j] = g;
+        if (!m) continue;
+        const size_t i = (size_t)p * d + j;
+        const float mi = b1 * m[i] + (1.0f - b1) * g;
+        const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        const float xn = x[j] - lr * (mi / (1.0f - b1t)) / (sqrtf(vi / (1.0f - b2t)) + eps);
+        x[j] = xn;
+        ss += xn * xn;
+    }
+    if (!m) return;
+    __shared__ float red[8];
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    float tot = 0.0f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
+    const float inv = tot > 0.0f ? rsqrtf(tot) : 1.0f;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) x[j] *= inv;
+}
+
+// Device workspace of one call (allocated per call: this is a set-up
+// routine, not part of the sum).  The GEMM stores whole 128-column blocks,
+// so the Gram rows (ldc) and the gradient rows (ldg) are padded to 128.
+struct DesignWork {
+    float *C = nullptr, *T = nullptr, *Gm = nullptr, *r = nullptr, *m = nullptr, *v = nullptr;
+    double* e = nullptr;
+    int64_t ldc = 0, ldg = 0;
+    ~DesignWork()
+    {
+        cudaFree(C);
+        cudaFree(T);
+        cudaFree(Gm);
+        cudaFree(r);
+        cudaFree(m);
+        cudaFree(v);
+        cudaFree(e);
+    }
+    cudaError_t alloc(int d, int P, bool adam)
+    {
+        ldc = ((int64_t)P + 127) / 128 * 128;
+        ldg = ((int64_t)d + 127) / 128 * 128;
+        cudaError_t err = cudaMalloc(&C, sizeof(float) * (size_t)P * ldc);
+        if (err == cudaSuccess) err = cudaMalloc(&T, sizeof(float) * (size_t)d * ldc);
+        if (err == cudaSuccess) err = cudaMalloc(&Gm, sizeof(float) * (size_t)P * ldg);
+        if (err == cudaSuccess) err = cudaMalloc(&r, sizeof(float) * (size_t)P);
+        if (err == cudaSuccess) err = cudaMalloc(&e, sizeof(double) * (size_t)P);
+        if (adam && err == cudaSuccess) err = cudaMalloc(&m, sizeof(float) * (size_t)P * d);
+        if (adam && err == cudaSuccess) err = cudaMalloc(&v, sizeof(float) * (size_t)P * d);
+        if (adam && err == cudaSuccess) err = cudaMemset(m, 0, sizeof(float) * (size_t)P * d);
+        if (adam && err == cudaSuccess) err = cudaMemset(v, 0, sizeof(float) * (size_t)P * d);
+        return err;
+    }
+};
+
+// Energy terms and the gradient pieces (r, Gm) of the rows in xi.
+cudaError_t esym_pieces(const float* xi, int d, int P, DesignWork& w, cudaStream_t st)
+{
+    cudaError_t e = qs_launch_project_fp32(xi, P, d, xi, P, w.C, w.ldc, st);  // C = Xi Xi^T
+    if (e != cudaSuccess) return e;
+    esym_weights_kernel<<<P, 256, 0, st>>>(w.C, P, w.ldc, w.r, w.e);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 tg((unsigned)((w.ldc + 31) / 32), (unsigned)((d + 31) / 32));
+    transpose_pad_kernel<<<tg, dim3(32, 8), 0, st>>>(xi, P, d, w.ldc, w.T);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // Gm[p][j] = sum_q W[p][q] Xi[q][j]: rows of W against rows of Xi^T, inner length ldc
+    return qs_launch_project_fp32(w.T, d, (int)w.ldc, w.C, P, w.Gm, w.ldg, st);
+}
+
+qs_status sum_energy(const DesignWork& w, int P, cudaStream_t st, double* energy)
+{
+    std::vector<double> e(P);
+    if (cudaMemcpyAsync(e.data(), w.e, sizeof(double) * (size_t)P, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return QS_ERR_CUDA;
+    double tot = 0.0;
+    for (int p = 0; p < P; ++p) tot += e[p];  // fixed order
+    *energy = -2.0 * tot;
+    return QS_OK;
+}
+
+qs_status design_args(const float* dirs, int d, int P)
+{
+    if (!dirs || d < 1 || P < 1) return QS_ERR_ARG;
+    if ((int64_t)P * (((int64_t)P + 127) / 128 * 128) > ((int64_t)1 << 31)) return QS_ERR_UNSUPPORTED;
+    return QS_OK;
+}
+
+}  // namespace
+
+extern "C" qs_status qs_distance_energy(const float* dirs_dev, int d, int P, double* energy, float* grad_dev,
+                                        void* stream)
+{
+    qs_status s = design_args(dirs_dev, d, P);
+    if (s == QS_ERR_ARG) return design_fail(QS_ERR_ARG, "qs_distance_energy: bad arguments");
+    if (s != QS_OK) return design_fail(s, "qs_distance_energy: P too large (P^2 floats of workspace)");
+    cudaStream_t st = (cudaStream_t)stream;
+    DesignWork w;
+    cudaError_t e = w.alloc(d, P, false);
+    if (e != cudaSuccess) return design_fail(QS_ERR_OOM, "qs_distance_energy: workspace allocation failed");
+    e = esym_pieces(dirs_dev, d, P, w, st);
+    if (e == cudaSuccess && grad_dev) {
+        // m == NULL: the kernel only reads xi and writes the gradient
+        esym_step_kernel<<<P, 256, 0, st>>>(const_cast<float*>(dirs_dev), d, w.r, w.Gm, w.ldg, grad_dev, nullptr,
+                                            nullptr, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return design_fail(QS_ERR_CUDA, cudaGetErrorString(e));
+    double E = 0.0;
+    if (sum_energy(w, P, st, &E) != QS_OK) return design_fail(QS_ERR_CUDA, "qs_distance_energy: readback");
+    if (energy) *energy = E;
+    return QS_OK;
+}
+
+extern "C" qs_status qs_distance_design(float* dirs_dev, int d, int P, int iters, double lr, double* energy,
+                                        void* stream)
+{
+    qs_status s = design_args(dirs_dev, d, P);
+    if (s == QS_ERR_ARG || iters < 0 || !(lr > 0.0))
+        return design_fail(QS_ERR_ARG, "qs_distance_design: bad arguments");
+    if (s != QS_OK) return design_fail(s, "qs_distance_design: P too large (P^2 floats of workspace)");
+    cudaStream_t st = (cudaStream_t)stream;
+    DesignWork w;
+    cudaError_t e = w.alloc(d, P, true);
+    if (e != cudaSuccess) return design_fail(QS_ERR_OOM, "qs_distance_design: workspace allocation failed");
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    double b1t = 1.0, b2t = 1.0;
+    for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+        e = esym_pieces(dirs_dev, d, P, w, st);
+        if (e != cudaSuccess) break;
+        b1t *= b1;
+        b2t *= b2;
+        esym_step_kernel<<<P, 256, 0, st>>>(dirs_dev, d, w.r, w.Gm, w.ldg, nullptr, w.m, w.v, (float)lr, b1, b2,
+                                            (float)b1t, (float)b2t, eps);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && energy) e = esym_pieces(dirs_dev, d, P, w, st);
+    if (e != cudaSuccess) return design_fail(QS_ERR_CUDA, cudaGetErrorString(e));
+    if (energy && sum_energy(w, P, st, energy) != QS_OK)
+        return design_fail(QS_ERR_CUDA, "qs_distance_design: readback");
+    if (!energy && cudaStreamSynchronize(st) != cudaSuccess)
+        return design_fail(QS_ERR_CUDA, "qs_distance_design: synchronise");
+    return QS_OK;
+}

@@ -478,6 +478,9 @@ qs_status qs_directions(qs_dirs kind, int d, int P, uint64_t seed, float* out)
         }
         return QS_OK;
     }
+    if (kind == QS_DIR_DISTANCE)
+        return fail(QS_ERR_UNSUPPORTED, "qs_directions: distance designs are optimised on the GPU "
+                                        "(QS_DIR_DISTANCE in a plan, or qs_distance_design)");
     return fail(QS_ERR_ARG, "qs_directions: unknown kind %d", (int)kind);
 }
 
@@ -506,6 +509,8 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     if (os != 2.0) return fail(QS_ERR_UNSUPPORTED, "qs_plan_create: only oversampling 2 is supported");
     if (D.max_n < 0 || D.max_m < 0) return fail(QS_ERR_ARG, "qs_plan_create: max_n / max_m must be >= 0");
     if (D.dirs == QS_DIR_USER && !D.dirs_host) return fail(QS_ERR_ARG, "qs_plan_create: dirs_host is NULL");
+    if (D.dirs < QS_DIR_USER || D.dirs > QS_DIR_DISTANCE)
+        return fail(QS_ERR_ARG, "qs_plan_create: unknown direction kind %d", (int)D.dirs);
     if (D.dirs == QS_DIR_FIBONACCI && D.d != 3)
         return fail(QS_ERR_ARG, "qs_plan_create: Fibonacci directions need d = 3");
 
@@ -558,7 +563,22 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
             dirs[i] = desc->dirs_host[i];
         }
     } else {
-        qs_status st = qs_directions(D.dirs, d, P, D.seed, dirs.data());
+        const bool distance = D.dirs == QS_DIR_DISTANCE;
+        qs_status st = qs_directions(distance ? QS_DIR_ORTHOGONAL : D.dirs, d, P, D.seed, dirs.data());
+        if (st == QS_OK && distance) {
+            // refine the seeded orthogonal start into a distance design on the device
+            float* d_tmp = nullptr;
+            const size_t bytes = dirs.size() * sizeof(float);
+            if (cudaMalloc(&d_tmp, bytes) != cudaSuccess) {
+                st = QS_ERR_OOM;
+            } else {
+                if (cudaMemcpy(d_tmp, dirs.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) st = QS_ERR_CUDA;
+                if (st == QS_OK) st = qs_distance_design(d_tmp, d, P, 300, 0.05 / sqrt((double)d), nullptr, nullptr);
+                if (st == QS_OK && cudaMemcpy(dirs.data(), d_tmp, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+                    st = QS_ERR_CUDA;
+                cudaFree(d_tmp);
+            }
+        }
         if (st != QS_OK) {
             free_plan(p);
             return st;
