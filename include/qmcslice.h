@@ -312,8 +312,10 @@ qs_status qs_plan_variants(qs_plan plan, unsigned int* available, int* current);
  * Distance QMC designs (Sec. 2.3, eq. distance-mmd with s = d/2; Sec. 4.1,
  * "Distance"; the symmetric energy of eq. distance-sym):
  *   E_sym(xi) = -2 sum_{p,q} (|xi_p - xi_q| + |xi_p + xi_q|)
- * over P unit directions in R^d, minimised by Adam (beta1 0.9, beta2 0.999,
- * step size lr) with every step followed by renormalising the rows.
+ * over P unit directions in R^d, minimised by Adam (beta1 0.9, beta2 0.999)
+ * on the gradient's component tangent to the sphere, the step annealed from
+ * lr to lr/100 (cosine) over the `iters` steps, every step followed by
+ * renormalising the rows.
  *
  * qs_distance_design: runs `iters` steps on the P x d FP32 rows in dirs_dev
  * (device, caller-owned, updated in place; start from any unit rows, e.g.

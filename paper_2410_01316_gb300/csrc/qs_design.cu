@@ -3,8 +3,9 @@
 //   E_sym(xi) = E((xi, -xi)) = -2 sum_{p,q} (|xi_p - xi_q| + |xi_p + xi_q|),
 // the energy of the points together with their antipodes (the sliced
 // integrand is even in xi, so the antipodes come for free).  As in Sec. 4.1
-// the minimiser is found with Adam; each step is followed by renormalising
-// the rows onto the sphere.
+// the minimiser is found with Adam (on the tangential gradient, with the step
+// annealed over the run); each step is followed by renormalising the rows
+// onto the sphere.
 //
 // For unit rows |xi_p -+ xi_q|^2 = 2 -+ 2 c_pq with c = Xi Xi^T, so with
 // a_pq = 1/sqrt(2 - 2c) (0 on the diagonal) and b_pq = 1/sqrt(2 + 2c):
@@ -93,21 +94,41 @@ __global__ void transpose_pad_kernel(const float* __restrict__ X, int P, int d, 
 
 // Gradient -4 (r_p xi_p + Gm_p) (Gm = (B - A) Xi, stride ldg), the Euclidean
 // gradient dE/dxi_p (grad_out, may be NULL); with m, v: one Adam step on row p
-// of xi and its renormalisation.  One CTA per row.
+// of xi along the tangential part g - <g, xi_p> xi_p (the radial part only
+// changes the length, which the renormalisation discards, and would dominate
+// Adam's second moment), then the renormalisation.  One CTA per row.
+__device__ __forceinline__ float block_sum(float v, float* red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float tot = 0.0f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
+    return tot;
+}
+
 __global__ void __launch_bounds__(256) esym_step_kernel(float* __restrict__ xi, int d, const float* __restrict__ r,
                                                         const float* __restrict__ Gm, int64_t ldg,
                                                         float* __restrict__ grad_out, float* __restrict__ m,
                                                         float* __restrict__ v, float lr, float b1, float b2,
                                                         float b1t, float b2t, float eps)
 {
+    __shared__ float red[8];
     const int p = blockIdx.x;
     float* x = xi + (size_t)p * d;
     const float rp = r[p];
-    float ss = 0.0f;
+    float dot = 0.0f;
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
         const float g = -4.0f * fmaf(rp, x[j], Gm[(size_t)p * ldg + j]);
         if (grad_out) grad_out[(size_t)p * d + j] = g;
-        if (!m) continue;
+        dot = fmaf(g, x[j], dot);
+    }
+    if (!m) return;
+    dot = block_sum(dot, red);
+    float ss = 0.0f;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const float g = -4.0f * fmaf(rp, x[j], Gm[(size_t)p * ldg + j]) - dot * x[j];
         const size_t i = (size_t)p * d + j;
         const float mi = b1 * m[i] + (1.0f - b1) * g;
         const float vi = b2 * v[i] + (1.0f - b2) * g * g;
@@ -115,15 +136,9 @@ __global__ void __launch_bounds__(256) esym_step_kernel(float* __restrict__ xi, 
         v[i] = vi;
         const float xn = x[j] - lr * (mi / (1.0f - b1t)) / (sqrtf(vi / (1.0f - b2t)) + eps);
         x[j] = xn;
-        ss += xn * xn;
+        ss = fmaf(xn, xn, ss);
     }
-    if (!m) return;
-    __shared__ float red[8];
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
-    __syncthreads();
-    float tot = 0.0f;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
+    const float tot = block_sum(ss, red);
     const float inv = tot > 0.0f ? rsqrtf(tot) : 1.0f;
     for (int j = threadIdx.x; j < d; j += blockDim.x) x[j] *= inv;
 }
@@ -241,7 +256,10 @@ extern "C" qs_status qs_distance_design(float* dirs_dev, int d, int P, int iters
         if (e != cudaSuccess) break;
         b1t *= b1;
         b2t *= b2;
-        esym_step_kernel<<<P, 256, 0, st>>>(dirs_dev, d, w.r, w.Gm, w.ldg, nullptr, w.m, w.v, (float)lr, b1, b2,
+        // cosine annealing from lr to lr/100: a constant Adam step keeps moving by ~lr on a
+        // deterministic objective instead of settling
+        const double lr_t = lr * (0.01 + 0.99 * 0.5 * (1.0 + cos(3.14159265358979323846 * it / iters)));
+        esym_step_kernel<<<P, 256, 0, st>>>(dirs_dev, d, w.r, w.Gm, w.ldg, nullptr, w.m, w.v, (float)lr_t, b1, b2,
                                             (float)b1t, (float)b2t, eps);
         e = cudaGetLastError();
     }
