@@ -3,13 +3,13 @@
 //
 //     U[p][n] = u_{n,p} = G tau <x_n, xi_p>,   D = X Xi_s^T on the tensor cores
 //
-// One CTA computes a 128-point x 256-slice tile.  TMA streams K-major tiles
-// of the points (A, 128 rows) and of the scaled directions (B, 256 rows) into
-// 64-byte-swizzled shared memory (64-byte k-slabs, two stages, 97 KB per CTA,
-// so two CTAs share an SM and one's epilogue overlaps the other's MMAs); one
-// thread issues tcgen05.mma with the FP32 accumulator in tensor memory (256
-// columns); all four warps read the accumulator back with tcgen05.ld and store
-// U with one coalesced 128-byte row segment per warp and slice.
+// A persistent kernel, one CTA per SM, computes 128-point x 256-slice tiles.
+// TMA streams K-major slabs of the points (A, 128 rows) and of the scaled
+// directions (B, 256 rows) into 64-byte-swizzled shared memory through a
+// ring of stages; one thread issues tcgen05.mma into one of two 256-column
+// FP32 accumulators in tensor memory while four warps read the other back
+// with tcgen05.ld and store U with one coalesced 128-byte row segment per
+// warp and slice.
 //
 // Two precision forms:
 //   BF16x3  x = x_hi + x_lo and xi = xi_hi + xi_lo in BF16 (round to nearest);
@@ -145,12 +145,12 @@ template <int KIND>
 struct TcCfg;
 template <>
 struct TcCfg<0> {  // BF16x3
-    static constexpr int ESZ = 2, BK = 32, STAGES = 2, NOPS = 2, KSTEP = 16;
+    static constexpr int ESZ = 2, BK = 32, NOPS = 2, KSTEP = 16;
     static constexpr uint32_t IDESC = make_idesc(1, TILE_M, TILE_N);
 };
 template <>
 struct TcCfg<1> {  // TF32
-    static constexpr int ESZ = 4, BK = 16, STAGES = 4, NOPS = 1, KSTEP = 8;
+    static constexpr int ESZ = 4, BK = 16, NOPS = 1, KSTEP = 8;
     static constexpr uint32_t IDESC = make_idesc(2, TILE_M, TILE_N);
 };
 
@@ -164,49 +164,83 @@ __host__ __device__ constexpr int stage_bytes()
     return TcCfg<KIND>::NOPS * (A_BYTES + B_BYTES);
 }
 
+
+// ---------------------------------------------------------------------------
+// Persistent form: one CTA per SM walks the tiles t = blockIdx.x, +gridDim.x,
+// ... (slice tile fastest, so CTAs running together share point tiles in L2).
+// Warp 0 lane 0 streams k-slabs through a STAGES-deep ring; warp 1 lane 0
+// issues the MMAs into one of two 256-column TMEM accumulators; warps 2..5
+// drain the other accumulator to U meanwhile, so a tile's epilogue overlaps
+// the next tile's MMAs.  Barriers: full/empty per ring stage, tfull/tempty
+// per accumulator (tempty counts the four epilogue warps).  Every wait is
+// bounded; a role that gives up raises the shared abort flag and the error
+// flag, and the others stop at their next tile.
+// ---------------------------------------------------------------------------
 template <int KIND>
-__host__ __device__ constexpr int tc_smem_bytes()
+struct PCfg;
+template <>
+struct PCfg<0> {  // BF16x3: 48 KB stages
+    static constexpr int STAGES = 4;
+};
+template <>
+struct PCfg<1> {  // TF32: 24 KB stages
+    static constexpr int STAGES = 8;
+};
+
+template <int KIND>
+__host__ __device__ constexpr int tcp_smem_bytes()
 {
-    return 1024 + TcCfg<KIND>::STAGES * stage_bytes<KIND>() + 256;
+    return 1024 + PCfg<KIND>::STAGES * stage_bytes<KIND>() + 256;
 }
 
-// mA0/mA1: points (hi/lo for BF16x3), mB0/mB1: scaled directions.
+constexpr int TCP_THREADS = 192;
+
 template <int KIND>
-__global__ void __launch_bounds__(128, 2)
-    tc_project_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
-                      const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, int d,
-                      int P, float* __restrict__ U, int64_t ldU, unsigned int* flag)
+__global__ void __launch_bounds__(TCP_THREADS, 1)
+    tc_project_persistent(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+                          const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, int d,
+                          int P, int64_t N, float* __restrict__ U, int64_t ldU, unsigned int* flag)
 {
     using C = TcCfg<KIND>;
+    constexpr int ST = PCfg<KIND>::STAGES;
     constexpr int SB = stage_bytes<KIND>();
     extern __shared__ uint8_t smem_raw[];
+    __shared__ volatile int abort_all;
     const uint32_t base = smem_u32(smem_raw);
     const uint32_t tiles = (base + 1023u) & ~1023u;
-    const uint32_t bars = tiles + C::STAGES * SB;
-    const uint32_t full0 = bars;                       // full[s]  = full0 + 8 s
-    const uint32_t empty0 = bars + 8 * C::STAGES;      // empty[s] = empty0 + 8 s
-    const uint32_t done = bars + 16 * C::STAGES;
-    const uint32_t tmem_slot = done + 8;
+    const uint32_t bars = tiles + ST * SB;
+    const uint32_t full0 = bars;              // full[s]   = full0 + 8 s
+    const uint32_t empty0 = bars + 8 * ST;    // empty[s]  = empty0 + 8 s
+    const uint32_t tfull0 = bars + 16 * ST;   // tfull[a]  = tfull0 + 8 a
+    const uint32_t tempty0 = tfull0 + 16;     // tempty[a] = tempty0 + 8 a
+    const uint32_t drain = tempty0 + 16;      // all MMAs of the CTA have completed
+    const uint32_t tmem_slot = drain + 8;
     uint32_t* tmem_slot_ptr = reinterpret_cast<uint32_t*>(smem_raw + (tmem_slot - base));
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int p0 = blockIdx.x * TILE_N;
-    const int n0 = blockIdx.y * TILE_M;
     const int nkb = (d + C::BK - 1) / C::BK;
+    const int ptiles = (P + TILE_N - 1) / TILE_N;
+    const int64_t ntiles = (N + TILE_M - 1) / TILE_M;
+    const int64_t T = ntiles * ptiles;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < C::STAGES; ++s) {
+        for (int s = 0; s < ST; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        mbar_init(done, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull0 + 8 * a, 1);
+            mbar_init(tempty0 + 8 * a, 4);
+        }
+        mbar_init(drain, 1);
+        abort_all = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tmem_slot),
-                     "r"(TILE_N)
+                     "r"(2 * TILE_N)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -216,89 +250,122 @@ __global__ void __launch_bounds__(128, 2)
     const uint32_t tmem = *tmem_slot_ptr;
 
     if (warp == 0 && lane == 0) {
-        // TMA producer
+        // TMA producer: slab g of the CTA's sequence uses stage g % ST
         bool ok = true;
-        int issued = 0;
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % C::STAGES;
-            const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-            if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) {
-                ok = false;
-                break;
+        int64_t g = 0;
+        for (int64_t t = blockIdx.x; t < T && ok && !abort_all; t += gridDim.x) {
+            const int p0 = (int)(t % ptiles) * TILE_N;
+            const int n0 = (int)(t / ptiles) * TILE_M;
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+                const int s = (int)(g % ST);
+                const uint32_t ph = (uint32_t)(g / ST) & 1u;
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t fb = full0 + 8 * s;
+                const uint32_t st = tiles + s * SB;
+                const int kc = kb * C::BK;
+                mbar_expect_tx(fb, SB);
+                tma_load_2d(st, &mA0, kc, n0, fb);
+                if (C::NOPS == 2) tma_load_2d(st + A_BYTES, &mA1, kc, n0, fb);
+                tma_load_2d(st + C::NOPS * A_BYTES, &mB0, kc, p0, fb);
+                if (C::NOPS == 2) tma_load_2d(st + C::NOPS * A_BYTES + B_BYTES, &mB1, kc, p0, fb);
             }
-            const uint32_t full = full0 + 8 * s;
-            const uint32_t st = tiles + s * SB;
-            const int kc = kb * C::BK;
-            mbar_expect_tx(full, SB);
-            tma_load_2d(st, &mA0, kc, n0, full);
-            if (C::NOPS == 2) tma_load_2d(st + A_BYTES, &mA1, kc, n0, full);
-            tma_load_2d(st + C::NOPS * A_BYTES, &mB0, kc, p0, full);
-            if (C::NOPS == 2) tma_load_2d(st + C::NOPS * A_BYTES + B_BYTES, &mB1, kc, p0, full);
-            issued = kb + 1;
         }
-        // make sure no copy of this CTA is still in flight when it exits
-        for (int kb = (issued > C::STAGES ? issued - C::STAGES : 0); kb < issued; ++kb)
-            if (!mbar_wait(full0 + 8 * (kb % C::STAGES), (uint32_t)(kb / C::STAGES) & 1u)) ok = false;
-        if (!ok) atomicOr(flag, QS_FLAG_TIMEOUT);
+        // no copy of this CTA may still be in flight when it exits
+        for (int64_t h = (g > ST ? g - ST : 0); h < g; ++h)
+            if (!mbar_wait(full0 + 8 * (int)(h % ST), (uint32_t)(h / ST) & 1u)) ok = false;
+        if (!ok) {
+            abort_all = 1;
+            atomicOr(flag, QS_FLAG_TIMEOUT);
+        }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         bool ok = true;
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % C::STAGES;
-            const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-            if (!mbar_wait(full0 + 8 * s, ph)) {
+        int64_t g = 0;
+        int i = 0;
+        for (int64_t t = blockIdx.x; t < T && ok && !abort_all; t += gridDim.x, ++i) {
+            const int a = i & 1;
+            if (!mbar_wait(tempty0 + 8 * a, (((uint32_t)i >> 1) & 1u) ^ 1u)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            const uint32_t st = tiles + s * SB;
-            const uint32_t a0 = st, a1 = st + A_BYTES;
-            const uint32_t b0 = st + C::NOPS * A_BYTES, b1 = b0 + B_BYTES;
-#pragma unroll
-            for (int k = 0; k < C::BK / C::KSTEP; ++k) {
-                const uint32_t off = (uint32_t)(k * C::KSTEP * C::ESZ);  // 32 bytes per step
-                const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-                if (KIND == 0) {
-                    mma_f16(tmem, sw64_desc(a0 + off), sw64_desc(b0 + off), C::IDESC, acc);
-                    mma_f16(tmem, sw64_desc(a0 + off), sw64_desc(b1 + off), C::IDESC, 1u);
-                    mma_f16(tmem, sw64_desc(a1 + off), sw64_desc(b0 + off), C::IDESC, 1u);
-                } else {
-                    mma_tf32(tmem, sw64_desc(a0 + off), sw64_desc(b0 + off), C::IDESC, acc);
+            const uint32_t dt = tmem + (uint32_t)(a * TILE_N);
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+                const int s = (int)(g % ST);
+                if (!mbar_wait(full0 + 8 * s, (uint32_t)(g / ST) & 1u)) {
+                    ok = false;
+                    break;
                 }
-            }
-            mma_commit(empty0 + 8 * s);
-        }
-        mma_commit(done);  // arrives once every MMA issued above has completed
-        if (!ok) atomicOr(flag, QS_FLAG_TIMEOUT);
-    }
-    __syncwarp();
-
-    // epilogue: warp w owns TMEM lanes 32w..32w+31 = points n0 + 32w + lane.
-    // Lanes leave the wait loop independently; the vote reconverges the warp
-    // before the warp-collective tcgen05.ld.
-    const bool got = __all_sync(0xffffffffu, mbar_wait(done, 0));
-    tc_fence_after();
-    if (got) {
-        const int64_t n = (int64_t)n0 + 32 * warp + lane;
-        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-#pragma unroll 1
-        for (int c = 0; c < TILE_N; c += 32) {
-            float v[32];
-            __syncwarp();
-            tmem_ld32(trow + (uint32_t)c, v);
-            const int pc = p0 + c;
+                tc_fence_after();
+                const uint32_t st = tiles + s * SB;
+                const uint32_t a0 = st, a1 = st + A_BYTES;
+                const uint32_t b0 = st + C::NOPS * A_BYTES, b1 = b0 + B_BYTES;
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (pc + j < P) U[(size_t)(pc + j) * ldU + n] = v[j];
+                for (int k = 0; k < C::BK / C::KSTEP; ++k) {
+                    const uint32_t off = (uint32_t)(k * C::KSTEP * C::ESZ);
+                    const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+                    if (KIND == 0) {
+                        mma_f16(dt, sw64_desc(a0 + off), sw64_desc(b0 + off), C::IDESC, acc);
+                        mma_f16(dt, sw64_desc(a0 + off), sw64_desc(b1 + off), C::IDESC, 1u);
+                        mma_f16(dt, sw64_desc(a1 + off), sw64_desc(b0 + off), C::IDESC, 1u);
+                    } else {
+                        mma_tf32(dt, sw64_desc(a0 + off), sw64_desc(b0 + off), C::IDESC, acc);
+                    }
+                }
+                mma_commit(empty0 + 8 * s);
+            }
+            if (ok) mma_commit(tfull0 + 8 * a);  // arrives once the tile's MMAs have completed
         }
-    } else if (lane == 0) {
-        atomicOr(flag, QS_FLAG_TIMEOUT);
+        // before the tensor memory is freed, every MMA issued above must have finished
+        mma_commit(drain);
+        if (!mbar_wait(drain, 0)) ok = false;
+        if (!ok) {
+            abort_all = 1;
+            atomicOr(flag, QS_FLAG_TIMEOUT);
+        }
+    } else if (warp >= 2) {
+        // epilogue: TMEM lane quarter q = warp % 4 holds points n0 + 32 q + lane
+        const int q = warp & 3;
+        int i = 0;
+        for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++i) {
+            if (abort_all) break;
+            const int a = i & 1;
+            const bool got = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * a, ((uint32_t)i >> 1) & 1u));
+            if (!got) {
+                if (lane == 0) {
+                    abort_all = 1;
+                    atomicOr(flag, QS_FLAG_TIMEOUT);
+                }
+                break;
+            }
+            tc_fence_after();
+            const int p0 = (int)(t % ptiles) * TILE_N;
+            const int64_t n = (t / ptiles) * TILE_M + 32 * q + lane;
+            const uint32_t trow = tmem + (uint32_t)(a * TILE_N) + ((uint32_t)(32 * q) << 16);
+#pragma unroll 1
+            for (int c = 0; c < TILE_N; c += 32) {
+                float v[32];
+                __syncwarp();
+                tmem_ld32(trow + (uint32_t)c, v);
+                const int pc = p0 + c;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (pc + j < P) U[(size_t)(pc + j) * ldU + n] = v[j];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8 * a) : "memory");
+        }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TILE_N) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TILE_N)
+                     : "memory");
     }
 }
 
@@ -425,18 +492,27 @@ cudaError_t qs_launch_project_tc(int kind, const void* maps, int64_t N, int d, i
 {
     if (N <= 0) return cudaSuccess;
     const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(maps);
-    dim3 grid((unsigned)((P + TILE_N - 1) / TILE_N), (unsigned)((N + TILE_M - 1) / TILE_M));
-    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t T = ((N + TILE_M - 1) / TILE_M) * ((P + TILE_N - 1) / TILE_N);
+    const unsigned grid = (unsigned)(T < sms ? T : sms);
     if (kind == 0) {
-        const int smem = tc_smem_bytes<0>();
-        cudaError_t e = cudaFuncSetAttribute(tc_project_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        const int smem = tcp_smem_bytes<0>();
+        cudaError_t e =
+            cudaFuncSetAttribute(tc_project_persistent<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        tc_project_kernel<0><<<grid, 128, smem, st>>>(m[0], m[1], m[2], m[3], d, P, U, ldU, flag);
+        tc_project_persistent<0><<<grid, TCP_THREADS, smem, st>>>(m[0], m[1], m[2], m[3], d, P, N, U, ldU, flag);
     } else {
-        const int smem = tc_smem_bytes<1>();
-        cudaError_t e = cudaFuncSetAttribute(tc_project_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        const int smem = tcp_smem_bytes<1>();
+        cudaError_t e =
+            cudaFuncSetAttribute(tc_project_persistent<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        tc_project_kernel<1><<<grid, 128, smem, st>>>(m[0], m[0], m[2], m[2], d, P, U, ldU, flag);
+        tc_project_persistent<1><<<grid, TCP_THREADS, smem, st>>>(m[0], m[0], m[2], m[2], d, P, N, U, ldU, flag);
     }
     return cudaGetLastError();
 }
