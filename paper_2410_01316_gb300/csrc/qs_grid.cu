@@ -762,6 +762,16 @@ __global__ void deriv_table_kernel(const double* __restrict__ c, const double* _
 // memory (double-buffered cp.async) with its first cells repeated after the
 // end, so the W taps of a target are read without wrapping.
 // ---------------------------------------------------------------------------
+// Interpolation of the filtered rows at the targets, per slice group.  Per
+// slice, the CTA first locates its targets' bins; when they span fewer than
+// QWIN bins (clustered projections) it expands the row into the bins'
+// polynomials in t (the tap polynomials of qs_taps summed against the row),
+// and each target is one degree-(K-1) Horner evaluation; otherwise each
+// target takes its W taps from the row.  Both evaluate the same polynomial
+// sum_j h[l0 + j] tap_j, rounded differently; which one a target takes
+// depends only on the data, so results are reproducible.
+constexpr int QWIN = 256;
+
 template <int W, bool FUSED, int DMAX, int TPT>
 __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const float* __restrict__ y)
 {
@@ -778,6 +788,24 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
     const int p1 = (int)(((int64_t)(g + 1) * L.P) / S);
     const int64_t m0 = (int64_t)blockIdx.x * IT_THREADS * TPT;
     const int mask = G - 1;
+
+    // windowed coefficient path: a_jk of tap_j(t) = sum_k a_jk t^k (t = 2 s;
+    // from the even / odd tap polynomials), the bins' polynomials Q, the
+    // block's bin range
+    constexpr int KQ = qs_moment_count(W);
+    constexpr int TQ = qs_tap_terms(W);
+    const int H0 = (G >> 1) + W / 2;
+    __shared__ float atab[W * KQ];
+    __shared__ float qwin[KQ * QWIN];
+    __shared__ int s_kmin[IT_THREADS / 32], s_kmax[IT_THREADS / 32];
+    for (int idx = threadIdx.x; idx < W * KQ; idx += IT_THREADS) {
+        const int j = idx / KQ, k = idx - j * KQ;
+        const int jj = j < W / 2 ? j : W - 1 - j;
+        const int i2 = k >> 1;
+        float a = 0.0f;
+        if (i2 < TQ) a = (k & 1) ? (j < W / 2 ? L.win.o[jj][i2] : -L.win.o[jj][i2]) : L.win.e[jj][i2];
+        atab[idx] = ldexpf(a, -k);
+    }
 
     float yr[FUSED ? DMAX * TPT : 1];
     float hi[TPT], lo[TPT];
@@ -819,28 +847,84 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
             cp_async_wait<0>();
         }
         __syncthreads();
+        // target positions: u, the bin kb = l0 + H0 in [0, G] (l0 the first
+        // tap cell, unwrapped) and t = 2 s in (-1, 1]
+        float uu[TPT], tt[TPT];
+        int kb[TPT];
+        int kmin = INT_MAX, kmax = INT_MIN;
 #pragma unroll
         for (int i = 0; i < TPT; ++i) {
-            if (!live[i]) continue;
-            float u;
-            if (FUSED) {
-                const float* xs = L.xi_s + (size_t)p * L.d;
-                u = 0.0f;
+            float u = 0.0f;
+            if (live[i]) {
+                if (FUSED) {
+                    const float* xs = L.xi_s + (size_t)p * L.d;
 #pragma unroll
-                for (int j = 0; j < DMAX; ++j)
-                    if (j < L.d) u = fmaf(__ldg(&xs[j]), yr[i * DMAX + j], u);
-            } else {
-                u = row[G + ROW_PAD + threadIdx.x + i * IT_THREADS];
+                    for (int j = 0; j < DMAX; ++j)
+                        if (j < L.d) u = fmaf(__ldg(&xs[j]), yr[i * DMAX + j], u);
+                } else {
+                    u = row[G + ROW_PAD + threadIdx.x + i * IT_THREADS];
+                }
+                u = qs_check_u(u, L.half_G, L.flag);
             }
-            u = qs_check_u(u, L.half_G, L.flag);
-            int l0;
-            float tap[W];
-            qs_taps<W>(u, L.win, l0, tap);
-            const float* h = row + (l0 & mask);
-            float t = 0.0f;
+            const float fl = ceilf(u - (float)(W / 2));
+            uu[i] = u;
+            kb[i] = (int)fl + H0;
+            tt[i] = 2.0f * ((u - fl) - ((float)(W / 2) - 0.5f));
+            if (live[i]) {
+                kmin = min(kmin, kb[i]);
+                kmax = max(kmax, kb[i]);
+            }
+        }
+        kmin = __reduce_min_sync(0xffffffffu, kmin);
+        kmax = __reduce_max_sync(0xffffffffu, kmax);
+        if ((threadIdx.x & 31) == 0) {
+            s_kmin[threadIdx.x >> 5] = kmin;
+            s_kmax[threadIdx.x >> 5] = kmax;
+        }
+        __syncthreads();
+        kmin = INT_MAX;
+        kmax = INT_MIN;
 #pragma unroll
-            for (int j = 0; j < W; ++j) t = fmaf(h[j], tap[j], t);
-            qs_two_sum(hi[i], lo[i], t);
+        for (int w = 0; w < IT_THREADS / 32; ++w) {
+            kmin = min(kmin, s_kmin[w]);
+            kmax = max(kmax, s_kmax[w]);
+        }
+        if (kmin <= kmax && kmax - kmin < QWIN) {
+            // the CTA's targets of this slice fall in few bins: per bin b the
+            // polynomial Q_b(t) = sum_j h[b + j] tap_j(t) (coefficients
+            // sum_j a_jk h[b + j]), then a target costs a Horner evaluation
+            const int nb = kmax - kmin + 1;
+            for (int idx = threadIdx.x; idx < nb * KQ; idx += IT_THREADS) {
+                const int b = idx / KQ, k = idx - b * KQ;
+                const int c0 = kmin + b - H0;
+                float q = 0.0f;
+#pragma unroll
+                for (int j = 0; j < W; ++j) q = fmaf(atab[j * KQ + k], row[(c0 + j) & mask], q);
+                qwin[k * QWIN + b] = q;  // coefficient-major: lanes at different bins hit different banks
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < TPT; ++i) {
+                if (!live[i]) continue;
+                const float* qb = qwin + (kb[i] - kmin);
+                float v = qb[(KQ - 1) * QWIN];
+#pragma unroll
+                for (int k = KQ - 2; k >= 0; --k) v = fmaf(v, tt[i], qb[k * QWIN]);
+                qs_two_sum(hi[i], lo[i], v);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < TPT; ++i) {
+                if (!live[i]) continue;
+                int l0;
+                float tap[W];
+                qs_taps<W>(uu[i], L.win, l0, tap);
+                const float* h = row + (l0 & mask);
+                float t = 0.0f;
+#pragma unroll
+                for (int j = 0; j < W; ++j) t = fmaf(h[j], tap[j], t);
+                qs_two_sum(hi[i], lo[i], t);
+            }
         }
         __syncthreads();  // the buffer just read is refilled two slices later
     }
