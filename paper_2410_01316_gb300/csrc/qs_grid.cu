@@ -449,17 +449,39 @@ __device__ __forceinline__ void moment_grid(const qs_launch& L, const float* __r
 
     {
         int* lanecol = lanewin + (threadIdx.x & 31);
+        // full batches of PF points, software-pipelined: the next batch's
+        // loads are in flight while the current one is spread
+        const int64_t step = (int64_t)PF * blockDim.x;
         int64_t n0 = threadIdx.x;
-        for (; n0 + (int64_t)(PF - 1) * blockDim.x < L.N; n0 += (int64_t)PF * blockDim.x) {
-            float ub[PF], wb[PF];
+        bool have = n0 + (int64_t)(PF - 1) * blockDim.x < L.N;
+        float ub[PF], wb[PF];
+        if (have) {
 #pragma unroll
             for (int k = 0; k < PF; ++k) {
                 const int64_t n = n0 + (int64_t)k * blockDim.x;
                 ub[k] = spread_u<W, FUSED>(L, x, urow, xi_sm, n);
                 wb[k] = w ? __ldg(&w[n]) : 1.0f;
             }
+        }
+        while (have) {
+            const int64_t n1 = n0 + step;
+            const bool next = n1 + (int64_t)(PF - 1) * blockDim.x < L.N;
+            float un[PF], wn[PF];
+#pragma unroll
+            for (int k = 0; k < PF; ++k) {
+                const int64_t n = n1 + (int64_t)k * blockDim.x;
+                un[k] = next ? spread_u<W, FUSED>(L, x, urow, xi_sm, n) : 0.0f;
+                wn[k] = next ? (w ? __ldg(&w[n]) : 1.0f) : 0.0f;
+            }
 #pragma unroll
             for (int k = 0; k < PF; ++k) moment_point<W, LW>(L, ub[k], wb[k], scale, H, tab, lanecol, wbase);
+#pragma unroll
+            for (int k = 0; k < PF; ++k) {
+                ub[k] = un[k];
+                wb[k] = wn[k];
+            }
+            n0 = n1;
+            have = next;
         }
         for (; n0 < L.N; n0 += blockDim.x)
             moment_point<W, LW>(L, spread_u<W, FUSED>(L, x, urow, xi_sm, n0), w ? __ldg(&w[n0]) : 1.0f, scale, H,
