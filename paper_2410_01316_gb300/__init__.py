@@ -177,6 +177,26 @@ class QSPlan:
                                     y.data_ptr(), M, out.data_ptr(), _stream_handle(stream)), "qs_sum")
         return out
 
+    def sum_sorted(self, x, w, y, out=None, stream=None):
+        """The sliced negative-distance sum computed exactly by sorting each slice (no Fourier
+        truncation); negdist plans with d <= 64.  The first call allocates the sorting workspace."""
+        import torch
+
+        self._check_points(x, "x")
+        self._check_points(y, "y")
+        if x.dim() != 2 or x.shape[1] != self.d or y.dim() != 2 or y.shape[1] != self.d:
+            raise ValueError("x and y must have shape (*, d)")
+        N, M = x.shape[0], y.shape[0]
+        if w is not None:
+            self._check_points(w, "w", rows=N)
+        if out is None:
+            out = torch.empty(M, dtype=torch.float32, device=self.device)
+        else:
+            self._check_points(out, "out", rows=M)
+        _lib.check(self._lib.qs_sum_sorted(self._handle, x.data_ptr(), N, None if w is None else w.data_ptr(),
+                                           y.data_ptr(), M, out.data_ptr(), _stream_handle(stream)), "qs_sum_sorted")
+        return out
+
     def project(self, x, out=None, stream=None):
         """u[p, n] = G tau <x_n, xi_p> in the plan's projection form (P x N tensor)."""
         import torch

@@ -141,6 +141,7 @@ struct qs_plan_s {
     void* d_xi_lo;        // P x ldk (BF16x3 only)
     void* d_xs_hi;        // max(max_n, max_m) x ldk staging of the points
     void* d_xs_lo;        // (BF16x3 only)
+    void* d_sortws = nullptr;  // sorting-slicing workspace, allocated by the first qs_sum_sorted
     alignas(64) unsigned char tmaps[4][128];  // CUtensorMap: points hi/lo, directions hi/lo
     // stage timing (qs_set_timing)
     int timing;
@@ -207,6 +208,11 @@ __host__ __device__ inline int qs_interp_tpt(bool fused, int d)
 // ---------------------------------------------------------------------------
 // launchers (defined in the .cu files); return cudaSuccess or the launch error
 // ---------------------------------------------------------------------------
+int qs_sort_chunk(int P);
+size_t qs_sort_workspace_bytes(int P, int64_t max_n, int64_t max_m);
+cudaError_t qs_launch_sum_sorted(const float* x, int64_t N, const float* w, const float* y, int64_t M,
+                                 const float* xi_s, int d, int P, double amp, void* ws, int64_t max_n,
+                                 int64_t max_m, float* s, unsigned int* flag, cudaStream_t st);
 cudaError_t qs_launch_coeffs(int kernel, double kparam, double kparam2, int d, double tau, int n_ft, int G,
                              const double* psihat, const double* c_in, double* c_out, float* D_out, cudaStream_t st);
 cudaError_t qs_launch_project_fp32(const float* X, int64_t N, int d, const float* xi_s, int P,

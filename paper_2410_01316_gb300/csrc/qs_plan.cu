@@ -326,7 +326,7 @@ void free_plan(qs_plan p)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
     void* bufs[] = {p->d_dirs, p->d_dirs_s, p->d_c, p->d_psihat, p->d_D, p->d_tw, p->d_U, p->d_H,
                     p->d_part, p->d_flag, p->d_wscale, p->d_x, p->d_w, p->d_y, p->d_s, p->d_xi_hi, p->d_xi_lo,
-                    p->d_xs_hi, p->d_xs_lo, p->d_Dd, p->d_H2, p->d_gpart};
+                    p->d_xs_hi, p->d_xs_lo, p->d_Dd, p->d_H2, p->d_gpart, p->d_sortws};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete p;
@@ -863,6 +863,37 @@ qs_status qs_project(qs_plan p, const float* x, int64_t N, float* u_out, int64_t
     e = cudaMemcpy2DAsync(u_out, (size_t)ldu * sizeof(float), p->d_U, (size_t)p->ldU * sizeof(float),
                           (size_t)N * sizeof(float), (size_t)p->desc.P, cudaMemcpyDeviceToDevice, st);
     return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_project: copy");
+}
+
+qs_status qs_sum_sorted(qs_plan p, const float* x, int64_t N, const float* w, const float* y, int64_t M, float* s,
+                        void* stream)
+{
+    if (!p) return fail(QS_ERR_ARG, "qs_sum_sorted: NULL plan");
+    if (p->desc.kernel != QS_NEGDIST)
+        return fail(QS_ERR_UNSUPPORTED, "qs_sum_sorted: sorting slicing is for the negative distance kernel");
+    if (p->desc.d > QS_FUSED_MAX_D)
+        return fail(QS_ERR_UNSUPPORTED, "qs_sum_sorted: d must be <= %d", QS_FUSED_MAX_D);
+    if (N < 0 || M < 0 || N > p->desc.max_n || M > p->desc.max_m)
+        return fail(QS_ERR_ARG, "qs_sum_sorted: sizes outside the plan's limits");
+    if ((N > 0 && !x) || (M > 0 && (!y || !s))) return fail(QS_ERR_ARG, "qs_sum_sorted: NULL data pointer");
+    if (p->desc.max_n + p->desc.max_m > (int64_t)1 << 31)
+        return fail(QS_ERR_UNSUPPORTED, "qs_sum_sorted: max_n + max_m beyond 2^31");
+    if (M == 0) return QS_OK;
+    DeviceGuard g(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!p->d_sortws) {
+        const size_t bytes = qs_sort_workspace_bytes(p->desc.P, p->desc.max_n, p->desc.max_m);
+        if (cudaMalloc(&p->d_sortws, bytes) != cudaSuccess) {
+            p->d_sortws = nullptr;
+            return fail(QS_ERR_OOM, "qs_sum_sorted: workspace of %zu bytes", bytes);
+        }
+    }
+    const int d = p->desc.d;
+    const double cd = exp(0.5 * log(kPi) + lgamma(0.5 * (d + 1)) - lgamma(0.5 * d));
+    const double amp = -cd / ((double)p->G * p->tau);  // f(t) = -c_d |t|, keys in grid units G tau <., xi>
+    cudaError_t e = qs_launch_sum_sorted(x, N, w, y, M, p->d_dirs_s, d, p->desc.P, amp, p->d_sortws, p->desc.max_n,
+                                         p->desc.max_m, s, p->d_flag, st);
+    return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_sum_sorted");
 }
 
 qs_status qs_grad(qs_plan p, const float* x, int64_t N, const float* w, const float* y, int64_t M, const float* v,

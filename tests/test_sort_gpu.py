@@ -1,0 +1,70 @@
+"""Sorting slicing for the negative distance kernel on the GPU (qs_sum_sorted):
+the exact sliced sum (Sec. 2.1 eq. kernel_sum_sliced with f(t) = -c_d |t|) against
+the oracle's closed-form sliced sum O3 on the plan's own directions, within
+1e-5 of sum|w| R (the inputs and projections are FP32; the 1D sums are exact)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_01316_gb300 import QSError, QSPlan
+from paper_2410_01316_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _cuda(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _sorted_sum(prob, use_w=True, proj="fp32", idx=None):
+    with QSPlan(prob.d, "negdist", prob.P, prob.n_ft, prob.R, dirs=prob.xi, proj=proj, max_n=prob.N,
+                max_m=prob.M) as plan:
+        w = _cuda(prob.w) if use_w else None
+        s = plan.sum_sorted(_cuda(prob.x), w, _cuda(prob.y))
+        plan.check()
+        xi = plan.directions()
+    return s.cpu().numpy().astype(np.float64), xi
+
+
+@pytest.mark.parametrize("d,N,M,P", [(3, 1000, 700, 40), (16, 3001, 517, 70), (64, 2500, 2048, 33)])
+def test_sorted_sum_matches_exact_sliced_sum(d, N, M, P):
+    prob = W.tiny(d=d, N=N, M=M, P=P, kernel="negdist", kparam=0.0, n_ft=256, seed=90 + d)
+    s, xi = _sorted_sum(prob)
+    ref = oracle.o3_sliced("negdist", 0.0, prob.x, prob.w, prob.y, xi)
+    assert np.max(np.abs(s - ref)) / (np.abs(prob.w).sum() * prob.R) < TOL
+
+
+def test_sorted_sum_unit_weights_duplicates_and_empty():
+    prob = W.tiny(d=5, N=1200, M=300, P=24, kernel="negdist", kparam=0.0, n_ft=128, seed=3)
+    prob.x[100:160] = prob.x[7]          # repeated sources: equal keys
+    prob.y[:20] = prob.x[7]              # targets on top of them
+    s, xi = _sorted_sum(prob, use_w=False)
+    ref = oracle.o3_sliced("negdist", 0.0, prob.x, None, prob.y, xi)
+    assert np.max(np.abs(s - ref)) / (prob.N * prob.R) < TOL
+    import torch
+
+    with QSPlan(prob.d, "negdist", prob.P, prob.n_ft, prob.R, dirs=prob.xi, proj="fp32", max_n=prob.N,
+                max_m=prob.M) as plan:
+        out = plan.sum_sorted(torch.empty((0, prob.d), device="cuda"), None, _cuda(prob.y))
+        plan.check()
+        assert np.all(out.cpu().numpy() == 0.0)
+
+
+def test_sorted_sum_large_sampled_targets():
+    prob = W.gauss64_negdist(N=60000, M=50000, P=96)
+    s, xi = _sorted_sum(prob, proj="bf16x3")
+    idx = np.random.default_rng(1).choice(prob.M, 64, replace=False)
+    ref = oracle.o3_sliced("negdist", 0.0, prob.x, prob.w, prob.y[idx], xi)
+    assert np.max(np.abs(s[idx] - ref)) / (np.abs(prob.w).sum() * prob.R) < TOL
+
+
+def test_sorted_sum_refuses_other_kernels():
+    prob = W.tiny(d=3, N=100, M=50, P=8, kernel="gauss", kparam=1.0, n_ft=64, seed=1)
+    with QSPlan(prob.d, "gauss", prob.P, prob.n_ft, prob.R, 1.0, dirs=prob.xi, max_n=prob.N, max_m=prob.M) as plan:
+        with pytest.raises(QSError) as ei:
+            plan.sum_sorted(_cuda(prob.x), _cuda(prob.w), _cuda(prob.y))
+        assert ei.value.status == 6
