@@ -65,6 +65,8 @@ def _load():
             lib.o_coeffs2.argtypes = [i, d, d, i, d, i, p]
             lib.o2_exact2.restype = i
             lib.o2_exact2.argtypes = [i, d, d, i, i64, p, p, i64, p, p, i]
+            lib.o3_grad_negdist.restype = i
+            lib.o3_grad_negdist.argtypes = [i, i64, p, p, i64, p, p, i, p, p, i]
             lib.o_esym.restype = i
             lib.o_esym.argtypes = [i, i, p, p, p, i]
             lib.o3_sliced2.restype = i
@@ -227,3 +229,14 @@ def esym(xi, grad: bool = True, threads: int = 0):
     g = np.zeros((P, d)) if grad else None
     _check(_load().o_esym(d, P, _ptr(xi), ctypes.byref(E), _ptr(g), int(threads)), "esym")
     return E.value, g
+
+
+def o3_grad_negdist(x, w, y, v, xi, threads: int = 0) -> np.ndarray:
+    """Gradient in y of L = sum_m v_m s_m for the sliced negative-distance sum with
+    closed-form f (eq. kernel_sum_sliced), sign(0) = 0."""
+    x, y, w, v, xi = _f32(x), _f32(y), _f32(w), _f32(v), _f32(xi)
+    M, d = y.shape
+    g = np.zeros((M, d))
+    _check(_load().o3_grad_negdist(d, x.shape[0], _ptr(x), _ptr(w), M, _ptr(y), _ptr(v), xi.shape[0], _ptr(xi),
+                                   _ptr(g), int(threads)), "o3_grad_negdist")
+    return g

@@ -25,6 +25,7 @@
  *   o1_grad        gradients of L = sum_m v_m s_m of the same sum
  *   o2_exact       exact kernel sum, O(NM)            (Sec. 1, eq. kernel_sum)
  *   o3_sliced      sliced sum with closed-form f      (Sec. 2.1, eq. kernel_sum_sliced)
+ *   o3_grad_negdist gradient in y of the sliced negative-distance sum (Sec. 2.1, eq. kernel_sum_sliced)
  *   o_esym         symmetric distance energy and its gradient (Sec. 2.3, eq. distance-mmd;
  *                  App. "Relation between Distance QMC Designs and Orthogonal Points", eq. distance-sym)
  *
@@ -734,5 +735,38 @@ int o_esym(int d, int P, const float* xi, double* E, double* grad, int nthreads)
         tot += acc;
     }
     *E = -2.0 * tot;
+    return O_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Gradient in y_m of L = sum_m v_m s_m for the sliced negative-distance   */
+/* sum s_m = (1/P) sum_p sum_n w_n (-c_d) |<xi_p, y_m - x_n>|              */
+/* (eq. kernel_sum_sliced, f(t) = -c_d |t|):                               */
+/*   dL/dy_m = v_m (-c_d / P) sum_p (sum_n w_n sign(<xi_p, y_m - x_n>)) xi_p, */
+/* with sign(0) = 0.  gy is M x d.                                         */
+/* ---------------------------------------------------------------------- */
+int o3_grad_negdist(int d, int64_t N, const float* x, const float* w, int64_t M, const float* y, const float* v,
+                    int P, const float* xi, double* gy, int nthreads)
+{
+    if (d < 1 || N < 0 || M < 0 || P < 1 || !xi || !gy) return O_EARG;
+    const double cd = o_riesz_const(d);
+#pragma omp parallel for schedule(static) num_threads(n_threads(nthreads))
+    for (int64_t m = 0; m < M; ++m) {
+        double* g = gy + (size_t)m * d;
+        for (int j = 0; j < d; ++j) g[j] = 0.0;
+        for (int p = 0; p < P; ++p) {
+            const float* xp = xi + (size_t)p * d;
+            const double bm = dot_fd(y + (size_t)m * d, xp, d);
+            double c = 0.0;
+            for (int64_t n = 0; n < N; ++n) {
+                const double t = bm - dot_fd(x + (size_t)n * d, xp, d);
+                const double wn = w ? (double)w[n] : 1.0;
+                c += t > 0.0 ? wn : (t < 0.0 ? -wn : 0.0);
+            }
+            for (int j = 0; j < d; ++j) g[j] += c * (double)xp[j];
+        }
+        const double vm = v ? (double)v[m] : 1.0;
+        for (int j = 0; j < d; ++j) g[j] *= vm * (-cd) / (double)P;
+    }
     return O_OK;
 }

@@ -419,3 +419,24 @@ def test_o1_grad_matches_central_differences(kernel, kp):
             e[j, q] = h
             fd = (L(x0, w0, y0 + e) - L(x0, w0, y0 - e)) / (2 * h)
             assert g["y"][j, q] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+def test_o3_negdist_gradient_matches_central_differences():
+    # derivative of L = sum_m v_m O3_m in y (eq. kernel_sum_sliced, f = -c_d |t|): away from ties the
+    # sliced sum is piecewise linear in y, so central differences are exact up to rounding, provided
+    # no projection difference lies within the step (checked)
+    prob = W.tiny(d=4, N=30, M=5, P=9, kernel="negdist", kparam=0.0, n_ft=64, seed=16)
+    v = np.random.default_rng(2).standard_normal(prob.M)
+    g = oracle.o3_grad_negdist(prob.x, prob.w, prob.y, v, prob.xi)
+    h = 1e-4
+    t = (prob.y.astype(np.float64)[:, None] - prob.x.astype(np.float64)[None]) @ prob.xi.astype(np.float64).T
+    assert np.abs(t).min() > 10 * h
+    y = prob.y.astype(np.float64)
+    for m in range(prob.M):
+        for j in range(prob.d):
+            yp, ym = y.copy(), y.copy()
+            yp[m, j] += h
+            ym[m, j] -= h
+            lp = v @ oracle.o3_sliced("negdist", 0.0, prob.x, prob.w, yp.astype(np.float32), prob.xi)
+            lm = v @ oracle.o3_sliced("negdist", 0.0, prob.x, prob.w, ym.astype(np.float32), prob.xi)
+            assert g[m, j] == pytest.approx((lp - lm) / (2 * h), rel=2e-3, abs=2e-3 * np.abs(g).max())
