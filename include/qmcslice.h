@@ -323,6 +323,17 @@ qs_status qs_plan_variants(qs_plan plan, unsigned int* available, int* current);
  */
 qs_status qs_sum_sorted(qs_plan plan, const float* x, int64_t N, const float* w, const float* y, int64_t M,
                         float* s, void* stream);
+/*
+ * Gradient in the targets of L = sum_m v_m s_m for the same exact sliced sum:
+ *   gy[m] = v_m (-c_d / P) sum_p (sum_n w_n sign(<xi_p, y_m - x_n>)) xi_p
+ * (M x d, row-major, device; v may be NULL for all ones), from the same sort
+ * (2 W_< - W per target and slice) and a fixed-order compensated sum over the
+ * slices.  A source whose projection equals a target's exactly counts as
+ * below it (one-sided subgradient).  Requirements, workspace and errors as
+ * for qs_sum_sorted.
+ */
+qs_status qs_grad_sorted(qs_plan plan, const float* x, int64_t N, const float* w, const float* y, int64_t M,
+                         const float* v, float* gy, void* stream);
 
 /*
  * Distance QMC designs (Sec. 2.3, eq. distance-mmd with s = d/2; Sec. 4.1,

@@ -197,6 +197,24 @@ class QSPlan:
                                            y.data_ptr(), M, out.data_ptr(), _stream_handle(stream)), "qs_sum_sorted")
         return out
 
+    def grad_sorted(self, x, w, y, v=None, out=None, stream=None):
+        """Gradient in y of sum_m v_m s_m for the exact sliced negative-distance sum (M x d tensor)."""
+        import torch
+
+        self._check_points(x, "x")
+        self._check_points(y, "y")
+        N, M = x.shape[0], y.shape[0]
+        if w is not None:
+            self._check_points(w, "w", rows=N)
+        if v is not None:
+            self._check_points(v, "v", rows=M)
+        if out is None:
+            out = torch.empty((M, self.d), dtype=torch.float32, device=self.device)
+        _lib.check(self._lib.qs_grad_sorted(self._handle, x.data_ptr(), N, None if w is None else w.data_ptr(),
+                                            y.data_ptr(), M, None if v is None else v.data_ptr(), out.data_ptr(),
+                                            _stream_handle(stream)), "qs_grad_sorted")
+        return out
+
     def project(self, x, out=None, stream=None):
         """u[p, n] = G tau <x_n, xi_p> in the plan's projection form (P x N tensor)."""
         import torch

@@ -33,7 +33,7 @@ EXPORTS = ("qs_plan_create", "qs_plan_destroy", "qs_plan_info", "qs_plan_directi
            "qs_set_timing", "qs_stage_times", "qs_project", "qs_sum_noalloc", "qs_grad",
            "qs_plan_autotune", "qs_plan_set_variant", "qs_batch_create", "qs_batch_destroy", "qs_sum_batched",
            "qs_batch_check", "qs_batch_set_tiling", "qs_plan_variants", "qs_distance_design",
-           "qs_distance_energy", "qs_sum_sorted")
+           "qs_distance_energy", "qs_sum_sorted", "qs_grad_sorted")
 
 
 class PlanDesc(ctypes.Structure):
@@ -91,6 +91,7 @@ def load() -> ctypes.CDLL:
         lib.qs_distance_design.argtypes = [c_vp, c_int, c_int, c_int, c_dbl, ctypes.POINTER(c_dbl), c_vp]
         lib.qs_distance_energy.argtypes = [c_vp, c_int, c_int, ctypes.POINTER(c_dbl), c_vp, c_vp]
         lib.qs_sum_sorted.argtypes = [c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp]
+        lib.qs_grad_sorted.argtypes = [c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]
         lib.qs_grad.argtypes = [c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]
         lib.qs_sum_noalloc.argtypes = [ctypes.POINTER(PlanDesc), c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp]
         lib.qs_set_timing.argtypes = [c_vp, c_int]
@@ -102,7 +103,7 @@ def load() -> ctypes.CDLL:
                      "qs_sum_noalloc", "qs_grad", "qs_plan_autotune", "qs_plan_set_variant",
                      "qs_batch_create", "qs_batch_destroy", "qs_sum_batched", "qs_batch_check",
                      "qs_batch_set_tiling", "qs_plan_variants", "qs_distance_design", "qs_distance_energy",
-                     "qs_sum_sorted"):
+                     "qs_sum_sorted", "qs_grad_sorted"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib

@@ -211,8 +211,9 @@ __host__ __device__ inline int qs_interp_tpt(bool fused, int d)
 int qs_sort_chunk(int P);
 size_t qs_sort_workspace_bytes(int P, int64_t max_n, int64_t max_m);
 cudaError_t qs_launch_sum_sorted(const float* x, int64_t N, const float* w, const float* y, int64_t M,
-                                 const float* xi_s, int d, int P, double amp, void* ws, int64_t max_n,
-                                 int64_t max_m, float* s, unsigned int* flag, cudaStream_t st);
+                                 const float* xi_s, const float* xi, int d, int P, double amp, void* ws,
+                                 int64_t max_n, int64_t max_m, float* s, const float* v, float scale, float* gy,
+                                 unsigned int* flag, cudaStream_t st);
 cudaError_t qs_launch_coeffs(int kernel, double kparam, double kparam2, int d, double tau, int n_ft, int G,
                              const double* psihat, const double* c_in, double* c_out, float* D_out, cudaStream_t st);
 cudaError_t qs_launch_project_fp32(const float* X, int64_t N, int d, const float* xi_s, int P,

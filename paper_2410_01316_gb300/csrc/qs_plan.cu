@@ -865,8 +865,9 @@ qs_status qs_project(qs_plan p, const float* x, int64_t N, float* u_out, int64_t
     return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_project: copy");
 }
 
-qs_status qs_sum_sorted(qs_plan p, const float* x, int64_t N, const float* w, const float* y, int64_t M, float* s,
-                        void* stream)
+namespace {
+qs_status sorted_call(qs_plan p, const float* x, int64_t N, const float* w, const float* y, int64_t M, float* s,
+                      const float* v, float* gy, void* stream)
 {
     if (!p) return fail(QS_ERR_ARG, "qs_sum_sorted: NULL plan");
     if (p->desc.kernel != QS_NEGDIST)
@@ -875,7 +876,7 @@ qs_status qs_sum_sorted(qs_plan p, const float* x, int64_t N, const float* w, co
         return fail(QS_ERR_UNSUPPORTED, "qs_sum_sorted: d must be <= %d", QS_FUSED_MAX_D);
     if (N < 0 || M < 0 || N > p->desc.max_n || M > p->desc.max_m)
         return fail(QS_ERR_ARG, "qs_sum_sorted: sizes outside the plan's limits");
-    if ((N > 0 && !x) || (M > 0 && (!y || !s))) return fail(QS_ERR_ARG, "qs_sum_sorted: NULL data pointer");
+    if ((N > 0 && !x) || (M > 0 && (!y || (!s && !gy)))) return fail(QS_ERR_ARG, "qs_sum_sorted: NULL data pointer");
     if (p->desc.max_n + p->desc.max_m > (int64_t)1 << 31)
         return fail(QS_ERR_UNSUPPORTED, "qs_sum_sorted: max_n + max_m beyond 2^31");
     if (M == 0) return QS_OK;
@@ -891,9 +892,25 @@ qs_status qs_sum_sorted(qs_plan p, const float* x, int64_t N, const float* w, co
     const int d = p->desc.d;
     const double cd = exp(0.5 * log(kPi) + lgamma(0.5 * (d + 1)) - lgamma(0.5 * d));
     const double amp = -cd / ((double)p->G * p->tau);  // f(t) = -c_d |t|, keys in grid units G tau <., xi>
-    cudaError_t e = qs_launch_sum_sorted(x, N, w, y, M, p->d_dirs_s, d, p->desc.P, amp, p->d_sortws, p->desc.max_n,
-                                         p->desc.max_m, s, p->d_flag, st);
+    const float scale = (float)(-cd / p->desc.P);
+    cudaError_t e = qs_launch_sum_sorted(x, N, w, y, M, p->d_dirs_s, p->d_dirs, d, p->desc.P, amp, p->d_sortws,
+                                         p->desc.max_n, p->desc.max_m, s, v, scale, gy, p->d_flag, st);
     return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_sum_sorted");
+}
+}  // namespace
+
+qs_status qs_sum_sorted(qs_plan p, const float* x, int64_t N, const float* w, const float* y, int64_t M, float* s,
+                        void* stream)
+{
+    if (M > 0 && !s) return fail(QS_ERR_ARG, "qs_sum_sorted: NULL output");
+    return sorted_call(p, x, N, w, y, M, s, nullptr, nullptr, stream);
+}
+
+qs_status qs_grad_sorted(qs_plan p, const float* x, int64_t N, const float* w, const float* y, int64_t M,
+                         const float* v, float* gy, void* stream)
+{
+    if (M > 0 && !gy) return fail(QS_ERR_ARG, "qs_grad_sorted: NULL output");
+    return sorted_call(p, x, N, w, y, M, nullptr, v, gy, stream);
 }
 
 qs_status qs_grad(qs_plan p, const float* x, int64_t N, const float* w, const float* y, int64_t M, const float* v,

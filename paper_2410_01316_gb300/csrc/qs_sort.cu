@@ -231,6 +231,9 @@ __global__ void sort_tilescan_kernel(double* __restrict__ tsum, int T, int cs, d
 // per sorted tile: exclusive FP64 prefix of (w, w a) over the sources before
 // each element; for every target m the slice's value
 // amp * (b (2 W_< - W) - (2 S_< - S)) goes to t[pl][m]
+// GRAD: t[pl][m] = 2 W_< - W = sum_n w_n sign(b - a_n) instead (sources whose
+// key equals b's sort before it and count as below: a one-sided subgradient)
+template <bool GRAD>
 __global__ void __launch_bounds__(SORT_THREADS) sort_eval_kernel(const uint32_t* __restrict__ key,
                                                                  const uint32_t* __restrict__ pay, int64_t N,
                                                                  int64_t M, int64_t LS, int T,
@@ -285,7 +288,8 @@ __global__ void __launch_bounds__(SORT_THREADS) sort_eval_kernel(const uint32_t*
         }
         if (e < L && i >= N) {
             const double Wl = ow + iw - vw, Sl = oa + ia - va;  // sources strictly before
-            tout[(size_t)pl * M + (i - N)] = (float)(amp * (b * (2.0 * Wl - W) - (2.0 * Sl - S)));
+            tout[(size_t)pl * M + (i - N)] =
+                GRAD ? (float)(2.0 * Wl - W) : (float)(amp * (b * (2.0 * Wl - W) - (2.0 * Sl - S)));
         }
         carry_w = bw;
         carry_a = ba;
@@ -303,6 +307,30 @@ __global__ void sort_accum_kernel(const float* __restrict__ t, int CS, int64_t M
     for (int pl = 0; pl < CS; ++pl) qs_two_sum(h, l, t[(size_t)pl * M + m]);
     hi[m] = h;
     lo[m] = l;
+}
+
+// gradient accumulators ghi/glo [j][m] += t[pl][m] xi_{p0+pl}[j], pl in order (TwoSum)
+__global__ void sort_gaccum_kernel(const float* __restrict__ t, int CS, int64_t M, const float* __restrict__ xi,
+                                   int d, int p0, float* __restrict__ ghi, float* __restrict__ glo)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    for (int j = 0; j < d; ++j) {
+        float h = ghi[(size_t)j * M + m], l = glo[(size_t)j * M + m];
+        for (int pl = 0; pl < CS; ++pl) qs_two_sum(h, l, t[(size_t)pl * M + m] * __ldg(&xi[(size_t)(p0 + pl) * d + j]));
+        ghi[(size_t)j * M + m] = h;
+        glo[(size_t)j * M + m] = l;
+    }
+}
+
+// gy[m][j] = v_m scale (hi + lo)
+__global__ void sort_gfinal_kernel(const float* __restrict__ ghi, const float* __restrict__ glo, int64_t M, int d,
+                                   const float* __restrict__ v, float scale, float* __restrict__ gy)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const float vm = (v ? v[m] : 1.0f) * scale;
+    for (int j = 0; j < d; ++j) gy[(size_t)m * d + j] = vm * (ghi[(size_t)j * M + m] + glo[(size_t)j * M + m]);
 }
 
 __global__ void sort_final_kernel(const float* __restrict__ hi, const float* __restrict__ lo, int64_t M, int P,
@@ -328,13 +356,17 @@ size_t qs_sort_workspace_bytes(int P, int64_t max_n, int64_t max_m)
            + (size_t)CS * T * 2 * sizeof(double)          // tile sums
            + (size_t)CS * 2 * sizeof(double)              // slice totals
            + (size_t)CS * max_m * sizeof(float)           // slice values of a chunk
-           + (size_t)2 * max_m * sizeof(float) + 1024;    // hi / lo
+           + (size_t)2 * max_m * QS_FUSED_MAX_D * sizeof(float) + 1024;  // hi / lo (x d for gradients)
 }
 
+// s != NULL: the sum; else gy (M x d) = v_m (-c_d/P) sum_p (sum_n w_n sign(b - a_n)) xi_p,
+// with `scale` = -c_d / P and xi the unscaled directions.
 cudaError_t qs_launch_sum_sorted(const float* x, int64_t N, const float* w, const float* y, int64_t M,
-                                 const float* xi_s, int d, int P, double amp, void* ws, int64_t max_n,
-                                 int64_t max_m, float* s, unsigned int* flag, cudaStream_t st)
+                                 const float* xi_s, const float* xi, int d, int P, double amp, void* ws,
+                                 int64_t max_n, int64_t max_m, float* s, const float* v, float scale, float* gy,
+                                 unsigned int* flag, cudaStream_t st)
 {
+    const bool grad = s == nullptr;
     if (M <= 0) return cudaSuccess;
     const int CS = qs_sort_chunk(P);
     const int64_t L = N + M;
@@ -353,7 +385,9 @@ cudaError_t qs_launch_sum_sorted(const float* x, int64_t N, const float* w, cons
     float* tb = reinterpret_cast<float*>(tot + (size_t)CS * 2);
     float* hi = tb + (size_t)CS * max_m;
     float* lo = hi + max_m;
-    cudaError_t e = cudaMemsetAsync(hi, 0, sizeof(float) * 2 * (size_t)max_m, st);
+    const size_t acc = (size_t)M * (grad ? d : 1);  // accumulators of this call, hi then lo
+    lo = hi + acc;
+    cudaError_t e = cudaMemsetAsync(hi, 0, sizeof(float) * 2 * acc, st);
     for (int p0 = 0; p0 < P && e == cudaSuccess; p0 += CS) {
         const int cs = P - p0 < CS ? P - p0 : CS;
         sort_init_kernel<<<dim3((unsigned)((L + 255) / 256), (unsigned)cs), 256, 0, st>>>(x, N, y, M, xi_s, d, p0, LS,
@@ -375,13 +409,21 @@ cudaError_t qs_launch_sum_sorted(const float* x, int64_t N, const float* w, cons
         // four passes: the sorted data are back in the A buffers
         sort_tilesum_kernel<<<dim3((unsigned)T, (unsigned)cs), SORT_THREADS, 0, st>>>(ki, pi, N, L, LS, T, w, tsum);
         sort_tilescan_kernel<<<1, 32, 0, st>>>(tsum, T, cs, tot);
-        sort_eval_kernel<<<dim3((unsigned)T, (unsigned)cs), SORT_THREADS, 0, st>>>(ki, pi, N, M, LS, T, w, tsum, tot,
-                                                                                   amp, tb);
-        sort_accum_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(tb, cs, M, hi, lo);
+        const dim3 eg((unsigned)T, (unsigned)cs);
+        if (grad) {
+            sort_eval_kernel<true><<<eg, SORT_THREADS, 0, st>>>(ki, pi, N, M, LS, T, w, tsum, tot, amp, tb);
+            sort_gaccum_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(tb, cs, M, xi, d, p0, hi, lo);
+        } else {
+            sort_eval_kernel<false><<<eg, SORT_THREADS, 0, st>>>(ki, pi, N, M, LS, T, w, tsum, tot, amp, tb);
+            sort_accum_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(tb, cs, M, hi, lo);
+        }
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        sort_final_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(hi, lo, M, P, s);
+        if (grad)
+            sort_gfinal_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(hi, lo, M, d, v, scale, gy);
+        else
+            sort_final_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(hi, lo, M, P, s);
         e = cudaGetLastError();
     }
     return e;

@@ -68,3 +68,17 @@ def test_sorted_sum_refuses_other_kernels():
         with pytest.raises(QSError) as ei:
             plan.sum_sorted(_cuda(prob.x), _cuda(prob.w), _cuda(prob.y))
         assert ei.value.status == 6
+
+
+@pytest.mark.parametrize("d,N,M,P", [(3, 900, 400, 40), (16, 2000, 700, 70)])
+def test_sorted_gradient_matches_exact_sliced_gradient(d, N, M, P):
+    prob = W.tiny(d=d, N=N, M=M, P=P, kernel="negdist", kparam=0.0, n_ft=256, seed=120 + d)
+    v = np.random.default_rng(9).standard_normal(M).astype(np.float32)
+    with QSPlan(prob.d, "negdist", prob.P, prob.n_ft, prob.R, dirs=prob.xi, proj="fp32", max_n=N, max_m=M) as plan:
+        g = plan.grad_sorted(_cuda(prob.x), _cuda(prob.w), _cuda(prob.y), _cuda(v))
+        plan.check()
+        xi = plan.directions()
+    ref = oracle.o3_grad_negdist(prob.x, prob.w, prob.y, v, xi)
+    norm = oracle.riesz_const(d) * np.abs(prob.w).sum() * np.abs(v).max()
+    assert np.max(np.abs(g.cpu().numpy() - ref)) / norm < TOL
+    assert np.max(np.abs(ref)) / norm > 1e-3
