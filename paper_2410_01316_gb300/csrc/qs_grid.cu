@@ -1026,13 +1026,13 @@ cudaError_t launch_interp_w(const qs_launch& L, const float* y, bool fused, cuda
     const size_t smem = (size_t)2 * (L.G + ROW_PAD + (fused ? 0 : IT_THREADS * tpt)) * sizeof(float);
     const unsigned gx = (unsigned)((L.M + (int64_t)IT_THREADS * tpt - 1) / ((int64_t)IT_THREADS * tpt));
     dim3 grid(gx, (unsigned)L.S);
+    // the kernel also holds ~8.5 KB of static shared memory, so the opt-in is
+    // needed below 48 KB of dynamic memory too; set it on every launch
 #define QS_LAUNCH_INTERP(FU, DM, TP)                                                                       \
     do {                                                                                                   \
         auto k_ = interp_kernel<W, FU, DM, TP>;                                                            \
-        if (smem > 48 * 1024) {                                                                            \
-            cudaError_t e_ = cudaFuncSetAttribute(k_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-            if (e_ != cudaSuccess) return e_;                                                              \
-        }                                                                                                  \
+        cudaError_t e_ = cudaFuncSetAttribute(k_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e_ != cudaSuccess) return e_;                                                                  \
         k_<<<grid, IT_THREADS, smem, st>>>(L, y);                                                          \
     } while (0)
     if (!fused) QS_LAUNCH_INTERP(false, 1, 4);

@@ -198,6 +198,15 @@ def test_equal_weights_clustered_error_stays_at_fp32_level(window):
     assert _err(s, ref, prob) < 1.5e-6
 
 
+@pytest.mark.parametrize("n_ft", [1024, 2048, 4096])
+def test_unfused_large_grids(n_ft):
+    # unfused interpolation rows of G = 2 n_ft cells plus the staged projections
+    # cross the 48 KB shared-memory line at G = 4096
+    prob = W.tiny(d=16, N=1500, M=600, P=24, kernel="negdist", kparam=0.0, n_ft=n_ft, seed=31)
+    s, _ = _gpu_sum(prob, "fp32")
+    assert _err(s, _oracle(prob), prob) < TOL_FP32
+
+
 def _variant_problem(case):
     if case == "grid512":  # the 512-cell window covers the whole grid
         return W.tiny(d=5, N=3001, M=500, P=20, kernel="negdist", kparam=0.0, n_ft=256, seed=21)
