@@ -789,7 +789,8 @@ __global__ void deriv_table_kernel(const double* __restrict__ c, const double* _
 // QWIN bins (clustered projections) it expands the row into the bins'
 // polynomials in t (the tap polynomials of qs_taps summed against the row),
 // and each target is one degree-(K-1) Horner evaluation; otherwise each
-// target takes its W taps from the row.  Both evaluate the same polynomial
+// target takes its W taps from the row, and the CTA stops looking for
+// narrow ranges in its remaining slices.  Both evaluate the same polynomial
 // sum_j h[l0 + j] tap_j, rounded differently; which one a target takes
 // depends only on the data, so results are reproducible.
 constexpr int QWIN = 256;
@@ -832,6 +833,7 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
     float yr[FUSED ? DMAX * TPT : 1];
     float hi[TPT], lo[TPT];
     bool live[TPT];
+    bool try_win = true;  // uniform over the block: decided from block-wide values
 #pragma unroll
     for (int i = 0; i < TPT; ++i) {
         const int64_t m = m0 + threadIdx.x + (int64_t)i * IT_THREADS;
@@ -869,6 +871,34 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
             cp_async_wait<0>();
         }
         __syncthreads();
+        if (!try_win) {
+            // an earlier slice's targets spanned too many bins: taps directly
+#pragma unroll
+            for (int i = 0; i < TPT; ++i) {
+                if (!live[i]) continue;
+                float u;
+                if (FUSED) {
+                    const float* xs = L.xi_s + (size_t)p * L.d;
+                    u = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < DMAX; ++j)
+                        if (j < L.d) u = fmaf(__ldg(&xs[j]), yr[i * DMAX + j], u);
+                } else {
+                    u = row[G + ROW_PAD + threadIdx.x + i * IT_THREADS];
+                }
+                u = qs_check_u(u, L.half_G, L.flag);
+                int l0;
+                float tap[W];
+                qs_taps<W>(u, L.win, l0, tap);
+                const float* h = row + (l0 & mask);
+                float t = 0.0f;
+#pragma unroll
+                for (int j = 0; j < W; ++j) t = fmaf(h[j], tap[j], t);
+                qs_two_sum(hi[i], lo[i], t);
+            }
+            __syncthreads();  // the buffer just read is refilled two slices later
+            continue;
+        }
         // target positions: u, the bin kb = l0 + H0 in [0, G] (l0 the first
         // tap cell, unwrapped) and t = 2 s in (-1, 1]
         float uu[TPT], tt[TPT];
@@ -935,6 +965,7 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
                 qs_two_sum(hi[i], lo[i], v);
             }
         } else {
+            if (kmin <= kmax) try_win = false;  // spread-out targets: stay on the tap path
 #pragma unroll
             for (int i = 0; i < TPT; ++i) {
                 if (!live[i]) continue;

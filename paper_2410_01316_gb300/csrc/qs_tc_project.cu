@@ -169,10 +169,11 @@ __host__ __device__ constexpr int stage_bytes()
 // Persistent form: one CTA per SM walks the tiles t = blockIdx.x, +gridDim.x,
 // ... (slice tile fastest, so CTAs running together share point tiles in L2).
 // Warp 0 lane 0 streams k-slabs through a STAGES-deep ring; warp 1 lane 0
-// issues the MMAs into one of two 256-column TMEM accumulators; warps 2..5
-// drain the other accumulator to U meanwhile, so a tile's epilogue overlaps
-// the next tile's MMAs.  Barriers: full/empty per ring stage, tfull/tempty
-// per accumulator (tempty counts the four epilogue warps).  Every wait is
+// issues the MMAs into one of two 256-column TMEM accumulators; warps 2..9
+// drain the other accumulator to U meanwhile (two warps per TMEM lane
+// quarter), so a tile's epilogue overlaps the next tile's MMAs; with a short
+// K (small d) the tile is bound by these stores of U.  Barriers: full/empty per ring stage, tfull/tempty
+// per accumulator (tempty counts the epilogue warps).  Every wait is
 // bounded; a role that gives up raises the shared abort flag and the error
 // flag, and the others stop at their next tile.
 // ---------------------------------------------------------------------------
@@ -193,7 +194,8 @@ __host__ __device__ constexpr int tcp_smem_bytes()
     return 1024 + PCfg<KIND>::STAGES * stage_bytes<KIND>() + 256;
 }
 
-constexpr int TCP_THREADS = 192;
+constexpr int TCP_EPI_WARPS = 8;  // two per TMEM lane quarter, each storing half the columns
+constexpr int TCP_THREADS = 32 * (2 + TCP_EPI_WARPS);
 
 template <int KIND>
 __global__ void __launch_bounds__(TCP_THREADS, 1)
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull0 + 8 * a, 1);
-            mbar_init(tempty0 + 8 * a, 4);
+            mbar_init(tempty0 + 8 * a, TCP_EPI_WARPS);
         }
         mbar_init(drain, 1);
         abort_all = 0;
@@ -327,8 +329,10 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
             atomicOr(flag, QS_FLAG_TIMEOUT);
         }
     } else if (warp >= 2) {
-        // epilogue: TMEM lane quarter q = warp % 4 holds points n0 + 32 q + lane
+        // epilogue: TMEM lane quarter q = warp % 4 holds points n0 + 32 q + lane;
+        // the two warps of a quarter take columns [128 h, 128 h + 128)
         const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
         int i = 0;
         for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++i) {
             if (abort_all) break;
@@ -346,7 +350,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
             const int64_t n = (t / ptiles) * TILE_M + 32 * q + lane;
             const uint32_t trow = tmem + (uint32_t)(a * TILE_N) + ((uint32_t)(32 * q) << 16);
 #pragma unroll 1
-            for (int c = 0; c < TILE_N; c += 32) {
+            for (int c = h * (TILE_N / 2); c < (h + 1) * (TILE_N / 2); c += 32) {
                 float v[32];
                 __syncwarp();
                 tmem_ld32(trow + (uint32_t)c, v);
