@@ -707,7 +707,7 @@ def launches_per_step(plan) -> int:
 # DRAM bytes (read + write) per launch from one ncu capture of the default workload itself
 # (d = 784, N = M = 60000, P = 2048, N_ft = 1024, BF16x3, momentwin32 spread;
 # profiles/traffic_mnist_laplace.md).  Only for that configuration and the kernels as captured.
-TRAFFIC_MNIST = {"project_x": 639.3e6, "project_y": 636.2e6, "spread_filter": 504.3e6, "interp": 515.7e6}
+TRAFFIC_MNIST = {"project_x": 631.3e6, "project_y": 628.4e6, "spread_filter": 504.5e6, "interp": 515.0e6}
 
 
 def _traffic(prob, plan, name):
