@@ -174,9 +174,15 @@ qs_status qs_project(qs_plan plan, const float* x, int64_t N, float* u_out, int6
 
 /*
  * Same sum from HOST buffers: copies x, w, y into plan-owned device staging
- * buffers, runs qs_sum on `stream`, copies s back into the host buffer and
- * synchronises the stream.  Pinned host memory gives the fastest copies.
- * Returns the data-error status as qs_check would.
+ * buffers, computes the sum, copies s back into the host buffer and
+ * synchronises `stream`.  The copies in run on a plan-owned copy stream in
+ * row chunks (at most 8 per input, after the work already queued on
+ * `stream`), and each chunk is projected on `stream` as soon as it has
+ * landed, so the transfers overlap the projections and the spread.  With
+ * stage timing on (qs_set_timing) or N == 0 the copies run first, on
+ * `stream`.  Pinned host memory gives the fastest copies; the host buffers
+ * must stay unchanged until the call returns.  Returns the data-error status
+ * as qs_check would.
  */
 qs_status qs_sum_host(qs_plan plan, const float* x_host, int64_t N, const float* w_host,
                       const float* y_host, int64_t M, float* s_host, void* stream);

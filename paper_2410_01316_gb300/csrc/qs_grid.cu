@@ -820,7 +820,11 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
     const int H0 = (G >> 1) + W / 2;
     __shared__ float atab[W * KQ];
     __shared__ float qwin[KQ * QWIN];
-    __shared__ int s_kmin[IT_THREADS / 32], s_kmax[IT_THREADS / 32];
+    __shared__ int s_krange[2][2];  // per slice parity: block-wide [min, max] bin
+    if (threadIdx.x < 2) {
+        s_krange[threadIdx.x][0] = INT_MAX;
+        s_krange[threadIdx.x][1] = INT_MIN;
+    }  // first read after the loop's first barrier
     for (int idx = threadIdx.x; idx < W * KQ; idx += IT_THREADS) {
         const int j = idx / KQ, k = idx - j * KQ;
         const int jj = j < W / 2 ? j : W - 1 - j;
@@ -918,29 +922,54 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
                 }
                 u = qs_check_u(u, L.half_G, L.flag);
             }
-            const float fl = ceilf(u - (float)(W / 2));
             uu[i] = u;
-            kb[i] = (int)fl + H0;
-            tt[i] = 2.0f * ((u - fl) - ((float)(W / 2) - 0.5f));
+            if constexpr (TPT % 2 != 0) {
+                const float fl = ceilf(u - (float)(W / 2));
+                kb[i] = (int)fl + H0;
+                tt[i] = 2.0f * ((u - fl) - ((float)(W / 2) - 0.5f));
+            }
+        }
+        if constexpr (TPT % 2 == 0) {
+            // the same bin and offset in packed pairs: fma(2, u - fl, 1 - W)
+            // equals 2 ((u - fl) - (W/2 - 1/2)) exactly (scaling by 2 commutes
+            // with rounding)
+#pragma unroll
+            for (int i = 0; i < TPT; i += 2) {
+                const float2 u2 = make_float2(uu[i], uu[i + 1]);
+                const float2 a2 = __fadd2_rn(u2, make_float2(-(float)(W / 2), -(float)(W / 2)));
+                const float2 fl2 = make_float2(ceilf(a2.x), ceilf(a2.y));
+                kb[i] = (int)fl2.x + H0;
+                kb[i + 1] = (int)fl2.y + H0;
+                const float2 t2 = __ffma2_rn(make_float2(2.0f, 2.0f), qs_sub2(u2, fl2),
+                                             make_float2((float)(1 - W), (float)(1 - W)));
+                tt[i] = t2.x;
+                tt[i + 1] = t2.y;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < TPT; ++i) {
             if (live[i]) {
                 kmin = min(kmin, kb[i]);
                 kmax = max(kmax, kb[i]);
             }
         }
+        // block range: one shared atomic pair per warp into this slice's
+        // cells; thread 0 resets the other parity's cells, last read in the
+        // previous slice (two barriers ago) and next written in the next one
+        const int par = (p - p0) & 1;
         kmin = __reduce_min_sync(0xffffffffu, kmin);
         kmax = __reduce_max_sync(0xffffffffu, kmax);
         if ((threadIdx.x & 31) == 0) {
-            s_kmin[threadIdx.x >> 5] = kmin;
-            s_kmax[threadIdx.x >> 5] = kmax;
+            atomicMin(&s_krange[par][0], kmin);
+            atomicMax(&s_krange[par][1], kmax);
+        }
+        if (threadIdx.x == 0) {
+            s_krange[par ^ 1][0] = INT_MAX;
+            s_krange[par ^ 1][1] = INT_MIN;
         }
         __syncthreads();
-        kmin = INT_MAX;
-        kmax = INT_MIN;
-#pragma unroll
-        for (int w = 0; w < IT_THREADS / 32; ++w) {
-            kmin = min(kmin, s_kmin[w]);
-            kmax = max(kmax, s_kmax[w]);
-        }
+        kmin = s_krange[par][0];
+        kmax = s_krange[par][1];
         if (kmin <= kmax && kmax - kmin < QWIN) {
             // the CTA's targets of this slice fall in few bins: per bin b the
             // polynomial Q_b(t) = sum_j h[b + j] tap_j(t) (coefficients
@@ -955,14 +984,35 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
                 qwin[k * QWIN + b] = q;  // coefficient-major: lanes at different bins hit different banks
             }
             __syncthreads();
+            if constexpr (TPT % 2 == 0) {
+                // two targets per packed FP32x2 Horner step and TwoSum (the
+                // same roundings as the scalar loop); a dead target reads
+                // bin kmin and is never stored
 #pragma unroll
-            for (int i = 0; i < TPT; ++i) {
-                if (!live[i]) continue;
-                const float* qb = qwin + (kb[i] - kmin);
-                float v = qb[(KQ - 1) * QWIN];
+                for (int i = 0; i < TPT; i += 2) {
+                    const float* qa = qwin + ((live[i] ? kb[i] : kmin) - kmin);
+                    const float* qc = qwin + ((live[i + 1] ? kb[i + 1] : kmin) - kmin);
+                    const float2 t2 = make_float2(tt[i], tt[i + 1]);
+                    float2 v = make_float2(qa[(KQ - 1) * QWIN], qc[(KQ - 1) * QWIN]);
 #pragma unroll
-                for (int k = KQ - 2; k >= 0; --k) v = fmaf(v, tt[i], qb[k * QWIN]);
-                qs_two_sum(hi[i], lo[i], v);
+                    for (int k = KQ - 2; k >= 0; --k) v = __ffma2_rn(v, t2, make_float2(qa[k * QWIN], qc[k * QWIN]));
+                    float2 h2 = make_float2(hi[i], hi[i + 1]), l2 = make_float2(lo[i], lo[i + 1]);
+                    qs_two_sum2(h2, l2, v);
+                    hi[i] = h2.x;
+                    hi[i + 1] = h2.y;
+                    lo[i] = l2.x;
+                    lo[i + 1] = l2.y;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < TPT; ++i) {
+                    if (!live[i]) continue;
+                    const float* qb = qwin + (kb[i] - kmin);
+                    float v = qb[(KQ - 1) * QWIN];
+#pragma unroll
+                    for (int k = KQ - 2; k >= 0; --k) v = fmaf(v, tt[i], qb[k * QWIN]);
+                    qs_two_sum(hi[i], lo[i], v);
+                }
             }
         } else {
             if (kmin <= kmax) try_win = false;  // spread-out targets: stay on the tap path
@@ -996,7 +1046,22 @@ __global__ void reduce_kernel(const float* __restrict__ part, int S, int64_t M, 
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     float hi = 0.0f, lo = 0.0f;
-    for (int g = 0; g < S; ++g) {
+    // groups in increasing order; eight groups' loads are issued together
+    int g = 0;
+    for (; g + 8 <= S; g += 8) {
+        float a[8], b[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            a[j] = part[(size_t)(g + j) * M + m];
+            b[j] = part[(size_t)(S + g + j) * M + m];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            qs_two_sum(hi, lo, a[j]);
+            lo += b[j];
+        }
+    }
+    for (; g < S; ++g) {
         qs_two_sum(hi, lo, part[(size_t)g * M + m]);
         lo += part[(size_t)(S + g) * M + m];
     }
@@ -1053,7 +1118,7 @@ cudaError_t launch_spread_w(const qs_launch& L, const float* x, const float* w, 
 template <int W>
 cudaError_t launch_interp_w(const qs_launch& L, const float* y, bool fused, cudaStream_t st)
 {
-    const int tpt = qs_interp_tpt(fused, L.d);
+    const int tpt = qs_interp_tpt(fused, L.d, L.G);
     const size_t smem = (size_t)2 * (L.G + ROW_PAD + (fused ? 0 : IT_THREADS * tpt)) * sizeof(float);
     const unsigned gx = (unsigned)((L.M + (int64_t)IT_THREADS * tpt - 1) / ((int64_t)IT_THREADS * tpt));
     dim3 grid(gx, (unsigned)L.S);
@@ -1066,7 +1131,8 @@ cudaError_t launch_interp_w(const qs_launch& L, const float* y, bool fused, cuda
         if (e_ != cudaSuccess) return e_;                                                                  \
         k_<<<grid, IT_THREADS, smem, st>>>(L, y);                                                          \
     } while (0)
-    if (!fused) QS_LAUNCH_INTERP(false, 1, 4);
+    if (!fused && tpt == 8) QS_LAUNCH_INTERP(false, 1, 8);
+    else if (!fused) QS_LAUNCH_INTERP(false, 1, 4);
     else if (L.d <= 4) QS_LAUNCH_INTERP(true, 4, 2);
     else if (L.d <= 8) QS_LAUNCH_INTERP(true, 8, 2);
     else if (L.d <= 16) QS_LAUNCH_INTERP(true, 16, 1);

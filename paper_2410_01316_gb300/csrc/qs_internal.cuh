@@ -13,6 +13,7 @@
 
 // stages timed by qs_set_timing / qs_stage_times
 #define QS_NUM_STAGES 7
+#define QS_HOST_CHUNKS 8  // most row chunks per input in the qs_sum_host pipeline
 
 // device error flag bits (qs_check maps them to qs_status)
 #define QS_FLAG_RANGE 1u
@@ -147,6 +148,9 @@ struct qs_plan_s {
     int timing;
     int timed_calls;
     cudaEvent_t ev[8];  // QS_NUM_STAGES + 1
+    // qs_sum_host pipeline: copy stream and per-chunk arrival events (created by the first call)
+    cudaStream_t copy_st;
+    cudaEvent_t hev[1 + 2 * QS_HOST_CHUNKS];
 };
 
 // ---------------------------------------------------------------------------
@@ -189,6 +193,23 @@ __device__ __forceinline__ void qs_two_sum(float& hi, float& lo, float x)
     lo += err;
 }
 
+// Two lanes of qs_two_sum in packed FP32x2 arithmetic (each lane rounds
+// exactly as the scalar form; a - b is formed as fma(b, -1, a), the same
+// correctly rounded difference).
+__device__ __forceinline__ float2 qs_sub2(float2 a, float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+
+__device__ __forceinline__ void qs_two_sum2(float2& hi, float2& lo, float2 x)
+{
+    const float2 s = __fadd2_rn(hi, x);
+    const float2 bp = qs_sub2(s, hi);
+    const float2 err = __fadd2_rn(qs_sub2(hi, qs_sub2(s, bp)), qs_sub2(x, bp));
+    hi = s;
+    lo = __fadd2_rn(lo, err);
+}
+
 // Validate a grid coordinate; returns a safe value and records the error.
 __device__ __forceinline__ float qs_check_u(float u, float half_G, unsigned int* flag)
 {
@@ -200,9 +221,11 @@ __device__ __forceinline__ float qs_check_u(float u, float half_G, unsigned int*
 }
 
 // Targets per thread of the interpolation kernel (256 threads per CTA).
-__host__ __device__ inline int qs_interp_tpt(bool fused, int d)
+// Unfused: 8 for grids up to 2048 cells (the per-slice staging and range work
+// spread over more targets), 4 for larger grids, whose rows would cut occupancy.
+__host__ __device__ inline int qs_interp_tpt(bool fused, int d, int G)
 {
-    return !fused ? 4 : (d <= 8 ? 2 : 1);
+    return !fused ? (G <= 2048 ? 8 : 4) : (d <= 8 ? 2 : 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -229,8 +252,10 @@ cudaError_t qs_launch_reduce_grad(const float* part, int S, int64_t M, int d, fl
 bool qs_make_tmap(void* map_out, const void* base, int elem_bytes, int d, int64_t rows, int ldk, int box_rows);
 cudaError_t qs_launch_split_bf16(const float* X, int64_t rows, int d, int ldk, void* hi, void* lo, cudaStream_t st);
 cudaError_t qs_launch_round_tf32(const float* X, int64_t rows, int d, int ldk, float* out, cudaStream_t st);
-cudaError_t qs_launch_project_tc(int kind, const void* maps, int64_t N, int d, int P, float* U, int64_t ldU,
-                                 unsigned int* flag, cudaStream_t st);
+// Rows [n_base, n_base + N) of the staged operands into columns [n_base, n_base + N) of U;
+// n_base a multiple of 128.
+cudaError_t qs_launch_project_tc(int kind, const void* maps, int64_t n_base, int64_t N, int d, int P, float* U,
+                                 int64_t ldU, unsigned int* flag, cudaStream_t st);
 cudaError_t qs_launch_weight_scale(const qs_launch& L, const float* w, cudaStream_t st);
 cudaError_t qs_launch_spread(const qs_launch& L, int W, const float* x, const float* w, bool fused,
                              cudaStream_t st);

@@ -324,6 +324,9 @@ void free_plan(qs_plan p)
     if (!p) return;
     for (int i = 0; i < QS_NUM_STAGES + 1; ++i)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+    for (int i = 0; i < 1 + 2 * QS_HOST_CHUNKS; ++i)
+        if (p->hev[i]) cudaEventDestroy(p->hev[i]);
+    if (p->copy_st) cudaStreamDestroy(p->copy_st);
     void* bufs[] = {p->d_dirs, p->d_dirs_s, p->d_c, p->d_psihat, p->d_D, p->d_tw, p->d_U, p->d_H,
                     p->d_part, p->d_flag, p->d_wscale, p->d_x, p->d_w, p->d_y, p->d_s, p->d_xi_hi, p->d_xi_lo,
                     p->d_xs_hi, p->d_xs_lo, p->d_Dd, p->d_H2, p->d_gpart, p->d_sortws};
@@ -394,10 +397,41 @@ cudaError_t project_gemm(const qs_plan p, const float* X, int64_t rows, cudaStre
     const int d = p->desc.d, P = p->desc.P;
     switch (p->proj) {
         case QS_PROJ_FP32: return qs_launch_project_fp32(X, rows, d, p->d_dirs_s, P, p->d_U, p->ldU, st);
-        case QS_PROJ_BF16X3: return qs_launch_project_tc(0, p->tmaps, rows, d, P, p->d_U, p->ldU, p->d_flag, st);
-        case QS_PROJ_TF32: return qs_launch_project_tc(1, p->tmaps, rows, d, P, p->d_U, p->ldU, p->d_flag, st);
+        case QS_PROJ_BF16X3: return qs_launch_project_tc(0, p->tmaps, 0, rows, d, P, p->d_U, p->ldU, p->d_flag, st);
+        case QS_PROJ_TF32: return qs_launch_project_tc(1, p->tmaps, 0, rows, d, P, p->d_U, p->ldU, p->d_flag, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// Rows [r0, r0 + rows) of X (N x d, row-major) projected into columns
+// [r0, r0 + rows) of U, operand preparation included; r0 a multiple of 128.
+cudaError_t project_rows(const qs_plan p, const float* X, int64_t r0, int64_t rows, cudaStream_t st)
+{
+    const int d = p->desc.d, P = p->desc.P;
+    const float* Xr = X + r0 * d;
+    cudaError_t e;
+    switch (p->proj) {
+        case QS_PROJ_FP32: return qs_launch_project_fp32(Xr, rows, d, p->d_dirs_s, P, p->d_U + r0, p->ldU, st);
+        case QS_PROJ_BF16X3:
+            e = qs_launch_split_bf16(Xr, rows, d, p->ldk, (uint16_t*)p->d_xs_hi + r0 * p->ldk,
+                                     (uint16_t*)p->d_xs_lo + r0 * p->ldk, st);
+            return e == cudaSuccess ? qs_launch_project_tc(0, p->tmaps, r0, rows, d, P, p->d_U, p->ldU, p->d_flag, st)
+                                    : e;
+        case QS_PROJ_TF32:
+            e = qs_launch_round_tf32(Xr, rows, d, p->ldk, (float*)p->d_xs_hi + r0 * p->ldk, st);
+            return e == cudaSuccess ? qs_launch_project_tc(1, p->tmaps, r0, rows, d, P, p->d_U, p->ldU, p->d_flag, st)
+                                    : e;
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Rows per chunk of the qs_sum_host pipeline: at most QS_HOST_CHUNKS chunks,
+// a multiple of the GEMM's 128-row tile, at least 4096 rows.
+int64_t host_chunk_rows(int64_t n)
+{
+    int64_t c = (n + QS_HOST_CHUNKS - 1) / QS_HOST_CHUNKS;
+    c = (c + 127) / 128 * 128;
+    return c < 4096 ? 4096 : c;
 }
 
 // U = G tau X Xi^T for the plan's projection form.
@@ -770,7 +804,7 @@ qs_status qs_sum(qs_plan p, const float* x, int64_t N, const float* w, const flo
         return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_sum: memset");
     }
     const bool fused = p->proj == QS_PROJ_FP32_FUSED;
-    qs_launch L = make_launch(p, N, M, 256 * qs_interp_tpt(fused, p->desc.d));
+    qs_launch L = make_launch(p, N, M, 256 * qs_interp_tpt(fused, p->desc.d, p->G));
     const bool tm = p->timing != 0;
 #define QS_MARK(i)                                              \
     do {                                                        \
@@ -956,7 +990,7 @@ qs_status qs_grad(qs_plan p, const float* x, int64_t N, const float* w, const fl
             // gw uses the (fused) interpolation kernel, gx the gradient kernel: each
             // gets the slice-group count matching its CTA shape
             qs_launch L = make_launch(p, M, N, 256);
-            qs_launch Lw = make_launch(p, M, N, 256 * qs_interp_tpt(fused, p->desc.d));
+            qs_launch Lw = make_launch(p, M, N, 256 * qs_interp_tpt(fused, p->desc.d, p->G));
             e = qs_launch_weight_scale(L, v, st);
             if (e == cudaSuccess && !fused) e = project(p, y, M, st);
             if (e == cudaSuccess) {
@@ -1077,13 +1111,70 @@ qs_status qs_sum_host(qs_plan p, const float* xh, int64_t N, const float* wh, co
     cudaStream_t st = (cudaStream_t)stream;
     const int d = p->desc.d;
     cudaError_t e = cudaSuccess;
-    if (N > 0) e = cudaMemcpyAsync(p->d_x, xh, (size_t)N * d * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && N > 0 && wh)
-        e = cudaMemcpyAsync(p->d_w, wh, (size_t)N * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_y, yh, (size_t)M * d * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: copy in");
-    qs_status rs = qs_sum(p, p->d_x, N, wh ? p->d_w : nullptr, p->d_y, M, p->d_s, stream);
-    if (rs != QS_OK) return rs;
+    if (N == 0 || p->timing) {
+        // serial form: the stage timers of qs_sum stay meaningful
+        if (N > 0) e = cudaMemcpyAsync(p->d_x, xh, (size_t)N * d * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && N > 0 && wh)
+            e = cudaMemcpyAsync(p->d_w, wh, (size_t)N * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p->d_y, yh, (size_t)M * d * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: copy in");
+        qs_status rs = qs_sum(p, p->d_x, N, wh ? p->d_w : nullptr, p->d_y, M, p->d_s, stream);
+        if (rs != QS_OK) return rs;
+    } else {
+        // pipelined form: x, then y, arrive in row chunks on the plan's copy
+        // stream; each chunk's projection runs on `stream` as soon as the
+        // chunk has landed, so the transfer of x overlaps its GEMM and the
+        // transfer of y overlaps the spread and the GEMM of y
+        if (!p->copy_st) {
+            e = cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking);
+            for (int i = 0; e == cudaSuccess && i < 1 + 2 * QS_HOST_CHUNKS; ++i)
+                e = cudaEventCreateWithFlags(&p->hev[i], cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: copy stream");
+        }
+        cudaStream_t cs = p->copy_st;
+        cudaEvent_t* ex = p->hev + 1;
+        cudaEvent_t* ey = p->hev + 1 + QS_HOST_CHUNKS;
+        const bool fused = p->proj == QS_PROJ_FP32_FUSED;
+        const int64_t cx = host_chunk_rows(N), cy = host_chunk_rows(M);
+        const int nx = (int)((N + cx - 1) / cx), ny = (int)((M + cy - 1) / cy);
+        // the copies wait for the work already queued on `stream` (it may read the staging buffers)
+        e = cudaEventRecord(p->hev[0], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, p->hev[0], 0);
+        if (e == cudaSuccess && wh) e = cudaMemcpyAsync(p->d_w, wh, (size_t)N * sizeof(float), cudaMemcpyHostToDevice, cs);
+        for (int i = 0; e == cudaSuccess && i < nx; ++i) {
+            const int64_t r0 = i * cx, r = (N - r0 < cx ? N - r0 : cx);
+            e = cudaMemcpyAsync(p->d_x + r0 * d, xh + r0 * d, (size_t)r * d * sizeof(float), cudaMemcpyHostToDevice, cs);
+            if (e == cudaSuccess) e = cudaEventRecord(ex[i], cs);
+        }
+        for (int i = 0; e == cudaSuccess && i < ny; ++i) {
+            const int64_t r0 = i * cy, r = (M - r0 < cy ? M - r0 : cy);
+            e = cudaMemcpyAsync(p->d_y + r0 * d, yh + r0 * d, (size_t)r * d * sizeof(float), cudaMemcpyHostToDevice, cs);
+            if (e == cudaSuccess) e = cudaEventRecord(ey[i], cs);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: copy in");
+        qs_launch L = make_launch(p, N, M, 256 * qs_interp_tpt(fused, d, p->G));
+        if (fused) e = cudaStreamWaitEvent(st, ex[nx - 1], 0);
+        for (int i = 0; !fused && e == cudaSuccess && i < nx; ++i) {
+            const int64_t r0 = i * cx, r = (N - r0 < cx ? N - r0 : cx);
+            e = cudaStreamWaitEvent(st, ex[i], 0);
+            if (e == cudaSuccess) e = project_rows(p, p->d_x, r0, r, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: projection of x");
+        e = qs_launch_weight_scale(L, wh ? p->d_w : nullptr, st);
+        if (e == cudaSuccess) e = qs_launch_spread(L, p->W, p->d_x, wh ? p->d_w : nullptr, fused, st);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: spread");
+        if (fused) e = cudaStreamWaitEvent(st, ey[ny - 1], 0);
+        for (int i = 0; !fused && e == cudaSuccess && i < ny; ++i) {
+            const int64_t r0 = i * cy, r = (M - r0 < cy ? M - r0 : cy);
+            e = cudaStreamWaitEvent(st, ey[i], 0);
+            if (e == cudaSuccess) e = project_rows(p, p->d_y, r0, r, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: projection of y");
+        e = qs_launch_interp(L, p->W, p->d_y, fused, st);
+        if (e == cudaSuccess) e = qs_launch_reduce(L, p->d_s, st);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: interpolation");
+    }
     e = cudaMemcpyAsync(sh, p->d_s, (size_t)M * sizeof(float), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: copy out");
     return qs_check(p, stream);

@@ -201,7 +201,7 @@ template <int KIND>
 __global__ void __launch_bounds__(TCP_THREADS, 1)
     tc_project_persistent(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                           const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, int d,
-                          int P, int64_t N, float* __restrict__ U, int64_t ldU, unsigned int* flag)
+                          int P, int64_t n_base, int64_t N, float* __restrict__ U, int64_t ldU, unsigned int* flag)
 {
     using C = TcCfg<KIND>;
     constexpr int ST = PCfg<KIND>::STAGES;
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
         int64_t g = 0;
         for (int64_t t = blockIdx.x; t < T && ok && !abort_all; t += gridDim.x) {
             const int p0 = (int)(t % ptiles) * TILE_N;
-            const int n0 = (int)(t / ptiles) * TILE_M;
+            const int n0 = (int)(n_base + (t / ptiles) * TILE_M);
             for (int kb = 0; kb < nkb; ++kb, ++g) {
                 const int s = (int)(g % ST);
                 const uint32_t ph = (uint32_t)(g / ST) & 1u;
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
             }
             tc_fence_after();
             const int p0 = (int)(t % ptiles) * TILE_N;
-            const int64_t n = (t / ptiles) * TILE_M + 32 * q + lane;
+            const int64_t n = n_base + (t / ptiles) * TILE_M + 32 * q + lane;
             const uint32_t trow = tmem + (uint32_t)(a * TILE_N) + ((uint32_t)(32 * q) << 16);
 #pragma unroll 1
             for (int c = h * (TILE_N / 2); c < (h + 1) * (TILE_N / 2); c += 32) {
@@ -491,8 +491,8 @@ cudaError_t qs_launch_round_tf32(const float* X, int64_t rows, int d, int ldk, f
 }
 
 // maps: [A0, A1, B0, B1] (A1 / B1 unused by TF32), each a 64-byte-aligned CUtensorMap.
-cudaError_t qs_launch_project_tc(int kind, const void* maps, int64_t N, int d, int P, float* U, int64_t ldU,
-                                 unsigned int* flag, cudaStream_t st)
+cudaError_t qs_launch_project_tc(int kind, const void* maps, int64_t n_base, int64_t N, int d, int P, float* U,
+                                 int64_t ldU, unsigned int* flag, cudaStream_t st)
 {
     if (N <= 0) return cudaSuccess;
     const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(maps);
@@ -510,13 +510,13 @@ cudaError_t qs_launch_project_tc(int kind, const void* maps, int64_t N, int d, i
         cudaError_t e =
             cudaFuncSetAttribute(tc_project_persistent<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        tc_project_persistent<0><<<grid, TCP_THREADS, smem, st>>>(m[0], m[1], m[2], m[3], d, P, N, U, ldU, flag);
+        tc_project_persistent<0><<<grid, TCP_THREADS, smem, st>>>(m[0], m[1], m[2], m[3], d, P, n_base, N, U, ldU, flag);
     } else {
         const int smem = tcp_smem_bytes<1>();
         cudaError_t e =
             cudaFuncSetAttribute(tc_project_persistent<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        tc_project_persistent<1><<<grid, TCP_THREADS, smem, st>>>(m[0], m[0], m[2], m[2], d, P, N, U, ldU, flag);
+        tc_project_persistent<1><<<grid, TCP_THREADS, smem, st>>>(m[0], m[0], m[2], m[2], d, P, n_base, N, U, ldU, flag);
     }
     return cudaGetLastError();
 }

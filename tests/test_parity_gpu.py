@@ -166,6 +166,40 @@ def test_host_entry_point_matches_device_entry_point():
     assert _err(s_host, _oracle(prob), prob) < TOL_FP32
 
 
+@pytest.mark.parametrize("proj", ["fp32_fused", "fp32", "bf16x3", "tf32"])
+@pytest.mark.parametrize("N,M,use_w", [(12365, 9000, True), (40000, 4097, False), (100, 30000, True)])
+def test_host_pipeline_matches_device_sum_bitwise(proj, N, M, use_w):
+    # the host entry point moves x and y in row chunks (ragged last chunk here)
+    # and projects each chunk as it lands; every projected value, and so the
+    # whole sum, is the one the device entry point computes
+    import torch
+
+    prob = W.tiny(d=16, N=N, M=M, P=64, kernel="laplace", kparam=1.0, n_ft=128, seed=N % 97)
+    with _plan(prob, proj) as plan:
+        dev = plan.sum(torch.from_numpy(prob.x).cuda(), torch.from_numpy(prob.w).cuda() if use_w else None,
+                       torch.from_numpy(prob.y).cuda()).cpu().numpy()
+        plan.check()
+        side = torch.cuda.Stream()
+        host = plan.sum_host(prob.x, prob.w if use_w else None, prob.y, stream=side)
+        again = plan.sum_host(prob.x, prob.w if use_w else None, prob.y)
+    assert np.array_equal(host, dev)
+    assert np.array_equal(again, dev)
+    idx = np.arange(0, M, max(1, M // 50))
+    assert _err(host[idx].astype(np.float64), _oracle(prob, use_w, y=prob.y[idx]), prob, use_w) < TOL_FP32
+
+
+def test_host_pipeline_with_timing_and_empty_sources():
+    prob = W.tiny(d=16, N=9000, M=5000, P=32, kernel="gauss", kparam=1.0, n_ft=128, seed=5)
+    with _plan(prob, "bf16x3") as plan:
+        a = plan.sum_host(prob.x, prob.w, prob.y)
+        plan.set_timing(True)
+        b = plan.sum_host(prob.x, prob.w, prob.y)
+        plan.set_timing(False)
+        assert np.array_equal(a, b)
+        z = plan.sum_host(prob.x[:0], prob.w[:0], prob.y)
+        assert np.all(z == 0.0)
+
+
 @pytest.mark.parametrize("proj", ["fp32_fused", "fp32"])
 def test_repeated_calls_are_bitwise_identical(proj):
     # fixed-point grid accumulation, fixed FFT order and a fixed slice order
