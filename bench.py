@@ -236,6 +236,9 @@ def run_ours(args, rank, world, local_rank):
         spread_variant = args.spread_variant
     else:
         spread_variant = plan.autotune(x, w)
+    if args.gemm != "auto" and plan.proj in ("bf16x3", "tf32"):
+        plan.set_gemm(args.gemm == "pair")
+    gemm = ("pair" if plan.gemm_pair() else "single") if plan.proj in ("bf16x3", "tf32") else None
     for _ in range(args.warmup):
         plan.sum(x, w, y, out=s)
     plan.check()
@@ -309,6 +312,8 @@ def run_ours(args, rank, world, local_rank):
                        "rel_err_norm": "max_m |s - s_oracle| / (sum|w| max|F|)",
                        "stage_ms": {k: round(v, 4) for k, v in stages.items()},
                        "spread_variant": spread_variant,
+                       "gemm": gemm,
+                       "gemm_ctas": plan.gemm_ctas() if gemm else None,
                        "device_status": int(status)},
             "roofline": roof,
             "stage_rooflines": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()
@@ -705,15 +710,18 @@ def launches_per_step(plan) -> int:
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of the default workload itself
-# (d = 784, N = M = 60000, P = 2048, N_ft = 1024, BF16x3, momentwin32 spread;
-# profiles/traffic_mnist_laplace.md).  Only for that configuration and the kernels as captured.
-TRAFFIC_MNIST = {"project_x": 631.3e6, "project_y": 628.4e6, "spread_filter": 504.5e6, "interp": 515.0e6}
+# (d = 784, N = M = 60000, P = 2048, N_ft = 1024, BF16x3 on the SM-pair GEMM, momentwin32
+# spread, 8 targets per interpolation thread; profiles/traffic_mnist_laplace.md).  Only for
+# that configuration and the kernels as captured.
+TRAFFIC_MNIST = {"project_x": 635.9e6, "project_y": 633.0e6, "spread_filter": 504.4e6, "interp": 520.4e6}
 
 
 def _traffic(prob, plan, name):
     if (prob.d, prob.N, prob.M, prob.P, prob.n_ft, plan.proj) != (784, 60000, 60000, 2048, 1024, "bf16x3"):
         return None
     if name == "spread_filter" and plan.variant() != "momentwin32":
+        return None
+    if name.startswith("project") and not plan.gemm_pair():
         return None
     return TRAFFIC_MNIST.get(name)
 
@@ -800,7 +808,8 @@ def roofline(prob, plan, stages, clocks, peaks, peak_src, sm_count):
                 "traffic": (sum(tr) / len(tr)) if all(t is not None for t in tr) else None,
                 "ms": best_ms, "ms_per_launch": best_ms / len(got)})
     if kern == "projection GEMM":
-        out["kernel"] = {"bf16x3": "tc_project_persistent<BF16x3>", "tf32": "tc_project_persistent<TF32>",
+        tc = "tc_project_pair" if plan.proj in ("bf16x3", "tf32") and plan.gemm_pair() else "tc_project_persistent"
+        out["kernel"] = {"bf16x3": f"{tc}<BF16x3>", "tf32": f"{tc}<TF32>",
                          "fp32": "project_fp32_kernel"}.get(plan.proj, kern)
     if len(got) > 1:
         out["algorithmic"] = (" + ".join(g["algorithmic"].split(" = ")[0] for g in got)
@@ -874,6 +883,8 @@ def main():
     ap.add_argument("--no-error-check", action="store_true")
     ap.add_argument("--spread-variant", default="", help="fix the spread variant instead of timing the family")
     ap.add_argument("--sorted", action="store_true", help="negdist workloads: exact sums by sorting slicing")
+    ap.add_argument("--gemm", default="auto", choices=["auto", "pair", "single"],
+                    help="tensor-core projection GEMM on SM pairs (cta_group::2) or one CTA per SM")
     ap.add_argument("--error-targets", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-slices", type=int, default=128)

@@ -315,6 +315,22 @@ qs_status qs_plan_set_variant(qs_plan plan, int spread_variant);
 qs_status qs_plan_variants(qs_plan plan, unsigned int* available, int* current);
 
 /*
+ * Projection GEMM form of a tensor-core plan (QS_PROJ_BF16X3 / QS_PROJ_TF32):
+ * pair = 0 runs one CTA per SM on 128-point x 256-slice tiles; pair = 1 runs
+ * clusters of two CTAs on SM pairs (tcgen05 cta_group::2) on 256-point x
+ * 256-slice tiles, which halves the shared-memory reads of the directions per
+ * SM.  qs_plan_create picks pair = 1 wherever such clusters can be resident.  Both give the same projections up to the order of the tensor cores'
+ * internal FP32 sums.  QS_ERR_UNSUPPORTED for pair = 1 on other projection
+ * forms or where two-CTA clusters of the kernel cannot be resident;
+ * QS_ERR_ARG for other values.  qs_plan_gemm reports the form in use (0 / 1)
+ * in *pair and, if ctas is not NULL, the CTAs a full-size launch of it runs
+ * (SM count, or twice the resident two-CTA clusters).  Host only; affects
+ * later calls.
+ */
+qs_status qs_plan_set_gemm(qs_plan plan, int pair);
+qs_status qs_plan_gemm(qs_plan plan, int* pair, int* ctas);
+
+/*
  * Sorting slicing for the negative distance kernel (Sec. 2.1, eq.
  * kernel_sum_sliced with f(t) = -c_d |t|; the sorting evaluation the paper
  * uses for this kernel): the sliced sum over the plan's directions computed

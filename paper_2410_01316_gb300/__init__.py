@@ -123,6 +123,22 @@ class QSPlan:
         _lib.check(self._lib.qs_plan_set_variant(self._handle, self.SPREAD_VARIANTS.index(name)),
                    "qs_plan_set_variant")
 
+    def set_gemm(self, pair: bool) -> None:
+        """Projection GEMM on SM pairs (tcgen05 cta_group::2, 256-point tiles) or one CTA per SM."""
+        _lib.check(self._lib.qs_plan_set_gemm(self._handle, 1 if pair else 0), "qs_plan_set_gemm")
+
+    def gemm_pair(self) -> bool:
+        """Whether the projection GEMM runs on SM pairs."""
+        v = ctypes.c_int(-1)
+        _lib.check(self._lib.qs_plan_gemm(self._handle, ctypes.byref(v), None), "qs_plan_gemm")
+        return v.value == 1
+
+    def gemm_ctas(self) -> int:
+        """CTAs of a full-size launch of the plan's projection GEMM."""
+        v, c = ctypes.c_int(-1), ctypes.c_int(-1)
+        _lib.check(self._lib.qs_plan_gemm(self._handle, ctypes.byref(v), ctypes.byref(c)), "qs_plan_gemm")
+        return c.value
+
     def spread_variants(self) -> tuple:
         """Names of the spread variants of this plan's family (bitwise identical to each other)."""
         mask = ctypes.c_uint(0)

@@ -33,7 +33,7 @@ EXPORTS = ("qs_plan_create", "qs_plan_destroy", "qs_plan_info", "qs_plan_directi
            "qs_set_timing", "qs_stage_times", "qs_project", "qs_sum_noalloc", "qs_grad",
            "qs_plan_autotune", "qs_plan_set_variant", "qs_batch_create", "qs_batch_destroy", "qs_sum_batched",
            "qs_batch_check", "qs_batch_set_tiling", "qs_plan_variants", "qs_distance_design",
-           "qs_distance_energy", "qs_sum_sorted", "qs_grad_sorted")
+           "qs_distance_energy", "qs_sum_sorted", "qs_grad_sorted", "qs_plan_set_gemm", "qs_plan_gemm")
 
 
 class PlanDesc(ctypes.Structure):
@@ -87,6 +87,8 @@ def load() -> ctypes.CDLL:
         lib.qs_batch_set_tiling.argtypes = [c_vp, c_int]
         lib.qs_plan_autotune.argtypes = [c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(c_int), c_vp]
         lib.qs_plan_set_variant.argtypes = [c_vp, c_int]
+        lib.qs_plan_set_gemm.argtypes = [c_vp, c_int]
+        lib.qs_plan_gemm.argtypes = [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
         lib.qs_plan_variants.argtypes = [c_vp, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(c_int)]
         lib.qs_distance_design.argtypes = [c_vp, c_int, c_int, c_int, c_dbl, ctypes.POINTER(c_dbl), c_vp]
         lib.qs_distance_energy.argtypes = [c_vp, c_int, c_int, ctypes.POINTER(c_dbl), c_vp, c_vp]
@@ -103,7 +105,7 @@ def load() -> ctypes.CDLL:
                      "qs_sum_noalloc", "qs_grad", "qs_plan_autotune", "qs_plan_set_variant",
                      "qs_batch_create", "qs_batch_destroy", "qs_sum_batched", "qs_batch_check",
                      "qs_batch_set_tiling", "qs_plan_variants", "qs_distance_design", "qs_distance_energy",
-                     "qs_sum_sorted", "qs_grad_sorted"):
+                     "qs_sum_sorted", "qs_grad_sorted", "qs_plan_set_gemm", "qs_plan_gemm"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib

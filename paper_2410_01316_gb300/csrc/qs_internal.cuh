@@ -143,7 +143,10 @@ struct qs_plan_s {
     void* d_xs_hi;        // max(max_n, max_m) x ldk staging of the points
     void* d_xs_lo;        // (BF16x3 only)
     void* d_sortws = nullptr;  // sorting-slicing workspace, allocated by the first qs_sum_sorted
-    alignas(64) unsigned char tmaps[4][128];  // CUtensorMap: points hi/lo, directions hi/lo
+    // CUtensorMap: points hi/lo (128-row boxes), directions hi/lo (256-row boxes),
+    // directions hi/lo (128-row boxes, the SM-pair kernel)
+    alignas(64) unsigned char tmaps[6][128];
+    bool gemm_pair;       // projection GEMM on SM pairs (cta_group::2)
     // stage timing (qs_set_timing)
     int timing;
     int timed_calls;
@@ -254,8 +257,11 @@ cudaError_t qs_launch_split_bf16(const float* X, int64_t rows, int d, int ldk, v
 cudaError_t qs_launch_round_tf32(const float* X, int64_t rows, int d, int ldk, float* out, cudaStream_t st);
 // Rows [n_base, n_base + N) of the staged operands into columns [n_base, n_base + N) of U;
 // n_base a multiple of 128.
+// pair: the SM-pair (cta_group::2) kernel, which needs maps 4 / 5 and qs_tc_pair_available.
 cudaError_t qs_launch_project_tc(int kind, const void* maps, int64_t n_base, int64_t N, int d, int P, float* U,
-                                 int64_t ldU, unsigned int* flag, cudaStream_t st);
+                                 int64_t ldU, unsigned int* flag, cudaStream_t st, bool pair);
+bool qs_tc_pair_available(int kind);
+int qs_tc_pair_ctas(int kind);  // CTAs of a full-size SM-pair launch (2 x resident clusters)
 cudaError_t qs_launch_weight_scale(const qs_launch& L, const float* w, cudaStream_t st);
 cudaError_t qs_launch_spread(const qs_launch& L, int W, const float* x, const float* w, bool fused,
                              cudaStream_t st);

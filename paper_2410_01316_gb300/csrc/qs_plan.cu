@@ -397,8 +397,10 @@ cudaError_t project_gemm(const qs_plan p, const float* X, int64_t rows, cudaStre
     const int d = p->desc.d, P = p->desc.P;
     switch (p->proj) {
         case QS_PROJ_FP32: return qs_launch_project_fp32(X, rows, d, p->d_dirs_s, P, p->d_U, p->ldU, st);
-        case QS_PROJ_BF16X3: return qs_launch_project_tc(0, p->tmaps, 0, rows, d, P, p->d_U, p->ldU, p->d_flag, st);
-        case QS_PROJ_TF32: return qs_launch_project_tc(1, p->tmaps, 0, rows, d, P, p->d_U, p->ldU, p->d_flag, st);
+        case QS_PROJ_BF16X3:
+            return qs_launch_project_tc(0, p->tmaps, 0, rows, d, P, p->d_U, p->ldU, p->d_flag, st, p->gemm_pair);
+        case QS_PROJ_TF32:
+            return qs_launch_project_tc(1, p->tmaps, 0, rows, d, P, p->d_U, p->ldU, p->d_flag, st, p->gemm_pair);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -415,11 +417,13 @@ cudaError_t project_rows(const qs_plan p, const float* X, int64_t r0, int64_t ro
         case QS_PROJ_BF16X3:
             e = qs_launch_split_bf16(Xr, rows, d, p->ldk, (uint16_t*)p->d_xs_hi + r0 * p->ldk,
                                      (uint16_t*)p->d_xs_lo + r0 * p->ldk, st);
-            return e == cudaSuccess ? qs_launch_project_tc(0, p->tmaps, r0, rows, d, P, p->d_U, p->ldU, p->d_flag, st)
+            return e == cudaSuccess ? qs_launch_project_tc(0, p->tmaps, r0, rows, d, P, p->d_U, p->ldU, p->d_flag, st,
+                                                           p->gemm_pair)
                                     : e;
         case QS_PROJ_TF32:
             e = qs_launch_round_tf32(Xr, rows, d, p->ldk, (float*)p->d_xs_hi + r0 * p->ldk, st);
-            return e == cudaSuccess ? qs_launch_project_tc(1, p->tmaps, r0, rows, d, P, p->d_U, p->ldU, p->d_flag, st)
+            return e == cudaSuccess ? qs_launch_project_tc(1, p->tmaps, r0, rows, d, P, p->d_U, p->ldU, p->d_flag, st,
+                                                           p->gemm_pair)
                                     : e;
         default: return cudaErrorInvalidValue;
     }
@@ -741,14 +745,18 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
         else
             QS_CHECK(qs_launch_round_tf32(p->d_dirs_s, P, d, p->ldk, (float*)p->d_xi_hi, 0), "round directions");
         bool ok = qs_make_tmap(p->tmaps[0], p->d_xs_hi, eb, d, stage_rows, p->ldk, 128) &&
-                  qs_make_tmap(p->tmaps[2], p->d_xi_hi, eb, d, P, p->ldk, 256);
+                  qs_make_tmap(p->tmaps[2], p->d_xi_hi, eb, d, P, p->ldk, 256) &&
+                  qs_make_tmap(p->tmaps[4], p->d_xi_hi, eb, d, P, p->ldk, 128);
         if (ok && proj == QS_PROJ_BF16X3)
             ok = qs_make_tmap(p->tmaps[1], p->d_xs_lo, eb, d, stage_rows, p->ldk, 128) &&
-                 qs_make_tmap(p->tmaps[3], p->d_xi_lo, eb, d, P, p->ldk, 256);
+                 qs_make_tmap(p->tmaps[3], p->d_xi_lo, eb, d, P, p->ldk, 256) &&
+                 qs_make_tmap(p->tmaps[5], p->d_xi_lo, eb, d, P, p->ldk, 128);
         if (!ok) {
             free_plan(p);
             return fail(QS_ERR_CUDA, "qs_plan_create: cuTensorMapEncodeTiled failed");
         }
+        // the SM-pair GEMM wherever two-CTA clusters of it can be resident
+        p->gemm_pair = qs_tc_pair_available(proj == QS_PROJ_BF16X3 ? 0 : 1);
     }
     QS_CHECK(cudaDeviceSynchronize(), "coefficient kernel");
 #undef QS_CHECK
@@ -1019,6 +1027,32 @@ qs_status qs_plan_set_variant(qs_plan p, int v)
         return fail(QS_ERR_ARG, "qs_plan_set_variant: variant %d is not in this plan's family (%s spread for G = %d, W = %d)",
                     v, qs_spread_moments(p->G, p->W) ? "moment" : "tap", p->G, p->W);
     p->spread_variant = v;
+    return QS_OK;
+}
+
+qs_status qs_plan_set_gemm(qs_plan p, int pair)
+{
+    if (!p) return fail(QS_ERR_ARG, "qs_plan_set_gemm: NULL plan");
+    if (pair != 0 && pair != 1) return fail(QS_ERR_ARG, "qs_plan_set_gemm: pair must be 0 or 1");
+    if (pair) {
+        if (p->proj != QS_PROJ_BF16X3 && p->proj != QS_PROJ_TF32)
+            return fail(QS_ERR_UNSUPPORTED, "qs_plan_set_gemm: the SM-pair GEMM needs a tensor-core projection");
+        DeviceGuard g(p->device);
+        if (!qs_tc_pair_available(p->proj == QS_PROJ_BF16X3 ? 0 : 1))
+            return fail(QS_ERR_UNSUPPORTED, "qs_plan_set_gemm: two-CTA clusters of the GEMM cannot be resident");
+    }
+    p->gemm_pair = pair != 0;
+    return QS_OK;
+}
+
+qs_status qs_plan_gemm(qs_plan p, int* pair, int* ctas)
+{
+    if (!p || !pair) return fail(QS_ERR_ARG, "qs_plan_gemm: NULL argument");
+    *pair = p->gemm_pair ? 1 : 0;
+    if (ctas) {
+        DeviceGuard g(p->device);
+        *ctas = p->gemm_pair ? qs_tc_pair_ctas(p->proj == QS_PROJ_BF16X3 ? 0 : 1) : p->sm_count;
+    }
     return QS_OK;
 }
 

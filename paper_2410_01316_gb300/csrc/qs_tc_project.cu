@@ -3,13 +3,18 @@
 //
 //     U[p][n] = u_{n,p} = G tau <x_n, xi_p>,   D = X Xi_s^T on the tensor cores
 //
-// A persistent kernel, one CTA per SM, computes 128-point x 256-slice tiles.
-// TMA streams K-major slabs of the points (A, 128 rows) and of the scaled
-// directions (B, 256 rows) into 64-byte-swizzled shared memory through a
-// ring of stages; one thread issues tcgen05.mma into one of two 256-column
-// FP32 accumulators in tensor memory while four warps read the other back
-// with tcgen05.ld and store U with one coalesced 128-byte row segment per
-// warp and slice.
+// Two persistent kernels.  tc_project_persistent: one CTA per SM computes
+// 128-point x 256-slice tiles; TMA streams K-major slabs of the points (A,
+// 128 rows) and of the scaled directions (B, 256 rows) into 64-byte-swizzled
+// shared memory through a ring of stages; one thread issues tcgen05.mma into
+// one of two 256-column FP32 accumulators in tensor memory while eight warps
+// read the other back with tcgen05.ld and store U with one coalesced 128-byte
+// row segment per warp and slice.  tc_project_pair (the default): a cluster
+// of two CTAs on an SM pair computes 256-point x 256-slice tiles with
+// cta_group::2 MMAs (M = 256), each CTA holding half of every A and B slab;
+// per SM that cuts the shared-memory traffic of a k-step from 160 to about
+// 106 bytes per clock at the tensor pipe's rate, below the 128 the shared
+// memory delivers, which bounded the single-SM form.
 //
 // Two precision forms:
 //   BF16x3  x = x_hi + x_lo and xi = xi_hi + xi_lo in BF16 (round to nearest);
@@ -373,6 +378,320 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// SM-pair form (cta_group::2): a cluster of two CTAs on an SM pair computes
+// 256-point x 256-slice tiles with one M = 256 MMA per k-step.  CTA r of the
+// pair (r = cluster rank) keeps points n0 + 128 r .. + 127 (A) and slices
+// p0 + 128 r .. + 127 (B) of each k-slab in its own shared memory; the pair's
+// MMA takes A from each CTA and B from both, so per SM a k-step reads half
+// the B bytes of the single-SM form from shared memory and TMA writes two
+// thirds of its bytes there.  The even CTA (the leader) issues the MMAs; its
+// producer announces both CTAs' TMA bytes on its full barrier of the stage,
+// on which the odd CTA's copies complete too (an mbarrier's transaction count
+// may run below zero until the announcement); the leader's commits arrive on the empty, tfull and drain barriers of both
+// CTAs (multicast); each CTA's tensor memory holds the accumulator rows of
+// its own 128 points, drained to U by its eight epilogue warps, which arrive
+// on the leader's tempty barriers.  One warp of each CTA allocates and frees
+// the pair's tensor memory together.  Waits on barriers are bounded as in the
+// single-SM form; both CTAs always reach the closing cluster barrier.
+// ---------------------------------------------------------------------------
+template <int KIND>
+struct PairCfg;
+template <>
+struct PairCfg<0> {  // BF16x3: 32 KB stages
+    static constexpr int STAGES = 6;
+};
+template <>
+struct PairCfg<1> {  // TF32: 16 KB stages
+    static constexpr int STAGES = 12;
+};
+
+constexpr int PB_ROWS = TILE_N / 2;            // slices of a B slab held by one CTA
+constexpr int PB_BYTES = PB_ROWS * ROW_BYTES;
+
+template <int KIND>
+__host__ __device__ constexpr int pair_stage_bytes()
+{
+    return TcCfg<KIND>::NOPS * (A_BYTES + PB_BYTES);
+}
+
+template <int KIND>
+__host__ __device__ constexpr int pair_smem_bytes()
+{
+    return 1024 + PairCfg<KIND>::STAGES * pair_stage_bytes<KIND>() + 256;
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_id_x()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_count_x()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+
+// All threads of both CTAs; release / acquire orders their shared-memory work.
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Shared::cluster address of the variable at shared::cta address `addr` in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cl_bar)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_bar) : "memory");
+}
+
+// TMA load into this CTA's shared memory whose completion is counted on a
+// barrier of either CTA of the pair (cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t cl_bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, "
+        "%3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(cl_bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_f16_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// Arrive once on the barrier at offset `bar` of both CTAs of the pair when all
+// MMAs issued so far by this thread have completed.
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"((unsigned short)3)
+        : "memory");
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(TCP_THREADS, 1)
+    tc_project_pair(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+                    const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, int d, int P,
+                    int64_t n_base, int64_t N, float* __restrict__ U, int64_t ldU, unsigned int* flag)
+{
+    using C = TcCfg<KIND>;
+    constexpr int ST = PairCfg<KIND>::STAGES;
+    constexpr int SB = pair_stage_bytes<KIND>();
+    constexpr uint32_t IDESC = make_idesc(KIND == 0 ? 1u : 2u, 2 * TILE_M, TILE_N);
+    constexpr int PAIR_M = 2 * TILE_M;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ volatile int abort_all;
+    const uint32_t base = smem_u32(smem_raw);
+    const uint32_t tiles = (base + 1023u) & ~1023u;
+    const uint32_t bars = tiles + ST * SB;
+    const uint32_t full0 = bars;              // full[s]   = full0 + 8 s   (used in the leader)
+    const uint32_t empty0 = bars + 8 * ST;    // empty[s]  = empty0 + 8 s
+    const uint32_t tfull0 = bars + 16 * ST;   // tfull[a]  = tfull0 + 8 a
+    const uint32_t tempty0 = tfull0 + 16;     // tempty[a] = tempty0 + 8 a (used in the leader)
+    const uint32_t drain = tempty0 + 16;      // every MMA of the pair has completed
+    const uint32_t tmem_slot = drain + 8;
+    uint32_t* tmem_slot_ptr = reinterpret_cast<uint32_t*>(smem_raw + (tmem_slot - base));
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int64_t cid = cluster_id_x();
+    const int64_t ncl = cluster_count_x();
+    const int nkb = (d + C::BK - 1) / C::BK;
+    const int ptiles = (P + TILE_N - 1) / TILE_N;
+    const int64_t ntiles = (N + PAIR_M - 1) / PAIR_M;
+    const int64_t T = ntiles * ptiles;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(full0 + 8 * s, 1);  // the leader's producer
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull0 + 8 * a, 1);
+            mbar_init(tempty0 + 8 * a, 2 * TCP_EPI_WARPS);
+        }
+        mbar_init(drain, 1);
+        abort_all = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tmem_slot),
+                     "r"(2 * TILE_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();  // both CTAs' barriers exist before any remote arrival
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot_ptr;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer of this CTA's halves: slab g uses stage g % ST; the
+        // copies complete on the leader's full barrier of that stage
+        bool ok = true;
+        int64_t g = 0;
+        for (int64_t t = cid; t < T && ok && !abort_all; t += ncl) {
+            const int pr = (int)(t % ptiles) * TILE_N + (int)rank * PB_ROWS;
+            const int nr = (int)(n_base + (t / ptiles) * PAIR_M + (int64_t)rank * TILE_M);
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+                const int s = (int)(g % ST);
+                const uint32_t ph = (uint32_t)(g / ST) & 1u;
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t fb = cluster_addr(full0 + 8 * s, 0);  // the leader's full[s]
+                const uint32_t st = tiles + s * SB;
+                const int kc = kb * C::BK;
+                if (leader) mbar_expect_tx(full0 + 8 * s, 2 * SB);
+                tma_load_2d_pair(st, &mA0, kc, nr, fb);
+                if (C::NOPS == 2) tma_load_2d_pair(st + A_BYTES, &mA1, kc, nr, fb);
+                tma_load_2d_pair(st + C::NOPS * A_BYTES, &mB0, kc, pr, fb);
+                if (C::NOPS == 2) tma_load_2d_pair(st + C::NOPS * A_BYTES + PB_BYTES, &mB1, kc, pr, fb);
+            }
+        }
+        // the leader's full barriers also count the odd CTA's bytes: once the
+        // last stages have completed, no copy of the pair is in flight
+        if (leader)
+            for (int64_t h = (g > ST ? g - ST : 0); h < g; ++h)
+                if (!mbar_wait(full0 + 8 * (int)(h % ST), (uint32_t)(h / ST) & 1u)) ok = false;
+        if (!ok) {
+            abort_all = 1;
+            atomicOr(flag, QS_FLAG_TIMEOUT);
+        }
+    } else if (warp == 1 && lane == 0) {
+        bool ok = true;
+        if (leader) {
+            // MMA issuer of the pair
+            int64_t g = 0;
+            int i = 0;
+            for (int64_t t = cid; t < T && ok && !abort_all; t += ncl, ++i) {
+                const int a = i & 1;
+                if (!mbar_wait(tempty0 + 8 * a, (((uint32_t)i >> 1) & 1u) ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)(a * TILE_N);
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = (int)(g % ST);
+                    if (!mbar_wait(full0 + 8 * s, (uint32_t)(g / ST) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = tiles + s * SB;
+                    const uint32_t a0 = st, a1 = st + A_BYTES;
+                    const uint32_t b0 = st + C::NOPS * A_BYTES, b1 = b0 + PB_BYTES;
+#pragma unroll
+                    for (int k = 0; k < C::BK / C::KSTEP; ++k) {
+                        const uint32_t off = (uint32_t)(k * C::KSTEP * C::ESZ);
+                        const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+                        if (KIND == 0) {
+                            mma_f16_pair(dt, sw64_desc(a0 + off), sw64_desc(b0 + off), IDESC, acc);
+                            mma_f16_pair(dt, sw64_desc(a0 + off), sw64_desc(b1 + off), IDESC, 1u);
+                            mma_f16_pair(dt, sw64_desc(a1 + off), sw64_desc(b0 + off), IDESC, 1u);
+                        } else {
+                            mma_tf32_pair(dt, sw64_desc(a0 + off), sw64_desc(b0 + off), IDESC, acc);
+                        }
+                    }
+                    mma_commit_pair(empty0 + 8 * s);
+                }
+                if (ok) mma_commit_pair(tfull0 + 8 * a);
+            }
+            mma_commit_pair(drain);
+        }
+        // tensor memory of both CTAs is written by the leader's MMAs: wait for all of them
+        if (!mbar_wait(drain, 0)) ok = false;
+        if (!ok) {
+            abort_all = 1;
+            atomicOr(flag, QS_FLAG_TIMEOUT);
+        }
+    } else if (warp >= 2) {
+        // epilogue: lane quarter q = warp % 4 of this CTA's accumulator holds
+        // points nr + 32 q + lane; the two warps of a quarter split the columns
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
+        const uint32_t tempty_l[2] = {cluster_addr(tempty0, 0), cluster_addr(tempty0 + 8, 0)};
+        int i = 0;
+        for (int64_t t = cid; t < T; t += ncl, ++i) {
+            if (abort_all) break;
+            const int a = i & 1;
+            const bool got = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * a, ((uint32_t)i >> 1) & 1u));
+            if (!got) {
+                if (lane == 0) {
+                    abort_all = 1;
+                    atomicOr(flag, QS_FLAG_TIMEOUT);
+                }
+                break;
+            }
+            tc_fence_after();
+            const int p0 = (int)(t % ptiles) * TILE_N;
+            const int64_t n = n_base + (t / ptiles) * PAIR_M + (int64_t)rank * TILE_M + 32 * q + lane;
+            // a 256-row pair tile can pass the 128-rounded width of U: store rows < n_base + N only
+            const bool row_ok = n < n_base + N;
+            const uint32_t trow = tmem + (uint32_t)(a * TILE_N) + ((uint32_t)(32 * q) << 16);
+#pragma unroll 1
+            for (int c = h * (TILE_N / 2); c < (h + 1) * (TILE_N / 2); c += 32) {
+                float v[32];
+                __syncwarp();
+                tmem_ld32(trow + (uint32_t)c, v);
+                const int pc = p0 + c;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (row_ok && pc + j < P) U[(size_t)(pc + j) * ldU + n] = v[j];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(tempty_l[a]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();  // both CTAs are done with the pair's barriers and tensor memory
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TILE_N)
+                     : "memory");
+    }
+}
+
 // BF16 split of an FP32 row-major matrix (rows x d) into hi and lo parts with
 // row stride ldk (padding columns zero): hi = bf16_rn(v), lo = bf16_rn(v - hi).
 // Each thread converts 4 consecutive entries of a row (ldk is a multiple of
@@ -490,12 +809,86 @@ cudaError_t qs_launch_round_tf32(const float* X, int64_t rows, int d, int ldk, f
     return cudaGetLastError();
 }
 
-// maps: [A0, A1, B0, B1] (A1 / B1 unused by TF32), each a 64-byte-aligned CUtensorMap.
+namespace {
+
+// Co-resident clusters of the SM-pair kernel (0 if it cannot run here).
+template <int KIND>
+int pair_clusters()
+{
+    static int n = -1;
+    if (n < 0) {
+        int v = 0;
+        const int smem = pair_smem_bytes<KIND>();
+        if (cudaFuncSetAttribute(tc_project_pair<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+            cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(2, 1, 1);
+            cfg.blockDim = dim3(TCP_THREADS, 1, 1);
+            cfg.dynamicSmemBytes = smem;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            if (cudaOccupancyMaxActiveClusters(&v, tc_project_pair<KIND>, &cfg) != cudaSuccess) v = 0;
+        }
+        cudaGetLastError();  // a refusal here only means the pair form is unavailable
+        n = v;
+    }
+    return n;
+}
+
+template <int KIND>
+cudaError_t launch_pair(const CUtensorMap* m, int64_t n_base, int64_t N, int d, int P, float* U, int64_t ldU,
+                        unsigned int* flag, cudaStream_t st)
+{
+    const int ncl_max = pair_clusters<KIND>();
+    if (ncl_max <= 0) return cudaErrorNotSupported;
+    const int smem = pair_smem_bytes<KIND>();
+    const int64_t T = ((N + 2 * TILE_M - 1) / (2 * TILE_M)) * ((P + TILE_N - 1) / TILE_N);
+    const int ncl = (int)(T < ncl_max ? T : ncl_max);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(2 * ncl), 1, 1);
+    cfg.blockDim = dim3(TCP_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // maps 4 / 5: the directions with 128-row boxes (one CTA's half of a B slab)
+    const CUtensorMap& a1 = KIND == 0 ? m[1] : m[0];
+    const CUtensorMap& b1 = KIND == 0 ? m[5] : m[4];
+    cudaError_t e = cudaLaunchKernelEx(&cfg, tc_project_pair<KIND>, m[0], a1, m[4], b1, d, P, n_base, N, U, ldU, flag);
+    return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+}  // namespace
+
+bool qs_tc_pair_available(int kind)
+{
+    return (kind == 0 ? pair_clusters<0>() : pair_clusters<1>()) > 0;
+}
+
+int qs_tc_pair_ctas(int kind)
+{
+    return 2 * (kind == 0 ? pair_clusters<0>() : pair_clusters<1>());
+}
+
+// maps: [A0, A1, B0, B1, B0 half, B1 half] (A1 / B1 unused by TF32), each a
+// 64-byte-aligned CUtensorMap; B maps 2 / 3 have 256-row boxes, 4 / 5 128-row boxes.
 cudaError_t qs_launch_project_tc(int kind, const void* maps, int64_t n_base, int64_t N, int d, int P, float* U,
-                                 int64_t ldU, unsigned int* flag, cudaStream_t st)
+                                 int64_t ldU, unsigned int* flag, cudaStream_t st, bool pair)
 {
     if (N <= 0) return cudaSuccess;
     const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(maps);
+    if (pair) return kind == 0 ? launch_pair<0>(m, n_base, N, d, P, U, ldU, flag, st)
+                               : launch_pair<1>(m, n_base, N, d, P, U, ldU, flag, st);
     static int sms = 0;
     if (!sms) {
         int dev = 0;

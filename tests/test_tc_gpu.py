@@ -94,3 +94,67 @@ def test_mnist_laplace_full_size_all_forms():
     for form, tol in (("bf16x3", 1e-3), ("tf32", 1e-3), ("fp32", 1e-5)):
         err = np.max(np.abs(_sum(prob, form)[idx] - ref)) / _norm(prob)
         assert err < tol, (form, err)
+
+
+# SM-pair GEMM (tcgen05 cta_group::2, 256-point x 256-slice tiles on a cluster of two CTAs)
+@pytest.mark.parametrize("form", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("d,N,P", [(784, 1000, 512), (5, 257, 100), (16, 129, 257), (64, 3000, 384), (33, 640, 1000)])
+def test_pair_gemm_projection_within_rounding_bound(form, d, N, P):
+    import torch
+
+    prob = W.tiny(d=d, N=N, M=7, P=P, kernel="negdist", kparam=0.0, n_ft=64, seed=d + N + 1)
+    out = {}
+    with QSPlan(d, "negdist", P, 64, prob.R, dirs=prob.xi, proj=form, max_n=N, max_m=7) as plan:
+        for pair in (False, True):
+            plan.set_gemm(pair)
+            assert plan.gemm_pair() == pair
+            u = plan.project(torch.from_numpy(prob.x).cuda())
+            plan.check()
+            out[pair] = u.cpu().numpy().astype(np.float64)
+        scale = plan.G * plan.tau
+    X = prob.x.astype(np.float64)
+    Xi = prob.xi.astype(np.float64)
+    ref = scale * (Xi @ X.T)
+    absb = scale * (np.abs(Xi) @ np.abs(X).T)
+    ratio = np.max(np.abs(out[True] - ref) / (_bound(form, d) * absb + 1e-30))
+    assert ratio <= 1.0, f"worst error / bound = {ratio:.3g}"
+    # same products, same K order: the two forms may differ only in the tensor
+    # cores' internal accumulation
+    gap = np.max(np.abs(out[True] - out[False]) / (_bound(form, d) * absb + 1e-30))
+    assert gap <= 1.0, f"pair vs single-SM gap / bound = {gap:.3g}"
+
+
+def test_pair_gemm_full_sum_and_host_pipeline():
+    # N = 33000 makes the host pipeline's row chunks odd multiples of 128
+    # (4224 rows), so pair tiles start inside a 256-row period and run into
+    # the next chunk's rows, which they must not store
+    prob = W.mnist_laplace(N=33000, M=5000, P=512)
+    import torch
+
+    with QSPlan(prob.d, prob.kernel, prob.P, prob.n_ft, prob.R, prob.kparam, dirs=prob.xi, proj="bf16x3",
+                max_n=prob.N, max_m=prob.M) as plan:
+        plan.set_gemm(False)
+        single = plan.sum(torch.from_numpy(prob.x).cuda(), torch.from_numpy(prob.w).cuda(),
+                          torch.from_numpy(prob.y).cuda()).cpu().numpy().astype(np.float64)
+        plan.check()
+        plan.set_gemm(True)
+        pair = plan.sum(torch.from_numpy(prob.x).cuda(), torch.from_numpy(prob.w).cuda(),
+                        torch.from_numpy(prob.y).cuda()).cpu().numpy().astype(np.float64)
+        plan.check()
+        host = plan.sum_host(prob.x, prob.w, prob.y).astype(np.float64)
+    assert np.array_equal(host, pair)
+    norm = _norm(prob)
+    assert np.max(np.abs(pair - single)) / norm < 1e-6
+    ref = oracle.o1_problem(prob, y=prob.y[:200])
+    assert np.max(np.abs(pair[:200] - ref)) / norm < 1e-5
+
+
+def test_pair_gemm_refused_without_tensor_core_projection():
+    from paper_2410_01316_gb300 import QSError
+
+    prob = W.tiny(d=8, N=100, M=10, P=16, kernel="gauss", kparam=1.0, n_ft=64, seed=2)
+    with QSPlan(prob.d, "gauss", prob.P, 64, prob.R, 1.0, dirs=prob.xi, proj="fp32", max_n=100, max_m=10) as plan:
+        with pytest.raises(QSError) as ei:
+            plan.set_gemm(True)
+        assert ei.value.status == 6
+        assert not plan.gemm_pair()
