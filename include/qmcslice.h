@@ -176,9 +176,11 @@ qs_status qs_project(qs_plan plan, const float* x, int64_t N, float* u_out, int6
  * Same sum from HOST buffers: copies x, w, y into plan-owned device staging
  * buffers, computes the sum, copies s back into the host buffer and
  * synchronises `stream`.  The copies in run on a plan-owned copy stream in
- * row chunks (at most 8 per input, after the work already queued on
+ * row chunks (at most 8 for x and 2 for y, after the work already queued on
  * `stream`), and each chunk is projected on `stream` as soon as it has
- * landed, so the transfers overlap the projections and the spread.  With
+ * landed (each target chunk also interpolated), so the transfers overlap the
+ * projections, the spread and the interpolation; the result is the one
+ * qs_sum computes, bit for bit.  With
  * stage timing on (qs_set_timing) or N == 0 the copies run first, on
  * `stream`.  Pinned host memory gives the fastest copies; the host buffers
  * must stay unchanged until the call returns.  Returns the data-error status
@@ -215,9 +217,13 @@ qs_status qs_directions(qs_dirs kind, int d, int P, uint64_t seed, float* out_ho
  *   [2] weight bound + spread + FFT filter        [3] operand split of y
  *   [4] projection GEMM of y                       [5] interpolation
  *   [6] slice reduction
- * Stages the plan's form does not run report 0.  Enabling creates the events
- * (host-side driver objects, no device memory).  Do not enable while a stream
- * that the plan uses is being captured into a CUDA graph.
+ * Stages the plan's form does not run report 0.  In the tensor-core forms
+ * with d >= 256 stage [3] runs on a plan-owned side stream concurrently with stage [1]
+ * (qs_sum forks it after stage [0] and joins it before stage [4]) and
+ * reports its own duration, which is off the critical path.
+ * Enabling creates the events (host-side driver objects, no device memory).
+ * Do not enable while a stream that the plan uses is being captured into a
+ * CUDA graph.
  */
 qs_status qs_set_timing(qs_plan plan, int enable);
 qs_status qs_stage_times(qs_plan plan, float* ms, int n);
@@ -319,7 +325,9 @@ qs_status qs_plan_variants(qs_plan plan, unsigned int* available, int* current);
  * pair = 0 runs one CTA per SM on 128-point x 256-slice tiles; pair = 1 runs
  * clusters of two CTAs on SM pairs (tcgen05 cta_group::2) on 256-point x
  * 256-slice tiles, which halves the shared-memory reads of the directions per
- * SM.  qs_plan_create picks pair = 1 wherever such clusters can be resident.  Both give the same projections up to the order of the tensor cores'
+ * SM.  qs_plan_create picks pair = 1 for d >= 256 (where the GEMM is bound by
+ * the tensor pipe rather than by its stores of U) wherever such clusters can
+ * be resident.  Both give the same projections up to the order of the tensor cores'
  * internal FP32 sums.  QS_ERR_UNSUPPORTED for pair = 1 on other projection
  * forms or where two-CTA clusters of the kernel cannot be resident;
  * QS_ERR_ARG for other values.  qs_plan_gemm reports the form in use (0 / 1)

@@ -809,7 +809,7 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
     const int S = gridDim.y;
     const int p0 = (int)(((int64_t)g * L.P) / S);
     const int p1 = (int)(((int64_t)(g + 1) * L.P) / S);
-    const int64_t m0 = (int64_t)blockIdx.x * IT_THREADS * TPT;
+    const int64_t m0 = L.m_base + (int64_t)blockIdx.x * IT_THREADS * TPT;
     const int mask = G - 1;
 
     // windowed coefficient path: a_jk of tap_j(t) = sum_k a_jk t^k (t = 2 s;
@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
 #pragma unroll
     for (int i = 0; i < TPT; ++i) {
         const int64_t m = m0 + threadIdx.x + (int64_t)i * IT_THREADS;
-        live[i] = m < L.M;
+        live[i] = m < L.m_end;
         hi[i] = 0.0f;
         lo[i] = 0.0f;
         if (FUSED) {
@@ -1120,7 +1120,9 @@ cudaError_t launch_interp_w(const qs_launch& L, const float* y, bool fused, cuda
 {
     const int tpt = qs_interp_tpt(fused, L.d, L.G);
     const size_t smem = (size_t)2 * (L.G + ROW_PAD + (fused ? 0 : IT_THREADS * tpt)) * sizeof(float);
-    const unsigned gx = (unsigned)((L.M + (int64_t)IT_THREADS * tpt - 1) / ((int64_t)IT_THREADS * tpt));
+    const int64_t mt = L.m_end - L.m_base;
+    if (mt <= 0) return cudaSuccess;
+    const unsigned gx = (unsigned)((mt + (int64_t)IT_THREADS * tpt - 1) / ((int64_t)IT_THREADS * tpt));
     dim3 grid(gx, (unsigned)L.S);
     // the kernel also holds ~8.5 KB of static shared memory, so the opt-in is
     // needed below 48 KB of dynamic memory too; set it on every launch
@@ -1131,8 +1133,7 @@ cudaError_t launch_interp_w(const qs_launch& L, const float* y, bool fused, cuda
         if (e_ != cudaSuccess) return e_;                                                                  \
         k_<<<grid, IT_THREADS, smem, st>>>(L, y);                                                          \
     } while (0)
-    if (!fused && tpt == 8) QS_LAUNCH_INTERP(false, 1, 8);
-    else if (!fused) QS_LAUNCH_INTERP(false, 1, 4);
+    if (!fused) QS_LAUNCH_INTERP(false, 1, 8);
     else if (L.d <= 4) QS_LAUNCH_INTERP(true, 4, 2);
     else if (L.d <= 8) QS_LAUNCH_INTERP(true, 8, 2);
     else if (L.d <= 16) QS_LAUNCH_INTERP(true, 16, 1);

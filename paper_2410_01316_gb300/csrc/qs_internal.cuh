@@ -85,6 +85,7 @@ struct qs_window {
 struct qs_launch {
     int d, P, G, n_ft;
     int64_t N, M;
+    int64_t m_base, m_end;  // targets [m_base, m_end) of an interpolation launch (0, M by default)
     int64_t ldU;          // row stride (elements) of the P x ldU projection workspace
     float half_G;         // |u| must stay <= G/2 (the half period)
     const float* xi_s;    // P x d, directions scaled by G tau
@@ -142,11 +143,19 @@ struct qs_plan_s {
     void* d_xi_lo;        // P x ldk (BF16x3 only)
     void* d_xs_hi;        // max(max_n, max_m) x ldk staging of the points
     void* d_xs_lo;        // (BF16x3 only)
+    void* d_ys_hi;        // max_m x ldk staging of the targets (split while the sources' GEMM runs)
+    void* d_ys_lo;        // (BF16x3 only)
     void* d_sortws = nullptr;  // sorting-slicing workspace, allocated by the first qs_sum_sorted
     // CUtensorMap: points hi/lo (128-row boxes), directions hi/lo (256-row boxes),
     // directions hi/lo (128-row boxes, the SM-pair kernel)
     alignas(64) unsigned char tmaps[6][128];
+    alignas(64) unsigned char tmaps_y[6][128];  // the same with the targets' staging as A
     bool gemm_pair;       // projection GEMM on SM pairs (cta_group::2)
+    // qs_sum's fork: the targets' operand split runs on side_st during the sources' GEMM;
+    // sev = fork, join (no timing), split start, split end (timing, read by qs_stage_times)
+    cudaStream_t side_st;
+    cudaEvent_t sev[4];
+    bool split_y_overlapped;  // the last timed qs_sum split the targets on side_st
     // stage timing (qs_set_timing)
     int timing;
     int timed_calls;
@@ -224,11 +233,12 @@ __device__ __forceinline__ float qs_check_u(float u, float half_G, unsigned int*
 }
 
 // Targets per thread of the interpolation kernel (256 threads per CTA).
-// Unfused: 8 for grids up to 2048 cells (the per-slice staging and range work
-// spread over more targets), 4 for larger grids, whose rows would cut occupancy.
+// Unfused: 8 (the per-slice staging and range work spread over more targets;
+// measured faster than 4 at G = 2048 and G = 4096).
 __host__ __device__ inline int qs_interp_tpt(bool fused, int d, int G)
 {
-    return !fused ? (G <= 2048 ? 8 : 4) : (d <= 8 ? 2 : 1);
+    (void)G;
+    return !fused ? 8 : (d <= 8 ? 2 : 1);
 }
 
 // ---------------------------------------------------------------------------

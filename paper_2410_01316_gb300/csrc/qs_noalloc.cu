@@ -240,6 +240,8 @@ extern "C" qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_
     L.n_ft = D.n_ft;
     L.N = N;
     L.M = M;
+    L.m_base = 0;
+    L.m_end = M;
     L.ldU = 0;
     L.half_G = 0.5f * (float)G;
     L.xi_s = reinterpret_cast<const float*>(base + o_xi);

@@ -327,9 +327,12 @@ void free_plan(qs_plan p)
     for (int i = 0; i < 1 + 2 * QS_HOST_CHUNKS; ++i)
         if (p->hev[i]) cudaEventDestroy(p->hev[i]);
     if (p->copy_st) cudaStreamDestroy(p->copy_st);
+    for (int i = 0; i < 4; ++i)
+        if (p->sev[i]) cudaEventDestroy(p->sev[i]);
+    if (p->side_st) cudaStreamDestroy(p->side_st);
     void* bufs[] = {p->d_dirs, p->d_dirs_s, p->d_c, p->d_psihat, p->d_D, p->d_tw, p->d_U, p->d_H,
                     p->d_part, p->d_flag, p->d_wscale, p->d_x, p->d_w, p->d_y, p->d_s, p->d_xi_hi, p->d_xi_lo,
-                    p->d_xs_hi, p->d_xs_lo, p->d_Dd, p->d_H2, p->d_gpart, p->d_sortws};
+                    p->d_xs_hi, p->d_xs_lo, p->d_ys_hi, p->d_ys_lo, p->d_Dd, p->d_H2, p->d_gpart, p->d_sortws};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete p;
@@ -357,6 +360,8 @@ qs_launch make_launch(const qs_plan p, int64_t N, int64_t M, int64_t targets_per
     L.n_ft = p->desc.n_ft;
     L.N = N;
     L.M = M;
+    L.m_base = 0;
+    L.m_end = M;
     L.ldU = p->ldU;
     L.half_G = 0.5f * (float)p->G;
     L.xi_s = p->d_dirs_s;
@@ -380,27 +385,32 @@ qs_launch make_launch(const qs_plan p, int64_t N, int64_t M, int64_t targets_per
 }
 
 // Operand preparation of the tensor-core forms (BF16 hi/lo split or TF32
-// rounding of the points into the plan's staging); nothing for FP32.
-cudaError_t project_prep(const qs_plan p, const float* X, int64_t rows, cudaStream_t st)
+// rounding of the points into the plan's staging: the targets' own staging
+// when ystage, so that it can run while the sources' GEMM reads theirs);
+// nothing for FP32.
+cudaError_t project_prep(const qs_plan p, const float* X, int64_t rows, cudaStream_t st, bool ystage = false)
 {
     const int d = p->desc.d;
+    void* hi = ystage ? p->d_ys_hi : p->d_xs_hi;
+    void* lo = ystage ? p->d_ys_lo : p->d_xs_lo;
     switch (p->proj) {
-        case QS_PROJ_BF16X3: return qs_launch_split_bf16(X, rows, d, p->ldk, p->d_xs_hi, p->d_xs_lo, st);
-        case QS_PROJ_TF32: return qs_launch_round_tf32(X, rows, d, p->ldk, (float*)p->d_xs_hi, st);
+        case QS_PROJ_BF16X3: return qs_launch_split_bf16(X, rows, d, p->ldk, hi, lo, st);
+        case QS_PROJ_TF32: return qs_launch_round_tf32(X, rows, d, p->ldk, (float*)hi, st);
         default: return cudaSuccess;
     }
 }
 
 // The projection GEMM U = G tau X Xi^T (after project_prep for the tensor-core forms).
-cudaError_t project_gemm(const qs_plan p, const float* X, int64_t rows, cudaStream_t st)
+cudaError_t project_gemm(const qs_plan p, const float* X, int64_t rows, cudaStream_t st, bool ystage = false)
 {
     const int d = p->desc.d, P = p->desc.P;
+    const void* maps = ystage ? (const void*)p->tmaps_y : (const void*)p->tmaps;
     switch (p->proj) {
         case QS_PROJ_FP32: return qs_launch_project_fp32(X, rows, d, p->d_dirs_s, P, p->d_U, p->ldU, st);
         case QS_PROJ_BF16X3:
-            return qs_launch_project_tc(0, p->tmaps, 0, rows, d, P, p->d_U, p->ldU, p->d_flag, st, p->gemm_pair);
+            return qs_launch_project_tc(0, maps, 0, rows, d, P, p->d_U, p->ldU, p->d_flag, st, p->gemm_pair);
         case QS_PROJ_TF32:
-            return qs_launch_project_tc(1, p->tmaps, 0, rows, d, P, p->d_U, p->ldU, p->d_flag, st, p->gemm_pair);
+            return qs_launch_project_tc(1, maps, 0, rows, d, P, p->d_U, p->ldU, p->d_flag, st, p->gemm_pair);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -429,13 +439,13 @@ cudaError_t project_rows(const qs_plan p, const float* X, int64_t r0, int64_t ro
     }
 }
 
-// Rows per chunk of the qs_sum_host pipeline: at most QS_HOST_CHUNKS chunks,
-// a multiple of the GEMM's 128-row tile, at least 4096 rows.
-int64_t host_chunk_rows(int64_t n)
+// Rows per chunk of the qs_sum_host pipeline: at most `chunks` chunks, a
+// multiple of `unit` (a multiple of the GEMM's 128-row tile), at least 4096 rows.
+int64_t host_chunk_rows(int64_t n, int64_t unit = 128, int chunks = QS_HOST_CHUNKS)
 {
-    int64_t c = (n + QS_HOST_CHUNKS - 1) / QS_HOST_CHUNKS;
-    c = (c + 127) / 128 * 128;
-    return c < 4096 ? 4096 : c;
+    int64_t c = (n + chunks - 1) / chunks;
+    c = (c + unit - 1) / unit * unit;
+    return c < 4096 ? (4096 + unit - 1) / unit * unit : c;
 }
 
 // U = G tau X Xi^T for the plan's projection form.
@@ -679,6 +689,7 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
         QS_ALLOC(p->d_U, p->U_elems);
     }
     const int64_t stage_rows = maxnm > 0 ? maxnm : 1;
+    const int64_t ystage_rows = D.max_m > 0 ? D.max_m : 1;
     if (proj == QS_PROJ_BF16X3) {
         p->ldk = (d + 7) / 8 * 8;  // 16-byte row stride for TMA
         uint16_t *xh = nullptr, *xl = nullptr, *sh = nullptr, *sl = nullptr;
@@ -690,13 +701,20 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
         p->d_xs_hi = sh;
         QS_ALLOC(sl, (size_t)stage_rows * p->ldk);
         p->d_xs_lo = sl;
+        uint16_t *yh = nullptr, *yl = nullptr;
+        QS_ALLOC(yh, (size_t)ystage_rows * p->ldk);
+        p->d_ys_hi = yh;
+        QS_ALLOC(yl, (size_t)ystage_rows * p->ldk);
+        p->d_ys_lo = yl;
     } else if (proj == QS_PROJ_TF32) {
         p->ldk = (d + 3) / 4 * 4;
-        float *xh = nullptr, *sh = nullptr;
+        float *xh = nullptr, *sh = nullptr, *yh = nullptr;
         QS_ALLOC(xh, (size_t)P * p->ldk);
         p->d_xi_hi = xh;
         QS_ALLOC(sh, (size_t)stage_rows * p->ldk);
         p->d_xs_hi = sh;
+        QS_ALLOC(yh, (size_t)ystage_rows * p->ldk);
+        p->d_ys_hi = yh;
     }
     QS_ALLOC(p->d_x, (size_t)(D.max_n > 0 ? D.max_n : 1) * d);
     QS_ALLOC(p->d_w, (size_t)(D.max_n > 0 ? D.max_n : 1));
@@ -751,12 +769,22 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
             ok = qs_make_tmap(p->tmaps[1], p->d_xs_lo, eb, d, stage_rows, p->ldk, 128) &&
                  qs_make_tmap(p->tmaps[3], p->d_xi_lo, eb, d, P, p->ldk, 256) &&
                  qs_make_tmap(p->tmaps[5], p->d_xi_lo, eb, d, P, p->ldk, 128);
+        memcpy(p->tmaps_y, p->tmaps, sizeof(p->tmaps));
+        if (ok) ok = qs_make_tmap(p->tmaps_y[0], p->d_ys_hi, eb, d, ystage_rows, p->ldk, 128);
+        if (ok && proj == QS_PROJ_BF16X3) ok = qs_make_tmap(p->tmaps_y[1], p->d_ys_lo, eb, d, ystage_rows, p->ldk, 128);
         if (!ok) {
             free_plan(p);
             return fail(QS_ERR_CUDA, "qs_plan_create: cuTensorMapEncodeTiled failed");
         }
-        // the SM-pair GEMM wherever two-CTA clusters of it can be resident
-        p->gemm_pair = qs_tc_pair_available(proj == QS_PROJ_BF16X3 ? 0 : 1);
+        QS_CHECK(cudaStreamCreateWithFlags(&p->side_st, cudaStreamNonBlocking), "side stream");
+        for (int i = 0; i < 4; ++i)
+            QS_CHECK(cudaEventCreateWithFlags(&p->sev[i], i < 2 ? cudaEventDisableTiming : cudaEventDefault),
+                     "fork / join events");
+        // the SM-pair GEMM where the GEMM is tensor-bound (d >= 256: 6 d flop
+        // per 4 B of U written) and two-CTA clusters of it can be resident;
+        // below, the U stores bound both forms and the single-SM one is faster
+        // (d = 64: 0.80 against 0.93 ms for N = 2e5, P = 4096)
+        p->gemm_pair = d >= 256 && qs_tc_pair_available(proj == QS_PROJ_BF16X3 ? 0 : 1);
     }
     QS_CHECK(cudaDeviceSynchronize(), "coefficient kernel");
 #undef QS_CHECK
@@ -827,6 +855,22 @@ qs_status qs_sum(qs_plan p, const float* x, int64_t N, const float* w, const flo
         if (e != cudaSuccess) return cuda_fail(e, "qs_sum: operand split of x");
     }
     QS_MARK(1);
+    // tensor-core forms with d >= 256: the targets' operand split (HBM-bound)
+    // runs on the side stream, in its own staging, while the sources' GEMM
+    // runs (tensor-bound there: 6 d flop per 4 B of U written; below that the
+    // GEMM is bound by its U stores and the split would slow it); the main
+    // stream joins it before the targets' GEMM
+    const bool fork = p->side_st != nullptr && (p->proj == QS_PROJ_BF16X3 || p->proj == QS_PROJ_TF32) &&
+                      p->desc.d >= 256;
+    if (fork) {
+        e = cudaEventRecord(p->sev[0], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side_st, p->sev[0], 0);
+        if (e == cudaSuccess && tm) e = cudaEventRecord(p->sev[2], p->side_st);
+        if (e == cudaSuccess) e = project_prep(p, y, M, p->side_st, true);
+        if (e == cudaSuccess && tm) e = cudaEventRecord(p->sev[3], p->side_st);
+        if (e == cudaSuccess) e = cudaEventRecord(p->sev[1], p->side_st);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_sum: operand split of y");
+    }
     if (!fused) {
         e = project_gemm(p, x, N, st);
         if (e != cudaSuccess) return cuda_fail(e, "qs_sum: projection of x");
@@ -837,13 +881,16 @@ qs_status qs_sum(qs_plan p, const float* x, int64_t N, const float* w, const flo
     e = qs_launch_spread(L, p->W, x, w, fused, st);
     if (e != cudaSuccess) return cuda_fail(e, "qs_sum: spread");
     QS_MARK(3);
-    if (!fused) {
+    if (fork) {
+        e = cudaStreamWaitEvent(st, p->sev[1], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_sum: join");
+    } else if (!fused) {
         e = project_prep(p, y, M, st);
         if (e != cudaSuccess) return cuda_fail(e, "qs_sum: operand split of y");
     }
     QS_MARK(4);
     if (!fused) {
-        e = project_gemm(p, y, M, st);
+        e = project_gemm(p, y, M, st, fork);
         if (e != cudaSuccess) return cuda_fail(e, "qs_sum: projection of y");
     }
     QS_MARK(5);
@@ -854,7 +901,10 @@ qs_status qs_sum(qs_plan p, const float* x, int64_t N, const float* w, const flo
     if (e != cudaSuccess) return cuda_fail(e, "qs_sum: reduction");
     QS_MARK(7);
 #undef QS_MARK
-    if (tm) p->timed_calls++;
+    if (tm) {
+        p->timed_calls++;
+        p->split_y_overlapped = fork;
+    }
     return QS_OK;
 }
 
@@ -882,7 +932,10 @@ qs_status qs_stage_times(qs_plan p, float* ms, int n)
     if (e != cudaSuccess) return cuda_fail(e, "qs_stage_times: event");
     for (int i = 0; i < n && i < QS_NUM_STAGES; ++i) {
         float t = 0.0f;
-        e = cudaEventElapsedTime(&t, p->ev[i], p->ev[i + 1]);
+        if (i == 3 && p->split_y_overlapped)  // the side stream's split, run during the GEMM of x
+            e = cudaEventElapsedTime(&t, p->sev[2], p->sev[3]);
+        else
+            e = cudaEventElapsedTime(&t, p->ev[i], p->ev[i + 1]);
         if (e != cudaSuccess) return cuda_fail(e, "qs_stage_times: elapsed");
         ms[i] = t;
     }
@@ -1157,9 +1210,14 @@ qs_status qs_sum_host(qs_plan p, const float* xh, int64_t N, const float* wh, co
         if (rs != QS_OK) return rs;
     } else {
         // pipelined form: x, then y, arrive in row chunks on the plan's copy
-        // stream; each chunk's projection runs on `stream` as soon as the
-        // chunk has landed, so the transfer of x overlaps its GEMM and the
-        // transfer of y overlaps the spread and the GEMM of y
+        // stream; each chunk is projected on `stream` as soon as it has
+        // landed, and each y chunk also interpolated, so the transfer of x
+        // overlaps its GEMM and the transfer of y the spread and the GEMM
+        // and interpolation of the chunks before it.  x comes in up to
+        // QS_HOST_CHUNKS chunks, y in two: an interpolation launch needs
+        // whole waves of CTAs (the slice groups are fixed by M).  y chunks are
+        // whole interpolation CTAs (256 x targets per thread), so every CTA
+        // sees the targets it sees in qs_sum and the results are the same bits
         if (!p->copy_st) {
             e = cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking);
             for (int i = 0; e == cudaSuccess && i < 1 + 2 * QS_HOST_CHUNKS; ++i)
@@ -1170,7 +1228,7 @@ qs_status qs_sum_host(qs_plan p, const float* xh, int64_t N, const float* wh, co
         cudaEvent_t* ex = p->hev + 1;
         cudaEvent_t* ey = p->hev + 1 + QS_HOST_CHUNKS;
         const bool fused = p->proj == QS_PROJ_FP32_FUSED;
-        const int64_t cx = host_chunk_rows(N), cy = host_chunk_rows(M);
+        const int64_t cx = host_chunk_rows(N), cy = host_chunk_rows(M, 256 * qs_interp_tpt(fused, d, p->G), 2);
         const int nx = (int)((N + cx - 1) / cx), ny = (int)((M + cy - 1) / cy);
         // the copies wait for the work already queued on `stream` (it may read the staging buffers)
         e = cudaEventRecord(p->hev[0], st);
@@ -1198,16 +1256,20 @@ qs_status qs_sum_host(qs_plan p, const float* xh, int64_t N, const float* wh, co
         e = qs_launch_weight_scale(L, wh ? p->d_w : nullptr, st);
         if (e == cudaSuccess) e = qs_launch_spread(L, p->W, p->d_x, wh ? p->d_w : nullptr, fused, st);
         if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: spread");
-        if (fused) e = cudaStreamWaitEvent(st, ey[ny - 1], 0);
-        for (int i = 0; !fused && e == cudaSuccess && i < ny; ++i) {
+        for (int i = 0; e == cudaSuccess && i < ny; ++i) {
             const int64_t r0 = i * cy, r = (M - r0 < cy ? M - r0 : cy);
             e = cudaStreamWaitEvent(st, ey[i], 0);
-            if (e == cudaSuccess) e = project_rows(p, p->d_y, r0, r, st);
+            if (e == cudaSuccess && !fused) e = project_rows(p, p->d_y, r0, r, st);
+            if (e == cudaSuccess) {
+                qs_launch Li = L;
+                Li.m_base = r0;
+                Li.m_end = r0 + r;
+                e = qs_launch_interp(Li, p->W, p->d_y, fused, st);
+            }
         }
-        if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: projection of y");
-        e = qs_launch_interp(L, p->W, p->d_y, fused, st);
-        if (e == cudaSuccess) e = qs_launch_reduce(L, p->d_s, st);
-        if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: interpolation");
+        if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: projection and interpolation of y");
+        e = qs_launch_reduce(L, p->d_s, st);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: reduction");
     }
     e = cudaMemcpyAsync(sh, p->d_s, (size_t)M * sizeof(float), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(e, "qs_sum_host: copy out");
