@@ -1214,8 +1214,9 @@ qs_status qs_sum_host(qs_plan p, const float* xh, int64_t N, const float* wh, co
         // landed, and each y chunk also interpolated, so the transfer of x
         // overlaps its GEMM and the transfer of y the spread and the GEMM
         // and interpolation of the chunks before it.  x comes in up to
-        // QS_HOST_CHUNKS chunks, y in two: an interpolation launch needs
-        // whole waves of CTAs (the slice groups are fixed by M).  y chunks are
+        // QS_HOST_CHUNKS chunks, y in QS_HOST_Y_CHUNKS: the slice groups are
+        // fixed by M, so an interpolation launch over a smaller chunk has
+        // fewer CTAs and wastes part of its waves.  y chunks are
         // whole interpolation CTAs (256 x targets per thread), so every CTA
         // sees the targets it sees in qs_sum and the results are the same bits
         if (!p->copy_st) {
@@ -1228,7 +1229,8 @@ qs_status qs_sum_host(qs_plan p, const float* xh, int64_t N, const float* wh, co
         cudaEvent_t* ex = p->hev + 1;
         cudaEvent_t* ey = p->hev + 1 + QS_HOST_CHUNKS;
         const bool fused = p->proj == QS_PROJ_FP32_FUSED;
-        const int64_t cx = host_chunk_rows(N), cy = host_chunk_rows(M, 256 * qs_interp_tpt(fused, d, p->G), 2);
+        const int64_t cx = host_chunk_rows(N),
+                      cy = host_chunk_rows(M, 256 * qs_interp_tpt(fused, d, p->G), QS_HOST_Y_CHUNKS);
         const int nx = (int)((N + cx - 1) / cx), ny = (int)((M + cy - 1) / cy);
         // the copies wait for the work already queued on `stream` (it may read the staging buffers)
         e = cudaEventRecord(p->hev[0], st);
