@@ -131,3 +131,15 @@ def test_plan_create_without_device_fails_cleanly(lib):
     desc.n_ft, desc.window, desc.radius, desc.max_n, desc.max_m = 128, 8, 2.0, 10, 10
     assert lib.qs_plan_create(ctypes.byref(h), ctypes.byref(desc)) == 5  # QS_ERR_CUDA
     assert not h.value
+
+
+def test_plan_level_setters_reject_null_plans(lib):
+    # QS_ERR_ARG (1) before any device work
+    v = ctypes.c_int(-1)
+    assert lib.qs_plan_set_gemm(None, 1) == 1
+    assert lib.qs_plan_set_gemm(None, 0) == 1
+    assert lib.qs_plan_gemm(None, ctypes.byref(v), None) == 1
+    assert lib.qs_plan_set_variant(None, 0) == 1
+    assert lib.qs_plan_variants(None, None, None) == 1
+    assert lib.qs_sum_host(None, None, 0, None, None, 0, None, None) == 1
+    assert "NULL" in lib.qs_last_error().decode()
