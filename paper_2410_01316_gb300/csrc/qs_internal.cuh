@@ -264,8 +264,11 @@ cudaError_t qs_launch_interp_grad(const qs_launch& L, int W, const float* y, con
 cudaError_t qs_launch_reduce_grad(const float* part, int S, int64_t M, int d, float scale, const float* fac,
                                   float* out, cudaStream_t st);
 bool qs_make_tmap(void* map_out, const void* base, int elem_bytes, int d, int64_t rows, int ldk, int box_rows);
-cudaError_t qs_launch_split_bf16(const float* X, int64_t rows, int d, int ldk, void* hi, void* lo, cudaStream_t st);
-cudaError_t qs_launch_round_tf32(const float* X, int64_t rows, int d, int ldk, float* out, cudaStream_t st);
+// max_blocks > 0 caps the grid (a split running beside another kernel).
+cudaError_t qs_launch_split_bf16(const float* X, int64_t rows, int d, int ldk, void* hi, void* lo, cudaStream_t st,
+                                 int max_blocks = 0);
+cudaError_t qs_launch_round_tf32(const float* X, int64_t rows, int d, int ldk, float* out, cudaStream_t st,
+                                 int max_blocks = 0);
 // Rows [n_base, n_base + N) of the staged operands into columns [n_base, n_base + N) of U;
 // n_base a multiple of 128.
 // pair: the SM-pair (cta_group::2) kernel, which needs maps 4 / 5 and qs_tc_pair_available.

@@ -393,9 +393,13 @@ cudaError_t project_prep(const qs_plan p, const float* X, int64_t rows, cudaStre
     const int d = p->desc.d;
     void* hi = ystage ? p->d_ys_hi : p->d_xs_hi;
     void* lo = ystage ? p->d_ys_lo : p->d_xs_lo;
+    // the targets' split runs beside the sources' GEMM: two blocks per SM
+    // leave the GEMM's epilogue warps their issue slots and still move the
+    // operands well within the GEMM's duration
+    const int cap = ystage ? 2 * p->sm_count : 0;
     switch (p->proj) {
-        case QS_PROJ_BF16X3: return qs_launch_split_bf16(X, rows, d, p->ldk, hi, lo, st);
-        case QS_PROJ_TF32: return qs_launch_round_tf32(X, rows, d, p->ldk, (float*)hi, st);
+        case QS_PROJ_BF16X3: return qs_launch_split_bf16(X, rows, d, p->ldk, hi, lo, st, cap);
+        case QS_PROJ_TF32: return qs_launch_round_tf32(X, rows, d, p->ldk, (float*)hi, st, cap);
         default: return cudaSuccess;
     }
 }

@@ -783,12 +783,14 @@ bool qs_make_tmap(void* map_out, const void* base, int elem_bytes, int d, int64_
     return r == CUDA_SUCCESS;
 }
 
-cudaError_t qs_launch_split_bf16(const float* X, int64_t rows, int d, int ldk, void* hi, void* lo, cudaStream_t st)
+cudaError_t qs_launch_split_bf16(const float* X, int64_t rows, int d, int ldk, void* hi, void* lo, cudaStream_t st,
+                                 int max_blocks)
 {
     if (rows <= 0) return cudaSuccess;
     const int64_t total = rows * (int64_t)(ldk / 4);
     int64_t blocks = (total + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
+    if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
     const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     if (vec)
         split_bf16_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(X, rows, d, ldk, (__nv_bfloat16*)hi,
@@ -799,12 +801,14 @@ cudaError_t qs_launch_split_bf16(const float* X, int64_t rows, int d, int ldk, v
     return cudaGetLastError();
 }
 
-cudaError_t qs_launch_round_tf32(const float* X, int64_t rows, int d, int ldk, float* out, cudaStream_t st)
+cudaError_t qs_launch_round_tf32(const float* X, int64_t rows, int d, int ldk, float* out, cudaStream_t st,
+                                 int max_blocks)
 {
     if (rows <= 0) return cudaSuccess;
     const int64_t total = rows * (int64_t)ldk;
     int64_t blocks = (total + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
+    if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
     round_tf32_kernel<<<(unsigned)blocks, 256, 0, st>>>(X, rows, d, ldk, out);
     return cudaGetLastError();
 }
