@@ -393,7 +393,11 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
 // its own 128 points, drained to U by its eight epilogue warps, which arrive
 // on the leader's tempty barriers.  One warp of each CTA allocates and frees
 // the pair's tensor memory together.  Waits on barriers are bounded as in the
-// single-SM form; both CTAs always reach the closing cluster barrier.
+// single-SM form; both CTAs always reach the closing cluster barrier.  On the
+// normal path every copy of the odd CTA has completed on the leader's full
+// barriers before the leader's MMA loop ends; only after a timeout (flagged)
+// can copies the odd CTA issued past the leader's last stage still be in
+// flight when the pair exits.
 // ---------------------------------------------------------------------------
 template <int KIND>
 struct PairCfg;
