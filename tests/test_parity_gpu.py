@@ -276,3 +276,15 @@ def test_spread_variants_are_bitwise_identical(case, proj, window):
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
     assert _err(outs[0].astype(np.float64), _oracle(prob), prob) < TOL_FP32
+
+
+@pytest.mark.parametrize("proj", ["fp32", "fp32_fused"])
+def test_moment_spread_with_one_dominant_weight(proj):
+    # one weight near sum|w| puts that source's fixed-point moments near 2^30
+    # (the scale is 2^30 / sum|w|) while the others' are tiny
+    prob = W.tiny(d=3, N=6000, M=700, P=48, kernel="laplace", kparam=1.0, n_ft=256, seed=31)
+    prob.w[1234] = 50.0 * float(np.abs(prob.w).sum())
+    s, _ = _gpu_sum(prob, proj)
+    assert _err(s, _oracle(prob), prob) < TOL_FP32
+    again, _ = _gpu_sum(prob, proj)
+    assert np.array_equal(s, again)
