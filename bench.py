@@ -317,7 +317,8 @@ def run_ours(args, rank, world, local_rank):
                        "device_status": int(status)},
             "roofline": roof,
             "stage_rooflines": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()
-                                    if kk in ("bound", "achieved", "peak", "unit", "frac", "ms")}
+                                    if kk in ("bound", "achieved", "peak", "unit", "frac", "ms", "hbm_achieved_gbs",
+                                              "hbm_frac")}
                                 for k, v in stage_roofs.items()},
             "clocks": clocks,
             "e2e": {"value": ps_step * args.steps * world / e2e_t / 1e9, "unit": UNIT,
@@ -765,17 +766,30 @@ def stage_rooflines(prob, plan, stages, clocks, peaks, peak_src, sm_count):
         by = rows * d * 8.0  # read FP32, write BF16 hi + lo (or TF32)
         add(name, "hbm", by / t / 1e9, peaks["hbm_gbs"], "GB/s", f"8 B per coordinate = {by:.3e} B",
             f"hbm_gbs ({peak_src})")
+    unfused = plan.proj != "fp32_fused"
+
+    def hbm(name, by, what):
+        # the same stage against HBM: its algorithmic byte stream
+        t_ = stages[name] / 1e3
+        out[name].update({"hbm_bytes": by, "hbm_algorithmic": what, "hbm_achieved_gbs": by / t_ / 1e9,
+                          "hbm_frac": by / t_ / 1e9 / peaks["hbm_gbs"]})
+
     t = stages.get("spread_filter", 0.0) / 1e3
     if t > 0:
         ops = float(N) * P * W
         add("spread_filter", "alu", ops / t / 1e9, smem_lanes / 1e9, "Gop/s",
             f"N P W = {ops:.3e} shared-memory atomic adds (grid accumulation)",
             f"shared-memory pipe: 32 lanes x {sm_count} SMs x {mhz:.0f} MHz")
+        if unfused:
+            hbm("spread_filter", 4.0 * N * P + 4.0 * N + 4.0 * P * G,
+                "4 N P (U) + 4 N (w) read, 4 P G (filtered rows) written")
     t = stages.get("interp", 0.0) / 1e3
     if t > 0:
         ops = float(M) * P * W
         add("interp", "alu", ops / t / 1e9, smem_lanes / 1e9, "Gop/s",
             f"M P W = {ops:.3e} shared-memory tap reads", f"shared-memory pipe: 32 lanes x {sm_count} SMs x {mhz:.0f} MHz")
+        if unfused:
+            hbm("interp", 4.0 * M * P + 4.0 * P * G, "4 M P (U) + 4 P G (filtered rows) read")
     return out
 
 
