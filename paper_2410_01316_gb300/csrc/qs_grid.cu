@@ -778,9 +778,9 @@ __global__ void deriv_table_kernel(const double* __restrict__ c, const double* _
 
 // ---------------------------------------------------------------------------
 // Interpolation + per-group compensated slice sums.
-// grid: (ceil(M / (256 TPT)), S); CTA (bx, g) handles the targets
-// bx*256*TPT + i*256 + tid (i < TPT) and the slices [g P / S, (g+1) P / S) in
-// increasing order.  The filtered row of each slice is staged in shared
+// grid: (ceil((m_end - m_base) / (256 TPT)), S); CTA (bx, g) handles the
+// targets m_base + bx*256*TPT + i*256 + tid (i < TPT) below m_end and the
+// slices [g P / S, (g+1) P / S) in increasing order.  The filtered row of each slice is staged in shared
 // memory (double-buffered cp.async) with its first cells repeated after the
 // end, so the W taps of a target are read without wrapping.
 // ---------------------------------------------------------------------------
@@ -792,7 +792,10 @@ __global__ void deriv_table_kernel(const double* __restrict__ c, const double* _
 // target takes its W taps from the row, and the CTA stops looking for
 // narrow ranges in its remaining slices.  Both evaluate the same polynomial
 // sum_j h[l0 + j] tap_j, rounded differently; which one a target takes
-// depends only on the data, so results are reproducible.
+// depends only on the data and the CTA's targets, so results are
+// reproducible.  With TPT even, targets go in pairs through packed FP32x2
+// arithmetic (each lane rounding as the scalar form).  The block's bin range
+// per slice comes from one shared atomic min / max per warp.
 constexpr int QWIN = 256;
 
 template <int W, bool FUSED, int DMAX, int TPT>

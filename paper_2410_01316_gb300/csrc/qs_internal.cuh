@@ -142,7 +142,7 @@ struct qs_plan_s {
     int ldk;              // row stride (elements) of the operand copies
     void* d_xi_hi;        // P x ldk
     void* d_xi_lo;        // P x ldk (BF16x3 only)
-    void* d_xs_hi;        // max(max_n, max_m) x ldk staging of the points
+    void* d_xs_hi;        // max(max_n, max_m) x ldk staging of the points (the sources, qs_project, host chunks)
     void* d_xs_lo;        // (BF16x3 only)
     void* d_ys_hi;        // max_m x ldk staging of the targets (split while the sources' GEMM runs)
     void* d_ys_lo;        // (BF16x3 only)
