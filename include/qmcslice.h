@@ -321,7 +321,8 @@ qs_status qs_plan_set_variant(qs_plan plan, int spread_variant);
 qs_status qs_plan_variants(qs_plan plan, unsigned int* available, int* current);
 
 /*
- * Projection GEMM form of a tensor-core plan (QS_PROJ_BF16X3 / QS_PROJ_TF32):
+ * Projection GEMM form of a tensor-core plan (QS_PROJ_BF16X3 / QS_PROJ_TF32),
+ * i.e. how the projections <x_n, xi_p> of Sec. 2.1 eq. kernel_sum_sliced are computed:
  * pair = 0 runs one CTA per SM on 128-point x 256-slice tiles; pair = 1 runs
  * clusters of two CTAs on SM pairs (tcgen05 cta_group::2) on 256-point x
  * 256-slice tiles, which halves the shared-memory reads of the directions per
