@@ -20,6 +20,9 @@ used instead:
 * ``gauss64_negdist`` d=64, N=M=200000, x,y ~ N(0,I), w ~ N(0,1), negative
                     distance kernel, P=4096 Sobol directions, N_ft=2048.
 * ``mmd_flow16``    d=16, N=M=100000 MMD-flow problem (App. H, MMD flows).
+* ``batch256_problems`` 256 Gauss problems of uneven N, M, d and N_ft.
+* ``gpu_compare30`` d=30, N=M=960000 PCA-shaped data summed against itself
+                    (App. H, "GPU Comparison").
 
 Direction designs (Sec. 4.1 "QMC Sequences"): iid uniform, Sobol mapped through
 the normal inverse CDF and normalised, orthogonal (first P columns of
@@ -254,3 +257,70 @@ def mnist_matern(N: int = 60000, M: int = 60000, P: int = 2048, n_ft: int = 512,
     med = base.meta["median"]
     return Problem(f"mnist_matern{int(2 * nu)}", d, "matern", med, P, n_ft, base.x, base.w, base.y, base.xi,
                    base.R, meta={"median": med}, kparam2=nu)
+
+
+def repeat_directions(xi: np.ndarray, P: int, seed: int) -> np.ndarray:
+    """A P x d direction array in which each of the U = len(xi) given rows
+    appears exactly P / U times, in a seeded random order.
+
+    The sliced sum averages over slices, so with equal multiplicities
+    (1/P) sum_p t(xi_{pi(p)}) = (1/U) sum_j t(xi_j) exactly: a full-size run
+    over P slices can be checked against a reference computed on the U
+    distinct directions only.  The random order makes a slice-indexing error
+    (a grid spread with one direction and read back with another) change the
+    result."""
+    U = xi.shape[0]
+    if P % U:
+        raise ValueError(f"P = {P} is not a multiple of the {U} distinct directions")
+    order = np.random.default_rng(seed).permutation(np.repeat(np.arange(U), P // U))
+    return np.ascontiguousarray(xi[order])
+
+
+def batch256_problems(n: int = 256, seed: int = SEED_BASE + 3) -> list:
+    """The batched workload: n Gauss problems, N, M log-uniform in [1e3, 1e5],
+    d in {3, 16, 64}, N_ft in {256, 512, 1024}, P = 256 (spherical Fibonacci
+    for d = 3, else orthogonal), sigma by the median rule (Sec. 4.1)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        N = int(np.exp(rng.uniform(np.log(1e3), np.log(1e5))))
+        M = int(np.exp(rng.uniform(np.log(1e3), np.log(1e5))))
+        d = int(rng.choice([3, 16, 64]))
+        n_ft = int(rng.choice([256, 512, 1024]))
+        x = gaussian(rng, N, d)
+        y = gaussian(rng, M, d)
+        w = rng.standard_normal(N).astype(np.float32)
+        sigma = median_pair_distance(x, y, 1000, seed + 7 * i)
+        xi = directions_fibonacci(256) if d == 3 else directions_orthogonal(rng, 256, d)
+        out.append(Problem(f"batch{i}", d, "gauss", sigma, 256, n_ft, x, w, y, xi, radius(x, y)))
+    return out
+
+
+def pca_like(rng: np.random.Generator, n: int, d: int, decay: float = 0.5) -> np.ndarray:
+    """Stand-in for PCA-reduced image data: independent coordinates
+    N(0, j^(-2 decay)), j = 1..d (principal components of decaying variance)."""
+    sd = np.arange(1, d + 1, dtype=np.float64) ** (-decay)
+    return (rng.standard_normal((n, d)) * sd).astype(np.float32)
+
+
+# N_ft per kernel as in the paper's experiments (App. C Step 2: 128 Gauss, 512
+# Matern, 1024 Laplace); the negative distance takes the Laplace value
+GPU_COMPARE_NFT = {"gauss": 128, "laplace": 1024, "matern": 512, "negdist": 1024}
+
+
+def gpu_compare30(kernel: str = "laplace", N: int = 960000, P: int = 5120, d: int = 30,
+                  seed: int = SEED_BASE + 6) -> Problem:
+    """The GPU-comparison shape (App. H, "GPU Comparison"): d = 30, N = M = 960000,
+    the data set summed against itself (y = x) with unit weights, kernel
+    parameters by the median rule (Sec. 4.1), P = 5120 (the largest of the
+    paper's P = 10 2^k), N_ft per kernel as above (Matern nu = 3/2).  The
+    directions returned are the seeded orthogonal start; the paper's distance
+    QMC design is formed from it by the library (QS_DIR_DISTANCE)."""
+    rng = np.random.default_rng(seed)
+    x = pca_like(rng, N, d)
+    w = np.ones(N, dtype=np.float32)
+    med = median_pair_distance(x, x, 1000, seed + 1000)
+    kparam = {"gauss": med, "laplace": 1.0 / med, "matern": med, "negdist": 0.0}[kernel]
+    xi = directions_orthogonal(rng, P, d)
+    return Problem(f"gpu_compare30_{kernel}", d, kernel, kparam, P, GPU_COMPARE_NFT[kernel], x, w, x, xi,
+                   radius(x, x), meta={"median": med}, kparam2=1.5 if kernel == "matern" else 0.0)

@@ -1,7 +1,15 @@
 """Sorting slicing for the negative distance kernel on the GPU (qs_sum_sorted):
 the exact sliced sum (Sec. 2.1 eq. kernel_sum_sliced with f(t) = -c_d |t|) against
-the oracle's closed-form sliced sum O3 on the plan's own directions, within
-1e-5 of sum|w| R (the inputs and projections are FP32; the 1D sums are exact)."""
+the oracle's closed-form sliced sum O3 on the plan's own directions, relative to
+sum|w| R.
+
+The 1D sums are exact (FP64 prefix sums over a stable sort); what remains is
+the FP32 rounding of the projections (sort keys) and of each slice's value,
+which averages out over sources and slices: the error falls like
+2^-24 c_d / sqrt(N P).  Measured on GB300: ~2e-9 for the small random cases
+(N ~ 1e3, P ~ 50), 1.2e-10 for the large one (N = 6e4, P = 96), 4e-8 with unit
+weights (no cancellation between sources, so the slice values are N R large);
+the tolerances sit a few times above those."""
 import numpy as np
 import pytest
 
@@ -11,7 +19,9 @@ from paper_2410_01316_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-5
+TOL = 1e-8          # random weights, small N and P
+TOL_UNIT = 2e-7     # unit weights
+TOL_LARGE = 1e-9    # N = 6e4, P = 96
 
 
 def _cuda(a):
@@ -35,7 +45,9 @@ def test_sorted_sum_matches_exact_sliced_sum(d, N, M, P):
     prob = W.tiny(d=d, N=N, M=M, P=P, kernel="negdist", kparam=0.0, n_ft=256, seed=90 + d)
     s, xi = _sorted_sum(prob)
     ref = oracle.o3_sliced("negdist", 0.0, prob.x, prob.w, prob.y, xi)
-    assert np.max(np.abs(s - ref)) / (np.abs(prob.w).sum() * prob.R) < TOL
+    err = np.max(np.abs(s - ref)) / (np.abs(prob.w).sum() * prob.R)
+    print(f"sorted sum d={d} N={N} M={M} P={P}: error vs exact sliced sum {err:.3e}")
+    assert err < TOL
 
 
 def test_sorted_sum_unit_weights_duplicates_and_empty():
@@ -44,7 +56,9 @@ def test_sorted_sum_unit_weights_duplicates_and_empty():
     prob.y[:20] = prob.x[7]              # targets on top of them
     s, xi = _sorted_sum(prob, use_w=False)
     ref = oracle.o3_sliced("negdist", 0.0, prob.x, None, prob.y, xi)
-    assert np.max(np.abs(s - ref)) / (prob.N * prob.R) < TOL
+    err = np.max(np.abs(s - ref)) / (prob.N * prob.R)
+    print(f"sorted sum with duplicates: error {err:.3e}")
+    assert err < TOL_UNIT
     import torch
 
     with QSPlan(prob.d, "negdist", prob.P, prob.n_ft, prob.R, dirs=prob.xi, proj="fp32", max_n=prob.N,
@@ -59,7 +73,9 @@ def test_sorted_sum_large_sampled_targets():
     s, xi = _sorted_sum(prob, proj="bf16x3")
     idx = np.random.default_rng(1).choice(prob.M, 64, replace=False)
     ref = oracle.o3_sliced("negdist", 0.0, prob.x, prob.w, prob.y[idx], xi)
-    assert np.max(np.abs(s[idx] - ref)) / (np.abs(prob.w).sum() * prob.R) < TOL
+    err = np.max(np.abs(s[idx] - ref)) / (np.abs(prob.w).sum() * prob.R)
+    print(f"sorted sum large: error {err:.3e}")
+    assert err < TOL_LARGE
 
 
 def test_sorted_sum_refuses_other_kernels():
@@ -80,5 +96,7 @@ def test_sorted_gradient_matches_exact_sliced_gradient(d, N, M, P):
         xi = plan.directions()
     ref = oracle.o3_grad_negdist(prob.x, prob.w, prob.y, v, xi)
     norm = oracle.riesz_const(d) * np.abs(prob.w).sum() * np.abs(v).max()
-    assert np.max(np.abs(g.cpu().numpy() - ref)) / norm < TOL
+    err = np.max(np.abs(g.cpu().numpy() - ref)) / norm
+    print(f"sorted gradient d={d}: error {err:.3e}")
+    assert err < TOL
     assert np.max(np.abs(ref)) / norm > 1e-3

@@ -9,8 +9,11 @@ rounding-error bound of each form, |u - u_ref| <= e_form * (G tau |X| |Xi|^T)[p,
           tensor core's internal accumulation, whose rounding is not specified
           bit-exactly and was measured at ~2^-17.5 for K = 5)
   TF32    e = 2^-10 + 4 (d + 2) 2^-24         (round-to-nearest TF32 of both operands)
-Full sums are checked against the FP64 oracle: 1e-5 relative for FP32, 1e-3
-for the reduced-precision projections (normalised by sum|w| max|F|).
+Full sums are checked against the FP64 oracle, normalised by sum|w| max|F|.
+The bars are 1e-5 (FP32) and 1e-3 (BF16x3); the tolerances below pin what
+the forms reach, a few times above the errors measured on GB300: BF16x3
+meets the FP32 bar with room to spare (full size d = 784: 7.1e-7), TF32 sits
+near it (7.7e-6) and FP32 well inside (4.3e-8).
 """
 import numpy as np
 import pytest
@@ -66,12 +69,14 @@ def _norm(prob):
     return float(np.abs(prob.w.astype(np.float64)).sum()) * (prob.R if prob.kernel == "negdist" else 1.0)
 
 
-@pytest.mark.parametrize("form,tol", [("bf16x3", 1e-3), ("tf32", 1e-3)])
+# measured: BF16x3 <= 4.7e-8, TF32 <= 3.4e-6 over these cases
+@pytest.mark.parametrize("form,tol", [("bf16x3", 5e-7), ("tf32", 2e-5)])
 @pytest.mark.parametrize("kernel,kp,d", [("laplace", 0.15, 784), ("negdist", 0.0, 64), ("gauss", 4.0, 16)])
 def test_tensor_core_sum_matches_oracle(form, tol, kernel, kp, d):
     prob = W.tiny(d=d, N=2000, M=600, P=300, kernel=kernel, kparam=kp, n_ft=512, seed=d + 3)
     ref = oracle.o1_problem(prob)
     err = np.max(np.abs(_sum(prob, form) - ref)) / _norm(prob)
+    print(f"tensor-core sum {form} {kernel} d={d}: error vs oracle {err:.3e}")
     assert err < tol
 
 
@@ -91,8 +96,9 @@ def test_mnist_laplace_full_size_all_forms():
     prob = W.mnist_laplace()
     idx = np.random.default_rng(78).choice(prob.M, 96, replace=False)
     ref = oracle.o1_problem(prob, y=prob.y[idx])
-    for form, tol in (("bf16x3", 1e-3), ("tf32", 1e-3), ("fp32", 1e-5)):
+    for form, tol in (("bf16x3", 2e-6), ("tf32", 2e-5), ("fp32", 2e-7)):
         err = np.max(np.abs(_sum(prob, form)[idx] - ref)) / _norm(prob)
+        print(f"mnist_laplace full size {form}: error vs oracle {err:.3e}")
         assert err < tol, (form, err)
 
 
