@@ -245,18 +245,25 @@ qs_status qs_stage_times(qs_plan plan, float* ms, int n);
  *       products inside the spread and interpolation; d <= 64).  QS_RIESZ and
  *       QS_TPS, whose coefficients need host quadrature, return
  *       QS_ERR_UNSUPPORTED.
- * dirs_dev: P x d FP32 directions in device memory (caller-owned).
+ * dirs_dev: P x d FP32 directions in device memory (caller-owned); a
+ *       non-finite entry makes the call return QS_ERR_NONFINITE.
  * x, w, y, s: as for qs_sum (device memory, w may be NULL).
  * Sizes: P * 2 n_ft grid values, the tables and the slice partial sums must
  * fit in the 16 MiB array (e.g. P = 1024 slices with n_ft = 1024 and M up to
  * about a million targets); larger problems return QS_ERR_UNSUPPORTED with a
  * message giving the bytes needed.  N and M are otherwise unbounded.
+ * Result: where the slice partial sums fit at the slice-group count qs_sum
+ * uses, the result is bit for bit that of qs_sum on a QS_PROJ_FP32_FUSED plan
+ * with the same description and directions (same tables, same kernels).
  * Synchronous: waits for `stream` and returns the data-error status that
- * qs_check would return.
- * The first call on a device looks up the array's device address; make that
- * first call before capturing the stream into a CUDA graph.  All calls share
- * the array: calls whose GPU work overlaps (other streams or threads on the
- * same device) race and must be serialised by the caller.
+ * qs_check would return.  The window tables are computed on the host once
+ * per (window, grid size) and kept in a small static cache.
+ * The first call on a device does a one-time set-up: it looks up the
+ * array's device address (and looks it up again after the device's context
+ * has been reset); make that first call before any stream capture begins.
+ * All calls share the array and it keeps the last call's contents: calls
+ * whose GPU work overlaps (other streams or threads on the same device) race
+ * and must be serialised by the caller.
  */
 qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_dev, const float* x, int64_t N,
                          const float* w, const float* y, int64_t M, float* s, void* stream);

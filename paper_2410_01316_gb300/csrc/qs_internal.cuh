@@ -243,6 +243,18 @@ __host__ __device__ inline int qs_interp_tpt(bool fused, int d, int G)
 }
 
 // ---------------------------------------------------------------------------
+// host tables (qs_tables.cu): fixed-size outputs, no heap
+// ---------------------------------------------------------------------------
+double qs_tau_rule(qs_kernel kernel, double kparam, double R);
+void qs_gauss_legendre(int n, double* x, double* w);
+void qs_fit_window(int W, double beta, qs_window* win);
+double qs_window_tap(const qs_window* win, int W, int j, double s);
+void qs_window_transform(const qs_window* win, int W, int K, int G, double* out);  // out[K + 1]
+void qs_twiddles(int G, float2* out);                                               // out[G / 2]
+// window shape parameter of the exponential of semicircle for sigma_os = 2
+inline double qs_window_beta(int W) { return 2.30 * W; }
+
+// ---------------------------------------------------------------------------
 // launchers (defined in the .cu files); return cudaSuccess or the launch error
 // ---------------------------------------------------------------------------
 int qs_sort_chunk(int P);

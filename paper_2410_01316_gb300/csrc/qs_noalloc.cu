@@ -20,6 +20,8 @@
 // cleared at the start).  Calls whose GPU work overlaps -- concurrent streams
 // or host threads on the same device -- race on the array and must be
 // serialised by the caller.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <math.h>
@@ -33,15 +35,13 @@
 
 #define QS_NOALLOC_SCRATCH_BYTES (16u << 20)
 #define QS_NOALLOC_MAX_DEVICES 64
+#define QS_NOALLOC_TABLE_CACHE 4
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[QS_NOALLOC_SCRATCH_BYTES];
 
 namespace {
 
-constexpr double kPi = 3.14159265358979323846264338327950288;
-
 std::mutex g_setup_mutex;
-void* g_scratch_ptr[QS_NOALLOC_MAX_DEVICES] = {nullptr};
 
 qs_status nfail(qs_status st, const char* fmt, ...)
 {
@@ -54,110 +54,112 @@ qs_status nfail(qs_status st, const char* fmt, ...)
     return st;
 }
 
-// Device address of the scratch array on the current device.  The array's
-// name in host code is only a stand-in; the address is looked up once per
-// device (first call on that device) and cached.
+// ---- device address of the scratch array -----------------------------------
+// In host code the array's name is only a stand-in, not a device address.
+// The address is looked up with cudaGetSymbolAddress once per device, with
+// that device current, and cached together with the identity of the device's
+// context: after a cudaDeviceReset the module is loaded again (possibly at
+// another address), the context identity changes and the lookup is repeated.
+struct ScratchEntry {
+    void* ptr = nullptr;
+    unsigned long long ctx_id = 0;
+    bool has_id = false;
+};
+ScratchEntry g_scratch[QS_NOALLOC_MAX_DEVICES];
+
+PFN_cuCtxGetCurrent_v4000 g_ctx_current = nullptr;
+PFN_cuCtxGetId_v12000 g_ctx_id = nullptr;
+bool g_ctx_fns_looked_up = false;
+
+// Identity of the calling thread's current context; false if it cannot be read.
+bool current_context_id(unsigned long long* id)
+{
+    if (!g_ctx_fns_looked_up) {
+        g_ctx_fns_looked_up = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+    }
+    if (!g_ctx_current || !g_ctx_id) return false;
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return g_ctx_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Caller holds g_setup_mutex; the device `dev` is current (the runtime has
+// made its primary context current by the time this runs).
 cudaError_t scratch_address(int dev, unsigned char** out)
 {
     if (dev < 0 || dev >= QS_NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    ScratchEntry& e = g_scratch[dev];
+    unsigned long long id = 0;
+    const bool has_id = current_context_id(&id);
+    if (!e.ptr || !has_id || !e.has_id || e.ctx_id != id) {
         void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = ptr;
+        const cudaError_t err = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (err != cudaSuccess) {
+            e.ptr = nullptr;
+            return err;
+        }
+        e.ptr = ptr;
+        e.has_id = has_id;
+        e.ctx_id = id;
     }
-    *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+    *out = static_cast<unsigned char*>(e.ptr);
     return cudaSuccess;
 }
 
-// ---- heap-free host tables (same arithmetic as plan creation) -------------
-double es(double v, int m, double beta)
+// ---- host tables, cached per (W, G) ------------------------------------------
+// The tap polynomials, the window transform (K + 1 = G/4 + 1 values) and the
+// twiddles depend only on the window width W and the grid size G.  They are
+// computed by the same host code as at plan creation (qs_tables.cu), so both
+// entry points use bitwise identical tables, and kept in a few static slots
+// (no heap) so repeated calls with the same sizes do not recompute them.
+struct TableEntry {
+    int W = 0, G = 0;
+    qs_window win;
+    double psihat[QS_MAX_G / 4 + 1];
+    float2 tw[QS_MAX_G / 2];
+};
+TableEntry g_tables[QS_NOALLOC_TABLE_CACHE];
+int g_tables_next = 0;
+
+// Caller holds g_setup_mutex.
+const TableEntry& tables_for(int W, int G)
 {
-    const double z = v / m;
-    if (fabs(z) >= 1.0) return 0.0;
-    return exp(beta * (sqrt(1.0 - z * z) - 1.0));
+    for (auto& t : g_tables)
+        if (t.W == W && t.G == G) return t;
+    TableEntry& t = g_tables[g_tables_next];
+    g_tables_next = (g_tables_next + 1) % QS_NOALLOC_TABLE_CACHE;
+    qs_fit_window(W, qs_window_beta(W), &t.win);
+    qs_window_transform(&t.win, W, G / 4, G, t.psihat);
+    qs_twiddles(G, t.tw);
+    t.W = W;
+    t.G = G;
+    return t;
 }
 
-void gl24(double* x, double* w)
-{
-    const int n = 24;
-    for (int i = 0; i < n; ++i) {
-        double t = cos(kPi * (i + 0.75) / (n + 0.5));
-        double dp = 1.0;
-        for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = t;
-            for (int j = 1; j < n; ++j) {
-                const double p2 = ((2.0 * j + 1.0) * t * p1 - j * p0) / (j + 1.0);
-                p0 = p1;
-                p1 = p2;
-            }
-            dp = n * (t * p1 - p0) / (t * t - 1.0);
-            const double dt = p1 / dp;
-            t -= dt;
-            if (fabs(dt) < 1e-16) break;
-        }
-        x[i] = t;
-        w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
-    }
-}
-
-void fit(int W, double beta, qs_window& win)
-{
-    const int m = W / 2;
-    const int n = qs_tap_degree(W) + 1;
-    double tm[QS_MAX_W + 2][QS_MAX_W + 2];
-    memset(&win, 0, sizeof(win));
-    for (int k = 0; k < n; ++k)
-        for (int i = 0; i < n; ++i) tm[k][i] = 0.0;
-    tm[0][0] = 1.0;
-    tm[1][1] = 2.0;
-    for (int k = 2; k < n; ++k)
-        for (int i = 0; i < n; ++i) {
-            double v = -tm[k - 2][i];
-            if (i > 0) v += 4.0 * tm[k - 1][i - 1];
-            tm[k][i] = v;
-        }
-    for (int j = 0; j < m; ++j) {
-        double cheb[QS_MAX_W + 2], fval[QS_MAX_W + 2], mono[QS_MAX_W + 2];
-        for (int i = 0; i < n; ++i) fval[i] = es(0.5 * cos(kPi * (i + 0.5) / n) + m - 0.5 - j, m, beta);
-        for (int k = 0; k < n; ++k) {
-            double acc = 0.0;
-            for (int i = 0; i < n; ++i) acc += fval[i] * cos(k * kPi * (i + 0.5) / n);
-            cheb[k] = (k == 0 ? 1.0 : 2.0) * acc / n;
-        }
-        for (int i = 0; i < n; ++i) mono[i] = 0.0;
-        for (int k = 0; k < n; ++k)
-            for (int i = 0; i < n; ++i) mono[i] += cheb[k] * tm[k][i];
-        for (int i = 0; i < n; ++i) {
-            if (i % 2 == 0) win.e[j][i / 2] = (float)mono[i];
-            else win.o[j][i / 2] = (float)mono[i];
-        }
-    }
-}
-
-double tap(const qs_window& win, int W, int j, double s)
-{
-    const int m = W / 2, T = qs_tap_terms(W);
-    const int jj = j < m ? j : W - 1 - j;
-    const double ss = j < m ? s : -s;
-    double e = 0.0, o = 0.0;
-    for (int i = T - 1; i >= 0; --i) {
-        e = e * ss * ss + (double)win.e[jj][i];
-        o = o * ss * ss + (double)win.o[jj][i];
-    }
-    return e + ss * o;
-}
-
-// Per-call host staging of the small tables (no heap): window transform
-// (K + 1 doubles) and twiddles (G/2 float2).  Serialised by g_setup_mutex.
-double g_psihat[QS_MAX_G / 4 + 1];
-float2 g_tw[QS_MAX_G / 2];
-
-__global__ void scale_dirs_kernel(const float* __restrict__ dirs, int64_t n, double scale, float* __restrict__ out)
+// Directions scaled by G tau, in the same FP64 product and FP32 rounding as at
+// plan creation; a non-finite direction entry sets the data-error flag.
+__global__ void scale_dirs_kernel(const float* __restrict__ dirs, int64_t n, double scale, float* __restrict__ out,
+                                  unsigned int* flag)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (float)(scale * (double)dirs[i]);
+    if (i < n) {
+        const float v = dirs[i];
+        if (!isfinite(v)) {
+            atomicOr(flag, QS_FLAG_NONFINITE);
+            out[i] = 0.0f;
+        } else {
+            out[i] = (float)(scale * (double)v);
+        }
+    }
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -194,9 +196,12 @@ extern "C" qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_
     if (M == 0) return QS_OK;
 
     const int G = 2 * D.n_ft, K = D.n_ft / 2, d = D.d, P = D.P;
-    // slice groups as in qs_sum, reduced only if the partial sums do not fit
+    // slice groups chosen as qs_sum chooses them for the fused form (targets
+    // per interpolation CTA from qs_interp_tpt), reduced only if the partial
+    // sums do not fit the scratch array
     const int S_max = P < 64 ? P : 64;
-    const int64_t blocks_m = (M + 255) / 256;
+    const int64_t tpc = 256 * (int64_t)qs_interp_tpt(true, d, G);
+    const int64_t blocks_m = (M + tpc - 1) / tpc;
     int64_t S = (1024 + blocks_m - 1) / blocks_m;
     if (S > S_max) S = S_max;
     if (S < 1) S = 1;
@@ -219,19 +224,8 @@ extern "C" qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return nfail(QS_ERR_CUDA, "qs_sum_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
-    unsigned char* base = nullptr;
-    e = scratch_address(dev, &base);
-    if (e != cudaSuccess)
-        return nfail(QS_ERR_CUDA, "qs_sum_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
     cudaStream_t st = (cudaStream_t)stream;
-
-    double tau;
-    switch (D.kernel) {
-        case QS_GAUSS: tau = fmin(0.3 / D.radius, 1.0 / (2.0 * 5.0 * D.kparam)); break;
-        case QS_LAPLACE: tau = fmin(0.1 / D.radius, 1.0 / (2.0 * 5.0 / D.kparam)); break;
-        case QS_MATERN: tau = fmin(0.2 / D.radius, 1.0 / (2.0 * 5.0 * D.kparam)); break;
-        default: tau = 1.0 / (2.0 * D.radius); break;
-    }
+    const double tau = qs_tau_rule(D.kernel, D.kparam, D.radius);
     qs_launch L;
     memset(&L, 0, sizeof(L));
     L.d = d;
@@ -244,50 +238,37 @@ extern "C" qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_
     L.m_end = M;
     L.ldU = 0;
     L.half_G = 0.5f * (float)G;
+    L.U = nullptr;
+    L.S = (int)S;
+    L.spread_variant = qs_spread_default(G, W);
+
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        e = scratch_address(dev, &base);
+        if (e != cudaSuccess)
+            return nfail(QS_ERR_CUDA, "qs_sum_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        const TableEntry& tb = tables_for(W, G);
+        L.win = tb.win;
+        // pageable source: each copy has been staged when the call returns, so
+        // the cache slot may be reused by a later call
+        e = cudaMemcpyAsync(base + o_psihat, tb.psihat, (size_t)(K + 1) * 8, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(base + o_tw, tb.tw, (size_t)(G / 2) * 8, cudaMemcpyHostToDevice, st);
+    }
+    if (e != cudaSuccess) return nfail(QS_ERR_CUDA, "qs_sum_noalloc: table upload: %s", cudaGetErrorString(e));
     L.xi_s = reinterpret_cast<const float*>(base + o_xi);
     L.D = reinterpret_cast<const float*>(base + o_D);
     L.tw = reinterpret_cast<const float2*>(base + o_tw);
     L.H = reinterpret_cast<float*>(base + o_H);
-    L.U = nullptr;
     L.part = reinterpret_cast<float*>(base + o_part);
-    L.S = (int)S;
-    L.spread_variant = qs_spread_default(G, W);
     L.flag = reinterpret_cast<unsigned int*>(base + o_flag);
     L.wscale = reinterpret_cast<float*>(base + o_wscale);
-
-    {
-        std::lock_guard<std::mutex> lock(g_setup_mutex);
-        fit(W, 2.30 * W, L.win);
-        double gx[24], gw[24];
-        gl24(gx, gw);
-        for (int k = 0; k <= K; ++k) {
-            const double nu = (double)k / G;
-            double acc = 0.0;
-            for (int j = 0; j < W; ++j) {
-                const double c = W / 2 - 0.5 - j;
-                for (int q = 0; q < 24; ++q) {
-                    const double sq = 0.5 * gx[q];
-                    acc += 0.5 * gw[q] * tap(L.win, W, j, sq) * cos(2.0 * kPi * nu * (sq + c));
-                }
-            }
-            g_psihat[k] = acc;
-        }
-        for (int t = 0; t < G / 2; ++t) {
-            const double ang = 2.0 * kPi * (double)t / (double)G;
-            g_tw[t] = make_float2((float)cos(ang), (float)(-sin(ang)));
-        }
-        // pageable source: each copy has been staged when the call returns, so
-        // the host tables may be rewritten by the next call
-        e = cudaMemcpyAsync(base + o_psihat, g_psihat, (size_t)(K + 1) * 8, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(base + o_tw, g_tw, (size_t)(G / 2) * 8, cudaMemcpyHostToDevice, st);
-    }
-    if (e != cudaSuccess) return nfail(QS_ERR_CUDA, "qs_sum_noalloc: table upload: %s", cudaGetErrorString(e));
     e = cudaMemsetAsync(base + o_flag, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return nfail(QS_ERR_CUDA, "qs_sum_noalloc: clear flag: %s", cudaGetErrorString(e));
     const int64_t nd = (int64_t)P * d;
     scale_dirs_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(dirs_dev, nd, (double)G * tau,
-                                                                     reinterpret_cast<float*>(base + o_xi));
+                                                                     reinterpret_cast<float*>(base + o_xi), L.flag);
     e = cudaGetLastError();
     if (e == cudaSuccess)
         e = qs_launch_coeffs((int)D.kernel, D.kparam, D.kparam2, d, tau, D.n_ft, G,

@@ -116,139 +116,6 @@ void haar_orthogonal(HostRng& rng, int d, std::vector<double>& q)
     }
 }
 
-// ---------------------------------------------------------------------------
-// window: exponential of semicircle on |v| < m, beta = 2.30 W for sigma_os = 2
-// ---------------------------------------------------------------------------
-double es_window(double v, int m, double beta)
-{
-    const double z = v / m;
-    if (fabs(z) >= 1.0) return 0.0;
-    return exp(beta * (sqrt(1.0 - z * z) - 1.0));
-}
-
-// Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on P_n.
-void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w)
-{
-    x.resize(n);
-    w.resize(n);
-    for (int i = 0; i < n; ++i) {
-        double t = cos(kPi * (i + 0.75) / (n + 0.5));
-        double dp = 1.0;
-        for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = t;
-            for (int j = 1; j < n; ++j) {
-                const double p2 = ((2.0 * j + 1.0) * t * p1 - j * p0) / (j + 1.0);
-                p0 = p1;
-                p1 = p2;
-            }
-            dp = n * (t * p1 - p0) / (t * t - 1.0);
-            const double dt = p1 / dp;
-            t -= dt;
-            if (fabs(dt) < 1e-16) break;
-        }
-        x[i] = t;
-        w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
-    }
-}
-
-// Fit the tap polynomials: Chebyshev interpolation of degree qs_tap_degree(W)
-// on s in [-1/2, 1/2] for each tap of the first half, conversion to
-// monomials in s, split into even and odd parts.
-void fit_window(int W, double beta, qs_window& win)
-{
-    const int m = W / 2;
-    const int deg = qs_tap_degree(W);
-    const int n = deg + 1;
-    memset(&win, 0, sizeof(win));
-    // T_k(2s) as monomials in s: tm[k][i]
-    std::vector<std::vector<double>> tm(n, std::vector<double>(n, 0.0));
-    tm[0][0] = 1.0;
-    if (n > 1) tm[1][1] = 2.0;
-    for (int k = 2; k < n; ++k) {
-        for (int i = 0; i < n; ++i) {
-            double v = -tm[k - 2][i];
-            if (i > 0) v += 4.0 * tm[k - 1][i - 1];  // 2 * (2s) * T_{k-1}
-            tm[k][i] = v;
-        }
-    }
-    for (int j = 0; j < m; ++j) {
-        std::vector<double> cheb(n, 0.0), fval(n);
-        for (int i = 0; i < n; ++i) {
-            const double th = kPi * (i + 0.5) / n;
-            fval[i] = es_window(0.5 * cos(th) + m - 0.5 - j, m, beta);
-        }
-        for (int k = 0; k < n; ++k) {
-            double acc = 0.0;
-            for (int i = 0; i < n; ++i) acc += fval[i] * cos(k * kPi * (i + 0.5) / n);
-            cheb[k] = (k == 0 ? 1.0 : 2.0) * acc / n;
-        }
-        std::vector<double> mono(n, 0.0);
-        for (int k = 0; k < n; ++k)
-            for (int i = 0; i < n; ++i) mono[i] += cheb[k] * tm[k][i];
-        for (int i = 0; i < n; ++i) {
-            if (i % 2 == 0) win.e[j][i / 2] = (float)mono[i];
-            else win.o[j][i / 2] = (float)mono[i];
-        }
-    }
-}
-
-// Evaluate the FP32 tap polynomials (in double) for offset s and tap j.
-double window_tap(const qs_window& win, int W, int j, double s)
-{
-    const int m = W / 2;
-    const int T = qs_tap_terms(W);
-    const int jj = j < m ? j : W - 1 - j;
-    const double ss = j < m ? s : -s;
-    double e = 0.0, o = 0.0;
-    for (int i = T - 1; i >= 0; --i) {
-        e = e * ss * ss + (double)win.e[jj][i];
-        o = o * ss * ss + (double)win.o[jj][i];
-    }
-    return e + ss * o;
-}
-
-// Fourier transform (grid units) of the window as the GPU applies it:
-// psi_eff(v) = p_j(v - (m - 1/2 - j)) on the j-th unit cell.  Even, so
-// psi^(nu) = sum_j int_{-1/2}^{1/2} p_j(s) cos(2 pi nu (s + m - 1/2 - j)) ds.
-void window_transform(const qs_window& win, int W, int K, int G, std::vector<double>& out)
-{
-    const int m = W / 2;
-    std::vector<double> gx, gw;
-    gauss_legendre(24, gx, gw);
-    std::vector<double> tap((size_t)W * gx.size());
-    for (int j = 0; j < W; ++j)
-        for (size_t q = 0; q < gx.size(); ++q) tap[(size_t)j * gx.size() + q] = window_tap(win, W, j, 0.5 * gx[q]);
-    out.assign(K + 1, 0.0);
-    for (int k = 0; k <= K; ++k) {
-        const double nu = (double)k / G;
-        double acc = 0.0;
-        for (int j = 0; j < W; ++j) {
-            const double c = m - 0.5 - j;
-            for (size_t q = 0; q < gx.size(); ++q) {
-                const double s = 0.5 * gx[q];
-                acc += 0.5 * gw[q] * tap[(size_t)j * gx.size() + q] * cos(2.0 * kPi * nu * (s + c));
-            }
-        }
-        out[k] = acc;
-    }
-}
-
-// Rescaling factor (App. C Step 1: T = 0.3 Gauss, 0.1 Laplace, 0.2 Matern,
-// g_max = 5 sigma, 5 / alpha, 5 beta; App. G for the kernels without a
-// classical Fourier transform: the half period T = R, tau = 1/(2R)).
-double tau_rule(qs_kernel kernel, double kparam, double R)
-{
-    switch (kernel) {
-        case QS_GAUSS: return fmin(0.3 / R, 1.0 / (2.0 * 5.0 * kparam));
-        case QS_LAPLACE: return fmin(0.1 / R, 1.0 / (2.0 * 5.0 / kparam));
-        case QS_MATERN: return fmin(0.2 / R, 1.0 / (2.0 * 5.0 * kparam));
-        case QS_NEGDIST:
-        case QS_RIESZ:
-        case QS_TPS: return 1.0 / (2.0 * R);
-    }
-    return -1.0;
-}
-
 // Fourier coefficients of the 1-periodic g(t) = f(|t| / tau), t in [-1/2, 1/2),
 // for the generalised Riesz kernel (f = -c_{d,q} |t|^q, c_{d,q} =
 // sqrt(pi) Gamma((d+q)/2) / (Gamma(d/2) Gamma((q+1)/2))) and the thin plate
@@ -279,12 +146,13 @@ void periodic_coeffs(qs_kernel kernel, double q, int d, double tau, int n_ft, st
         if (kernel == QS_RIESZ) return amp * pow(u, q);
         return u > 0.0 ? (double)d * u * u * log(u) + cd * u * u : 0.0;
     };
-    std::vector<double> gx, gw;
-    gauss_legendre(16, gx, gw);
+    constexpr int nq = 16;
+    double gx[nq], gw[nq];
+    qs_gauss_legendre(nq, gx, gw);
     std::vector<double> nodes, vals;
     auto panel = [&](double a, double b) {
         const double m = 0.5 * (a + b), hh = 0.5 * (b - a);
-        for (size_t i = 0; i < gx.size(); ++i) {
+        for (int i = 0; i < nq; ++i) {
             const double t = m + hh * gx[i];
             nodes.push_back(t);
             vals.push_back(2.0 * hh * gw[i] * g(t));
@@ -596,8 +464,8 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     p->W = W;
     p->G = 2 * D.n_ft;
     p->spread_variant = qs_spread_default(p->G, W);
-    p->beta = 2.30 * W;
-    p->tau = tau_rule(D.kernel, D.kparam, D.radius);
+    p->beta = qs_window_beta(W);
+    p->tau = qs_tau_rule(D.kernel, D.kparam, D.radius);
     p->S_max = D.P < 64 ? D.P : 64;
     const int64_t maxnm = D.max_n > D.max_m ? D.max_n : D.max_m;
     p->ldU = ((maxnm + 127) / 128) * 128;
@@ -641,14 +509,11 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     for (size_t i = 0; i < dirs.size(); ++i) dirs_s[i] = (float)(scale * (double)dirs[i]);
 
     // window tables
-    fit_window(W, p->beta, p->win);
-    std::vector<double> psihat;
-    window_transform(p->win, W, K, G, psihat);
+    qs_fit_window(W, p->beta, &p->win);
+    std::vector<double> psihat(K + 1);
+    qs_window_transform(&p->win, W, K, G, psihat.data());
     std::vector<float2> tw(G / 2);
-    for (int t = 0; t < G / 2; ++t) {
-        const double ang = 2.0 * kPi * (double)t / (double)G;
-        tw[t] = make_float2((float)cos(ang), (float)(-sin(ang)));
-    }
+    qs_twiddles(G, tw.data());
 
     // device buffers
 #define QS_ALLOC(ptr, n)                                                       \
