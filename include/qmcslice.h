@@ -72,9 +72,12 @@ typedef enum {
     QS_DIR_FIBONACCI = 1,  /* spherical Fibonacci points, d = 3 only */
     QS_DIR_ORTHOGONAL = 2, /* first P columns of ceil(P/d) Haar-orthogonal matrices */
     QS_DIR_IID = 3,        /* iid uniform on the sphere */
-    QS_DIR_DISTANCE = 4    /* distance QMC design: QS_DIR_ORTHOGONAL (seeded) refined by
+    QS_DIR_DISTANCE = 4,   /* distance QMC design: QS_DIR_ORTHOGONAL (seeded) refined by
                               qs_distance_design (300 steps, lr 0.05/sqrt(d)) at plan creation;
                               plans only (qs_directions refuses it: it needs the GPU) */
+    QS_DIR_SOBOL = 5       /* Sobol' points (qs_sobol_points, digitally shifted by `seed`; seed 0 =
+                              unshifted) mapped through the inverse normal CDF per coordinate and
+                              normalised; d <= 4096 */
 } qs_dirs;
 
 /* Precision / form of the projection step a = tau X Xi^T. */
@@ -203,10 +206,25 @@ const char* qs_last_error(void);
 
 /*
  * Host-only direction generator (no GPU needed): writes P x d unit rows into
- * out_host for QS_DIR_FIBONACCI (d = 3), QS_DIR_ORTHOGONAL or QS_DIR_IID
- * (Sec. 4.1).  Deterministic in `seed`.
+ * out_host for QS_DIR_FIBONACCI (d = 3), QS_DIR_ORTHOGONAL, QS_DIR_IID or
+ * QS_DIR_SOBOL (Sec. 4.1).  Deterministic in `seed`.
  */
 qs_status qs_directions(qs_dirs kind, int d, int P, uint64_t seed, float* out_host);
+
+/*
+ * The Sobol' sequence behind QS_DIR_SOBOL (Sec. 4.1, "QMC Sequences"): writes
+ * points i = 0 .. P-1 of a d-dimensional Sobol' sequence, u[i * d + j] =
+ * (x_ij + 1/2) / 2^32 in (0, 1), into the host array out_host (P x d doubles,
+ * caller-owned).  Coordinate 0 is the van der Corput sequence; coordinate
+ * j >= 1 uses the j-th primitive polynomial over GF(2) (ordered by degree,
+ * then coefficients) with 32-bit direction numbers; points in Gray-code
+ * (Antonov-Saleev) order.  The first 2^m points of
+ * every coordinate hold one point in each interval [k 2^-m, (k+1) 2^-m), and
+ * coordinates 0 and 1 form a (0, m, 2)-net.  seed != 0 applies a seeded
+ * random digital shift (XOR per coordinate), which keeps these properties.
+ * Errors: QS_ERR_ARG (NULL output, P < 1, d outside 1 .. 4096).
+ */
+qs_status qs_sobol_points(int d, int P, uint64_t seed, double* out_host);
 
 /*
  * Stage timing for benchmarks.  While enabled, qs_sum records a CUDA event on

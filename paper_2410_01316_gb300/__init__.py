@@ -18,7 +18,7 @@ import numpy as np
 from . import _lib
 from ._lib import QSError
 
-__all__ = ["QSPlan", "QSBatch", "QSError", "KernelSumFn", "directions", "kernel_sum", "version",
+__all__ = ["QSPlan", "QSBatch", "QSError", "KernelSumFn", "directions", "sobol_points", "kernel_sum", "version",
            "distance_design", "distance_energy"]
 
 
@@ -27,10 +27,18 @@ def version() -> str:
 
 
 def directions(kind: str, d: int, P: int, seed: int = 0) -> np.ndarray:
-    """Host-side direction design from the library (Fibonacci / orthogonal / iid)."""
+    """Host-side direction design from the library (Fibonacci / orthogonal / iid / Sobol)."""
     out = np.empty((P, d), dtype=np.float32)
     _lib.check(_lib.load().qs_directions(_lib.DIRS[kind], d, P, seed, out.ctypes.data_as(ctypes.c_void_p)),
                "qs_directions")
+    return out
+
+
+def sobol_points(d: int, P: int, seed: int = 0) -> np.ndarray:
+    """The library's Sobol' points in (0, 1)^d (P x d, float64) behind the "sobol" directions;
+    seed != 0 applies a random digital shift."""
+    out = np.empty((P, d), dtype=np.float64)
+    _lib.check(_lib.load().qs_sobol_points(d, P, seed, out.ctypes.data_as(ctypes.c_void_p)), "qs_sobol_points")
     return out
 
 

@@ -24,7 +24,7 @@ STATUS = {
     5: "QS_ERR_CUDA", 6: "QS_ERR_UNSUPPORTED", 7: "QS_ERR_TIMEOUT",
 }
 KERNELS = {"gauss": 0, "laplace": 1, "negdist": 2, "matern": 3, "riesz": 4, "tps": 5}
-DIRS = {"user": 0, "fibonacci": 1, "orthogonal": 2, "iid": 3, "distance": 4}
+DIRS = {"user": 0, "fibonacci": 1, "orthogonal": 2, "iid": 3, "distance": 4, "sobol": 5}
 PROJ = {"auto": 0, "fp32": 1, "fp32_fused": 2, "bf16x3": 3, "tf32": 4}
 
 # every symbol declared in include/qmcslice.h
@@ -33,7 +33,8 @@ EXPORTS = ("qs_plan_create", "qs_plan_destroy", "qs_plan_info", "qs_plan_directi
            "qs_set_timing", "qs_stage_times", "qs_project", "qs_sum_noalloc", "qs_grad",
            "qs_plan_autotune", "qs_plan_set_variant", "qs_batch_create", "qs_batch_destroy", "qs_sum_batched",
            "qs_batch_check", "qs_batch_set_tiling", "qs_plan_variants", "qs_distance_design",
-           "qs_distance_energy", "qs_sum_sorted", "qs_grad_sorted", "qs_plan_set_gemm", "qs_plan_gemm")
+           "qs_distance_energy", "qs_sum_sorted", "qs_grad_sorted", "qs_plan_set_gemm", "qs_plan_gemm",
+           "qs_sobol_points")
 
 
 class PlanDesc(ctypes.Structure):
@@ -79,6 +80,7 @@ def load() -> ctypes.CDLL:
         lib.qs_last_error.argtypes = []
         lib.qs_last_error.restype = c_char_p
         lib.qs_directions.argtypes = [c_int, c_int, c_int, c_u64, c_vp]
+        lib.qs_sobol_points.argtypes = [c_int, c_int, c_u64, c_vp]
         lib.qs_project.argtypes = [c_vp, c_vp, c_i64, c_vp, c_i64, c_vp]
         lib.qs_batch_create.argtypes = [ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_int]
         lib.qs_batch_destroy.argtypes = [c_vp]
@@ -105,7 +107,7 @@ def load() -> ctypes.CDLL:
                      "qs_sum_noalloc", "qs_grad", "qs_plan_autotune", "qs_plan_set_variant",
                      "qs_batch_create", "qs_batch_destroy", "qs_sum_batched", "qs_batch_check",
                      "qs_batch_set_tiling", "qs_plan_variants", "qs_distance_design", "qs_distance_energy",
-                     "qs_sum_sorted", "qs_grad_sorted", "qs_plan_set_gemm", "qs_plan_gemm"):
+                     "qs_sum_sorted", "qs_grad_sorted", "qs_plan_set_gemm", "qs_plan_gemm", "qs_sobol_points"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib

@@ -31,6 +31,7 @@ constexpr int QS_MAX_G = 16384;                // grid cells per slice (64 KB sh
 constexpr int QS_FUSED_MAX_D = 64;             // largest d of the fused form
 constexpr int QS_GRAD_MAX_D = 32;              // largest d of the gradients
 constexpr int QS_BATCH_MAX_D = 64;             // largest d of a batched problem
+constexpr int QS_SOBOL_MAX_D = 4096;           // largest d of the Sobol' directions
 
 // Spread kernel variants, in two families fixed by (G, W): the moment family
 // where its table fits two CTAs per SM, the tap family otherwise.  Within a
@@ -251,6 +252,9 @@ void qs_fit_window(int W, double beta, qs_window* win);
 double qs_window_tap(const qs_window* win, int W, int j, double s);
 void qs_window_transform(const qs_window* win, int W, int K, int G, double* out);  // out[K + 1]
 void qs_twiddles(int G, float2* out);                                               // out[G / 2]
+// Sobol' points (qs_sobol.cu): u in (0,1)^d (P x d) and the unit rows Phi^{-1}(u) / |Phi^{-1}(u)|
+qs_status qs_sobol_cube(int d, int P, uint64_t seed, double* out);
+qs_status qs_sobol_sphere(int d, int P, uint64_t seed, float* out);
 // window shape parameter of the exponential of semicircle for sigma_os = 2
 inline double qs_window_beta(int W) { return 2.30 * W; }
 

@@ -398,6 +398,12 @@ qs_status qs_directions(qs_dirs kind, int d, int P, uint64_t seed, float* out)
         }
         return QS_OK;
     }
+    if (kind == QS_DIR_SOBOL) {
+        if (d > QS_SOBOL_MAX_D) return fail(QS_ERR_UNSUPPORTED, "qs_directions: Sobol' directions need d <= %d",
+                                            QS_SOBOL_MAX_D);
+        const qs_status st = qs_sobol_sphere(d, P, seed, out);
+        return st == QS_OK ? QS_OK : fail(st, "qs_directions: Sobol' directions unavailable for d = %d", d);
+    }
     if (kind == QS_DIR_DISTANCE)
         return fail(QS_ERR_UNSUPPORTED, "qs_directions: distance designs are optimised on the GPU "
                                         "(QS_DIR_DISTANCE in a plan, or qs_distance_design)");
@@ -429,7 +435,7 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     if (os != 2.0) return fail(QS_ERR_UNSUPPORTED, "qs_plan_create: only oversampling 2 is supported");
     if (D.max_n < 0 || D.max_m < 0) return fail(QS_ERR_ARG, "qs_plan_create: max_n / max_m must be >= 0");
     if (D.dirs == QS_DIR_USER && !D.dirs_host) return fail(QS_ERR_ARG, "qs_plan_create: dirs_host is NULL");
-    if (D.dirs < QS_DIR_USER || D.dirs > QS_DIR_DISTANCE)
+    if (D.dirs < QS_DIR_USER || D.dirs > QS_DIR_SOBOL)
         return fail(QS_ERR_ARG, "qs_plan_create: unknown direction kind %d", (int)D.dirs);
     if (D.dirs == QS_DIR_FIBONACCI && D.d != 3)
         return fail(QS_ERR_ARG, "qs_plan_create: Fibonacci directions need d = 3");
