@@ -393,11 +393,18 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
 // its own 128 points, drained to U by its eight epilogue warps, which arrive
 // on the leader's tempty barriers.  One warp of each CTA allocates and frees
 // the pair's tensor memory together.  Waits on barriers are bounded as in the
-// single-SM form; both CTAs always reach the closing cluster barrier.  On the
-// normal path every copy of the odd CTA has completed on the leader's full
-// barriers before the leader's MMA loop ends; only after a timeout (flagged)
-// can copies the odd CTA issued past the leader's last stage still be in
-// flight when the pair exits.
+// single-SM form; both CTAs always reach the two closing cluster barriers.
+// Teardown: the producers stop only at the end of their work or when their
+// own bounded wait on an empty barrier runs out (never on the other warps'
+// abort flag), so both normally issue the same number of stages; each
+// publishes that count in the leader's shared memory before the first closing
+// barrier.  The leader then completes any stage only one CTA issued (after a
+// timeout: it announces the odd CTA's bytes, or issues its own copies of the
+// stage a second time, which rewrites the same bytes, in place of the odd
+// CTA's missing ones) and waits, bounded, for the last ring of stages on its
+// full barriers, which count both CTAs' bytes.  Only then do the CTAs pass
+// the second barrier and exit, so no copy is in flight into either CTA's
+// shared memory when it exits unless that final bounded wait itself runs out.
 // ---------------------------------------------------------------------------
 template <int KIND>
 struct PairCfg;
@@ -517,6 +524,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
     constexpr int PAIR_M = 2 * TILE_M;
     extern __shared__ uint8_t smem_raw[];
     __shared__ volatile int abort_all;
+    __shared__ long long issued[2];           // stages issued by each CTA's producer (the leader's copy is read)
     const uint32_t base = smem_u32(smem_raw);
     const uint32_t tiles = (base + 1023u) & ~1023u;
     const uint32_t bars = tiles + ST * SB;
@@ -565,14 +573,29 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot_ptr;
 
+    // this CTA's copies of k-slab kb of tile t into stage s, completing on the
+    // leader's full barrier of that stage
+    auto issue_stage = [&](int64_t t, int kb, int s) {
+        const int pr = (int)(t % ptiles) * TILE_N + (int)rank * PB_ROWS;
+        const int nr = (int)(n_base + (t / ptiles) * PAIR_M + (int64_t)rank * TILE_M);
+        const uint32_t fb = cluster_addr(full0 + 8 * s, 0);  // the leader's full[s]
+        const uint32_t st = tiles + s * SB;
+        const int kc = kb * C::BK;
+        tma_load_2d_pair(st, &mA0, kc, nr, fb);
+        if (C::NOPS == 2) tma_load_2d_pair(st + A_BYTES, &mA1, kc, nr, fb);
+        tma_load_2d_pair(st + C::NOPS * A_BYTES, &mB0, kc, pr, fb);
+        if (C::NOPS == 2) tma_load_2d_pair(st + C::NOPS * A_BYTES + PB_BYTES, &mB1, kc, pr, fb);
+    };
+
     if (warp == 0 && lane == 0) {
-        // TMA producer of this CTA's halves: slab g uses stage g % ST; the
-        // copies complete on the leader's full barrier of that stage
+        // TMA producer of this CTA's halves: slab g (tile step g / nkb, k-slab
+        // g % nkb) uses stage g % ST.  It stops only at the end of its slabs
+        // or when its own bounded wait runs out, so both CTAs' producers issue
+        // the same stages unless one of them timed out (the teardown below
+        // completes the difference)
         bool ok = true;
         int64_t g = 0;
-        for (int64_t t = cid; t < T && ok && !abort_all; t += ncl) {
-            const int pr = (int)(t % ptiles) * TILE_N + (int)rank * PB_ROWS;
-            const int nr = (int)(n_base + (t / ptiles) * PAIR_M + (int64_t)rank * TILE_M);
+        for (int64_t t = cid; t < T && ok; t += ncl) {
             for (int kb = 0; kb < nkb; ++kb, ++g) {
                 const int s = (int)(g % ST);
                 const uint32_t ph = (uint32_t)(g / ST) & 1u;
@@ -580,21 +603,14 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
                     ok = false;
                     break;
                 }
-                const uint32_t fb = cluster_addr(full0 + 8 * s, 0);  // the leader's full[s]
-                const uint32_t st = tiles + s * SB;
-                const int kc = kb * C::BK;
                 if (leader) mbar_expect_tx(full0 + 8 * s, 2 * SB);
-                tma_load_2d_pair(st, &mA0, kc, nr, fb);
-                if (C::NOPS == 2) tma_load_2d_pair(st + A_BYTES, &mA1, kc, nr, fb);
-                tma_load_2d_pair(st + C::NOPS * A_BYTES, &mB0, kc, pr, fb);
-                if (C::NOPS == 2) tma_load_2d_pair(st + C::NOPS * A_BYTES + PB_BYTES, &mB1, kc, pr, fb);
+                issue_stage(t, kb, s);
             }
         }
-        // the leader's full barriers also count the odd CTA's bytes: once the
-        // last stages have completed, no copy of the pair is in flight
-        if (leader)
-            for (int64_t h = (g > ST ? g - ST : 0); h < g; ++h)
-                if (!mbar_wait(full0 + 8 * (int)(h % ST), (uint32_t)(h / ST) & 1u)) ok = false;
+        // publish the count in the leader's shared memory (ordered before the
+        // first closing cluster barrier by its release)
+        const uint32_t slot = cluster_addr(smem_u32(&issued[rank]), 0);
+        asm volatile("st.shared::cluster.s64 [%0], %1;" ::"r"(slot), "l"((long long)g) : "memory");
         if (!ok) {
             abort_all = 1;
             atomicOr(flag, QS_FLAG_TIMEOUT);
@@ -688,7 +704,27 @@ __global__ void __launch_bounds__(TCP_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    cluster_sync_all();  // both CTAs are done with the pair's barriers and tensor memory
+    cluster_sync_all();  // both producers' counts are in the leader's shared memory
+    if (leader && warp == 0 && lane == 0) {
+        // every copy of the pair completes on the leader's full barriers; a
+        // stage's phase completes once both CTAs' bytes have landed.  Stages
+        // below max(g0, g1) - ST completed before the last ring was issued
+        // (a stage is issued only after the MMAs consumed the one ST slabs
+        // earlier), and |g0 - g1| <= ST for the same reason.
+        const int64_t g0 = issued[0], g1 = issued[1];
+        const int64_t hi = g0 > g1 ? g0 : g1, mid = g0 > g1 ? g1 : g0;
+        bool ok = true;
+        for (int64_t h = mid; h < hi; ++h) {
+            if (g0 > g1) issue_stage(cid + (h / nkb) * ncl, (int)(h % nkb), (int)(h % ST));  // the odd CTA's bytes
+                                                                                           // will not come: send ours again
+            else mbar_expect_tx(full0 + 8 * (int)(h % ST), SB);  // announce the odd CTA's bytes
+        }
+        for (int64_t h = (hi > ST ? hi - ST : 0); h < hi; ++h)
+            if (!mbar_wait(full0 + 8 * (int)(h % ST), (uint32_t)(h / ST) & 1u)) ok = false;
+        if (!ok) atomicOr(flag, QS_FLAG_TIMEOUT);
+    }
+    __syncthreads();
+    cluster_sync_all();  // no copy of the pair is in flight; both CTAs are done with its barriers and tensor memory
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TILE_N)
