@@ -29,6 +29,7 @@ import subprocess
 import sys
 import tempfile
 import time
+import warnings
 
 import numpy as np
 
@@ -332,6 +333,13 @@ def run_ours(args, rank, world, local_rank):
             r, dt, desc = oracle_sample_rate(prob, args.cpu_slices, args.cpu_targets)
             line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                                     "sample": desc, "seconds": dt}
+            # the paper's CPU timings are single-threaded (Sec. 4.3)
+            r1, dt1, desc1 = oracle_sample_rate(prob, args.cpu1_slices, args.cpu1_targets, threads=1)
+            line["cpu_baseline_1thread"] = {"value": r1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                            "sample": desc1, "seconds": dt1}
+        if world == 1 and args.workload == "mnist_laplace" and not args.no_extra_configs:
+            line["config"]["precision_forms"] = precision_forms(args, flush, clocks, peaks, peak_src, sm_count)
+            line["config"]["small_gauss"] = small_gauss_latency(args)
         print(json.dumps(line), flush=True)
     plan.close()
 
@@ -453,6 +461,309 @@ def plain_fp32_compare(prob, x, w, y, flush, args, err_idx_err=True):
         if err_idx_err:
             out["rel_err_vs_oracle"], _ = error_vs_oracle(prob, s, args.error_targets)
         return out
+
+
+def precision_forms(args, flush, clocks, peaks, peak_src, sm_count):
+    """The precision-form workload (d = 64, N = M = 2e5, x, y ~ N(0, I), w ~ N(0, 1),
+    negative distance, P = 4096 Sobol directions, N_ft = 2048) in every projection
+    form (FP32 SIMT, TF32 and BF16x3 tensor-core GEMMs; spread, FFT and interpolation
+    in FP32 throughout), each timed like the headline and with its error against the
+    FP64 oracle.  The oracle's cost does not depend on how many targets are sampled
+    (every slice needs the full adjoint NDFT of all 2e5 sources), so each form's error
+    is measured on a plan over the first `pf_error_slices` of the 4096 directions, the
+    same sources and 64 sampled targets: the same kernels on the same data, a subset
+    of the slices."""
+    import torch
+
+    import oracle
+    from paper_2410_01316_gb300 import QSPlan
+
+    prob = make_problem("gauss64_negdist")
+    dev = flush.device
+    x = torch.from_numpy(prob.x).to(dev)
+    y = torch.from_numpy(prob.y).to(dev)
+    w = torch.from_numpy(prob.w).to(dev)
+    s = torch.empty(prob.M, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    n_sub = max(1, min(prob.P, args.pf_error_slices))
+    idx = np.random.default_rng(4242).choice(prob.M, 64, replace=False)
+    t_ = oracle.tau(prob.kernel, prob.kparam, prob.R)
+    c = oracle.coeffs(prob.kernel, prob.kparam, prob.d, t_, prob.n_ft)
+    t0 = time.perf_counter()
+    ref = oracle.o1_sum(prob.x, prob.w, np.ascontiguousarray(prob.y[idx]), np.ascontiguousarray(prob.xi[:n_sub]),
+                        t_, c)
+    oracle_s = time.perf_counter() - t0
+    norm = float(np.abs(prob.w.astype(np.float64)).sum()) * prob.R
+    out = {"workload": workload_desc(prob, "per form"),
+           "rel_err_sample": f"plan over the first {n_sub} of the {prob.P} directions, all {prob.N} sources, "
+                             f"64 sampled targets (oracle {oracle_s:.1f} s)",
+           "rel_err_norm": "max_m |s - s_oracle| / (sum|w| R)",
+           "l2": "flushed between steps (256 MB write); inputs also exceed L2", "forms": {}}
+    steps = max(3, min(args.steps, 10))
+    sampler = ClockSampler(smi_gpu_id(dev))
+    sampler.start()
+    for form in ("fp32", "tf32", "bf16x3"):
+        with QSPlan(prob.d, prob.kernel, prob.P, prob.n_ft, prob.R, prob.kparam, dirs=prob.xi, window=prob.window,
+                    proj=form, max_n=prob.N, max_m=prob.M) as plan:
+            variant = plan.autotune(x, w)
+            gemm = ("pair" if plan.gemm_pair() else "single") if form in ("bf16x3", "tf32") else None
+            for _ in range(max(3, args.warmup)):
+                plan.sum(x, w, y, out=s)
+            plan.check()
+            plan.set_timing(True)
+            ms, stage_acc = [], {}
+            for _ in range(steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                plan.sum(x, w, y, out=s)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                for k, v in plan.stage_times().items():
+                    stage_acc[k] = stage_acc.get(k, 0.0) + v
+            plan.set_timing(False)
+            status = plan.status()
+            stages = {k: v / steps for k, v in stage_acc.items()}
+            _, rl = roofline(prob, plan, stages, clocks, peaks, peak_src, sm_count)
+        with QSPlan(prob.d, prob.kernel, n_sub, prob.n_ft, prob.R, prob.kparam, dirs=prob.xi[:n_sub],
+                    window=prob.window, proj=form, max_n=prob.N, max_m=prob.M) as sp:
+            sp.sum(x, w, y, out=s)
+            sp.check()
+            err = float(np.max(np.abs(s.cpu().numpy().astype(np.float64)[idx] - ref))) / norm
+        t = sum(ms) / len(ms)
+        out["forms"][form] = {
+            "ms_per_step": t, "value": prob.point_slices / (t / 1e3) / 1e9, "unit": UNIT,
+            "rel_err_vs_oracle": err, "steps": steps, "spread_variant": variant, "gemm": gemm,
+            "device_status": int(status), "stage_ms": {k: round(v, 4) for k, v in stages.items()},
+            "stage_rooflines": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()
+                                    if kk in ("bound", "achieved", "peak", "unit", "frac", "ms", "hbm_achieved_gbs",
+                                              "hbm_frac")}
+                                for k, v in rl.items()}}
+    out["clocks"] = sampler.stop()
+    f = out["forms"]
+    out["bf16x3_speedup_vs_fp32"] = f["fp32"]["ms_per_step"] / f["bf16x3"]["ms_per_step"]
+    return out
+
+
+def small_gauss_latency(args):
+    """The small d = 3 workload (N = M = 1000, Gauss sigma = 0.5, P = 64 spherical
+    Fibonacci, N_ft = 256, fused FP32 projection): launch-bound, so reported as
+    microseconds per call, directly and as a CUDA-graph replay of one call."""
+    import torch
+
+    from paper_2410_01316_gb300 import QSPlan
+
+    prob = make_problem("small_gauss")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x = torch.from_numpy(prob.x).to(dev)
+    y = torch.from_numpy(prob.y).to(dev)
+    w = torch.from_numpy(prob.w).to(dev)
+    s = torch.empty(prob.M, dtype=torch.float32, device=dev)
+    reps = 200
+    with QSPlan(prob.d, prob.kernel, prob.P, prob.n_ft, prob.R, prob.kparam, dirs=prob.xi, window=prob.window,
+                proj="fp32_fused", max_n=prob.N, max_m=prob.M) as plan:
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(5):
+                plan.sum(x, w, y, out=s, stream=side)
+            side.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(side)
+            for _ in range(reps):
+                plan.sum(x, w, y, out=s, stream=side)
+            e1.record(side)
+            e1.synchronize()
+            direct_us = 1e3 * e0.elapsed_time(e1) / reps
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=side):
+                plan.sum(x, w, y, out=s, stream=side)
+            for _ in range(5):
+                g.replay()
+            side.synchronize()
+            e0.record(side)
+            for _ in range(reps):
+                g.replay()
+            e1.record(side)
+            e1.synchronize()
+            graph_us = 1e3 * e0.elapsed_time(e1) / reps
+        plan.check()
+    err, desc = error_vs_oracle(prob, s, prob.M)
+    return {"workload": workload_desc(prob, "fp32_fused"), "us_per_call": direct_us, "us_per_graph_replay": graph_us,
+            "calls": reps, "launches_per_call": 4, "rel_err_vs_oracle": err, "rel_err_sample": desc,
+            "window": "exponential of semicircle, W = 8 taps (in place of Kaiser-Bessel; same width, "
+                      "the oracle has no window)"}
+
+
+def run_gpu_compare(args, rank, world, local_rank):
+    """The paper's GPU-comparison shape (App. H, "GPU Comparison"): d = 30, N = M = 960000
+    PCA-shaped points summed against themselves with unit weights, P = 5120 distance QMC
+    directions (QS_DIR_DISTANCE), for the Gauss, Laplace, Matern (nu = 3/2) and negative
+    distance kernels with the paper's N_ft.  A step = the four sums; per kernel: ms,
+    Gpoint-slices/s, the error against the oracle (on a plan over the first
+    `pf_error_slices` directions, 64 sampled targets) and the relative L1 error of the
+    full sum against the exact kernel sum on those targets (the paper's error measure)."""
+    import torch
+
+    import oracle
+    from paper_2410_01316_gb300 import QSPlan
+    from paper_2410_01316_gb300 import build as qbuild
+    from paper_2410_01316_gb300 import workloads as W
+
+    qbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    kernels = ("gauss", "laplace", "matern", "negdist")
+    per, tot_ps, tot_ms = {}, 0, 0.0
+    sampler = ClockSampler(smi_gpu_id(dev))
+    sampler.start()
+    for kern in kernels:
+        prob = W.gpu_compare30(kern, P=args.P or 5120)
+        x = torch.from_numpy(prob.x).to(dev)
+        w = torch.from_numpy(prob.w).to(dev)
+        s = torch.empty(prob.M, dtype=torch.float32, device=dev)
+        with QSPlan(prob.d, prob.kernel, prob.P, prob.n_ft, prob.R, prob.kparam, dirs="distance", seed=7,
+                    window=prob.window, proj="auto", max_n=prob.N, max_m=prob.M, kparam2=prob.kparam2) as plan:
+            variant = plan.autotune(x, w)
+            for _ in range(max(3, args.warmup)):
+                plan.sum(x, w, x, out=s)
+            plan.check()
+            ms = []
+            for _ in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                plan.sum(x, w, x, out=s)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            status = plan.status()
+            xi = plan.directions()
+            proj = plan.proj
+        t = sum(ms) / len(ms)
+        tot_ps += prob.point_slices
+        tot_ms += t
+        rec = {"ms_per_step": t, "value": prob.point_slices / (t / 1e3) / 1e9, "unit": UNIT, "N_ft": prob.n_ft,
+               "kparam": prob.kparam, "proj": proj, "spread_variant": variant, "device_status": int(status)}
+        if not args.no_error_check:
+            idx = np.random.default_rng(4242).choice(prob.M, 64, replace=False)
+            yi = np.ascontiguousarray(prob.x[idx])
+            sg = s.cpu().numpy().astype(np.float64)[idx]
+            exact = oracle.o2_exact(prob.kernel, prob.kparam, prob.x, prob.w, yi, nu=prob.kparam2)
+            rec["rel_l1_vs_exact"] = float(np.abs(sg - exact).sum() / np.abs(exact).sum())
+            n_sub = max(1, min(prob.P, args.pf_error_slices))
+            with QSPlan(prob.d, prob.kernel, n_sub, prob.n_ft, prob.R, prob.kparam, dirs=xi[:n_sub],
+                        window=prob.window, proj="auto", max_n=prob.N, max_m=prob.M, kparam2=prob.kparam2) as sp:
+                sp.sum(x, w, x, out=s)
+                sp.check()
+                sub = s.cpu().numpy().astype(np.float64)[idx]
+            tt = oracle.tau(prob.kernel, prob.kparam, prob.R)
+            c = oracle.coeffs(prob.kernel, prob.kparam, prob.d, tt, prob.n_ft, nu=prob.kparam2)
+            ref = oracle.o1_sum(prob.x, prob.w, yi, np.ascontiguousarray(xi[:n_sub]), tt, c)
+            norm = float(prob.N) * (prob.R if prob.kernel == "negdist" else 1.0)
+            rec["rel_err_vs_oracle"] = float(np.max(np.abs(sub - ref))) / norm
+            rec["rel_err_sample"] = f"plan over the first {n_sub} of the {prob.P} directions, 64 sampled targets"
+        per[kern] = rec
+        del x, w, s
+    clocks = sampler.stop()
+    line = {"metric": METRIC, "value": tot_ps / (tot_ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "gpu_compare30: d=30, N=M=960000 PCA-shaped points (independent N(0, 1/j) "
+                                   "coordinates) summed against themselves, w = 1, P=5120 distance QMC directions, "
+                                   "median rule; one step = the Gauss, Laplace, Matern and negative distance sums",
+                       "kernels": per, "l2": "flushed between steps (256 MB write); inputs also exceed L2"},
+            "clocks": clocks, "gpu_launches": args.steps * 4 * 6}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def slicing_rate_study(dims=(3, 10, 50), kernels=("negdist", "gauss", "laplace"), Ps=None, reps=50, n_x=1000,
+                       iters=1000, designs=("iid", "orthogonal", "sobol", "distance"), seed=20241007):
+    """Slicing error |F(|x|) - (1/P) sum_p f(|<xi_p, x>|)| (Sec. 4.2, eq. approximation)
+    for x ~ N(0, 0.1 I), averaged over n_x samples of x and `reps` realisations of the
+    directions, and its rate r (error ~ P^-r, a least-squares line in the log-log plot,
+    as for Table tab:rates).  Designs: iid, orthogonal, scrambled Sobol (Sec. 4.1) and
+    the library's distance QMC design (qs_distance_design on the GPU, from a seeded
+    orthogonal start), randomised by a Haar rotation per realisation (App. D).  The
+    sliced estimate is the oracle's closed-form sliced sum (one source at the origin),
+    so only kernels whose f the oracle has in closed form enter: the negative distance
+    in any d, Gauss and Laplace at d = 3.  Kernel parameters: median rule on |x|."""
+    import torch
+
+    import oracle
+    from paper_2410_01316_gb300 import distance_design
+    from paper_2410_01316_gb300 import workloads as W
+
+    Ps = Ps or [5 * 2 ** k for k in range(1, 9)]
+    out = {}
+    for d in dims:
+        rng = np.random.default_rng(seed + d)
+        xs = W.gaussian(rng, n_x, d, scale=math.sqrt(0.1))
+        med = float(np.median(np.linalg.norm(xs.astype(np.float64), axis=1)))
+        origin = np.zeros((1, d), dtype=np.float32)
+        base = {}
+        if "distance" in designs:
+            for P in Ps:
+                xi0 = torch.from_numpy(W.directions_orthogonal(np.random.default_rng(seed + P), P, d)).cuda()
+                distance_design(xi0, iters=iters)
+                base[P] = xi0.cpu().numpy()
+        for kern in kernels:
+            if kern != "negdist" and d != 3:
+                continue
+            kp = {"negdist": 0.0, "gauss": med, "laplace": 1.0 / med}[kern]
+            exact = np.array([oracle.F(kern, kp, float(r)) for r in np.linalg.norm(xs.astype(np.float64), axis=1)])
+            res = {}
+            for des in designs:
+                errs = []
+                for P in Ps:
+                    e = 0.0
+                    for rep in range(reps):
+                        r = np.random.default_rng([seed, d, P, rep])
+                        if des == "iid":
+                            xi = W.directions_iid(r, P, d)
+                        elif des == "orthogonal":
+                            xi = W.directions_orthogonal(r, P, d)
+                        elif des == "sobol":
+                            with warnings.catch_warnings():  # P = 5 2^k is not a power of two
+                                warnings.simplefilter("ignore")
+                                xi = W.directions_sobol(r, P, d)
+                        else:
+                            xi = W.random_rotation(r, base[P])
+                        est = oracle.o3_sliced(kern, kp, origin, None, xs, xi)
+                        e += float(np.mean(np.abs(est - exact)))
+                    errs.append(e / reps)
+                slope = np.polyfit(np.log(Ps), np.log(errs), 1)[0]
+                res[des] = {"rate": float(-slope), "errors": errs}
+            out[f"{kern}_d{d}"] = {"kparam": kp, "P": list(Ps), "designs": res}
+    return out
+
+
+def run_rates(args, rank, world, local_rank):
+    """Slicing-error rates of the direction designs (Sec. 4.2, Table tab:rates): one JSON
+    line with the fitted rate r per kernel, dimension and design.  Not a throughput run."""
+    import torch
+
+    from paper_2410_01316_gb300 import build as qbuild
+
+    qbuild.build()
+    torch.cuda.set_device(local_rank)
+    t0 = time.perf_counter()
+    study = slicing_rate_study(reps=args.rate_reps)
+    line = {"metric": "slicing error rate r (error ~ P^-r)", "workload": "slicing_rates: x ~ N(0, 0.1 I), d in "
+            "{3, 10, 50}, P = 5 2^k (k = 1..8), iid / orthogonal / scrambled Sobol / distance QMC (library, "
+            "randomly rotated) directions, median rule on |x|", "reps": args.rate_reps, "samples_x": 1000,
+            "paper_rates_distance": {"gauss_d3": 2.10, "laplace_d3": 1.26, "negdist": [1.27, 0.71, 0.70]},
+            "rates": {k: {des: round(v["rate"], 3) for des, v in r["designs"].items()} for k, r in study.items()},
+            "study": study, "seconds": time.perf_counter() - t0}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_mmd_flow(args, rank, world, local_rank):
@@ -592,28 +903,6 @@ def run_design(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
-def batch256_problems(n=256, seed=20241004):
-    """256 Gauss problems: N, M log-uniform in [1e3, 1e5], d in {3, 16, 64},
-    N_ft in {256, 512, 1024}, P = 256 (Fibonacci for d = 3, else orthogonal),
-    sigma by the median rule."""
-    from paper_2410_01316_gb300 import workloads as W
-
-    rng = np.random.default_rng(seed)
-    out = []
-    for i in range(n):
-        N = int(np.exp(rng.uniform(np.log(1e3), np.log(1e5))))
-        M = int(np.exp(rng.uniform(np.log(1e3), np.log(1e5))))
-        d = int(rng.choice([3, 16, 64]))
-        n_ft = int(rng.choice([256, 512, 1024]))
-        x = W.gaussian(rng, N, d)
-        y = W.gaussian(rng, M, d)
-        w = rng.standard_normal(N).astype(np.float32)
-        sigma = W.median_pair_distance(x, y, 1000, seed + 7 * i)
-        xi = W.directions_fibonacci(256) if d == 3 else W.directions_orthogonal(rng, 256, d)
-        out.append(W.Problem(f"batch{i}", d, "gauss", sigma, 256, n_ft, x, w, y, xi, W.radius(x, y)))
-    return out
-
-
 def run_batch(args, rank, world, local_rank):
     """One persistent, graph-captured launch over 256 independent problems."""
     import torch
@@ -624,7 +913,9 @@ def run_batch(args, rank, world, local_rank):
     qbuild.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    probs = batch256_problems()
+    from paper_2410_01316_gb300 import workloads as W
+
+    probs = W.batch256_problems()
     plans = [QSPlan(p.d, p.kernel, p.P, p.n_ft, p.R, p.kparam, dirs=p.xi, proj="auto", max_n=p.N,
                     max_m=p.M) for p in probs]
     data = [(torch.from_numpy(p.x).to(dev), torch.from_numpy(p.w).to(dev), torch.from_numpy(p.y).to(dev),
@@ -761,7 +1052,7 @@ def stage_rooflines(prob, plan, stages, clocks, peaks, peak_src, sm_count):
                 f"{sm_count} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz")
     for name, rows in (("prep_x", N), ("prep_y", M)):
         t = stages.get(name, 0.0) / 1e3
-        if t <= 0:
+        if t <= 0 or plan.proj not in ("bf16x3", "tf32"):  # only the tensor-core forms split operands
             continue
         by = rows * d * 8.0  # read FP32, write BF16 hi + lo (or TF32)
         add(name, "hbm", by / t / 1e9, peaks["hbm_gbs"], "GB/s", f"8 B per coordinate = {by:.3e} B",
@@ -903,6 +1194,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-slices", type=int, default=128)
     ap.add_argument("--cpu-targets", type=int, default=1024)
+    ap.add_argument("--cpu1-slices", type=int, default=8, help="single-thread oracle sample: slices")
+    ap.add_argument("--cpu1-targets", type=int, default=256, help="single-thread oracle sample: targets")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="skip the precision-form (d = 64) and small d = 3 sub-records of the default workload")
+    ap.add_argument("--pf-error-slices", type=int, default=64,
+                    help="slices of the precision-form error check (oracle cost grows with them)")
+    ap.add_argument("--rate-reps", type=int, default=50, help="slicing_rates: realisations per design and P")
     ap.add_argument("--ref-slices", type=int, default=16)
     ap.add_argument("--ref-targets", type=int, default=1024)
     args = ap.parse_args()
@@ -913,6 +1211,10 @@ def main():
         run_mmd_flow(args, rank, world, local)
     elif args.workload == "batch256":
         run_batch(args, rank, world, local)
+    elif args.workload == "gpu_compare30":
+        run_gpu_compare(args, rank, world, local)
+    elif args.workload == "slicing_rates":
+        run_rates(args, rank, world, local)
     elif args.workload == "distance_design":
         run_design(args, rank, world, local)
     elif args.sorted:
