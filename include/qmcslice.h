@@ -157,11 +157,16 @@ qs_status qs_sum(qs_plan plan, const float* x, int64_t N, const float* w,
  *   gw[n] = dL/dw_n = (1/P) sum_p sum_m v_m g(a_{n,p} - b_{m,p})
  * computed by the same spread / FFT / interpolation pipeline with the filter
  * 2 pi i k c_k / psi^2 and a back-projection onto the directions (x and w
- * swap roles with y and v).  x: N x d, w: N (NULL = ones), y: M x d,
- * v: M (NULL = ones), gx: N x d, gw: N, gy: M x d; all device memory; any
- * output may be NULL to skip it.  Needs d <= 32.  Asynchronous on `stream`,
- * allocates nothing.  Errors: QS_ERR_ARG, QS_ERR_UNSUPPORTED (d > 32),
- * QS_ERR_CUDA; data errors via qs_check.
+ * swap roles with y and v).  For d <= 32 the back-projection is summed inside
+ * the interpolation, per component; for d > 32 the derivative values of
+ * every (point, slice) pair are written over the plan's projection buffer
+ * and back-projected by a GEMM (points x P)(P x d), which needs an unfused
+ * projection form (QS_PROJ_FP32, QS_PROJ_BF16X3, QS_PROJ_TF32).  x: N x d,
+ * w: N (NULL = ones), y: M x d, v: M (NULL = ones), gx: N x d, gw: N,
+ * gy: M x d; all device memory; any output may be NULL to skip it.
+ * Asynchronous on `stream`, allocates nothing.  Errors: QS_ERR_ARG,
+ * QS_ERR_UNSUPPORTED (fused form with d > 32), QS_ERR_CUDA; data errors via
+ * qs_check.
  */
 qs_status qs_grad(qs_plan plan, const float* x, int64_t N, const float* w, const float* y, int64_t M,
                   const float* v, float* gx, float* gw, float* gy, void* stream);

@@ -741,6 +741,116 @@ __global__ void __launch_bounds__(256) interp_grad_kernel(qs_launch L, const flo
         }
 }
 
+// ---------------------------------------------------------------------------
+// Gradients for d > QS_GRAD_MAX_D (unfused projection forms): the derivative
+// interpolation without the back-projection, written over the projections,
+//   q_{m,p} = sum_l h'_p[l] psi(u_{m,p} - l)   in place of u_{m,p} in U,
+// then the back-projection onto the directions as a GEMM (backproj_kernel).
+// grid (ceil(M / (256 ID_TPT)), P): the CTA stages its slice's derivative row
+// once (wrapped by ROW_PAD cells) and walks ID_TPT targets per thread.  The
+// taps and their sum are those of interp_grad_kernel, so q is the same number.
+// ---------------------------------------------------------------------------
+constexpr int ID_TPT = 16;
+
+template <int W>
+__global__ void __launch_bounds__(256) interp_deriv_kernel(qs_launch L, const float* __restrict__ Hd)
+{
+    extern __shared__ float4 drow4[];
+    float* row = reinterpret_cast<float*>(drow4);
+    const int G = L.G, mask = G - 1;
+    const int p = blockIdx.y;
+    const float* src = Hd + (size_t)p * G;
+    for (int i = threadIdx.x; i < G + ROW_PAD; i += blockDim.x) row[i] = __ldg(&src[i < G ? i : i - G]);
+    __syncthreads();
+    float* urow = L.U + (size_t)p * L.ldU;
+    const int64_t m0 = (int64_t)blockIdx.x * blockDim.x * ID_TPT + threadIdx.x;
+#pragma unroll 4
+    for (int i = 0; i < ID_TPT; ++i) {
+        const int64_t m = m0 + (int64_t)i * blockDim.x;
+        if (m >= L.M) break;
+        const float u = qs_check_u(urow[m], L.half_G, L.flag);
+        int l0;
+        float tap[W];
+        qs_taps<W>(u, L.win, l0, tap);
+        const float* h = row + (l0 & mask);
+        float q = 0.0f;
+#pragma unroll
+        for (int j = 0; j < W; ++j) q = fmaf(h[j], tap[j], q);
+        urow[m] = q;
+    }
+}
+
+// out[m][j] = scale * fac_m * sum_p Q[p][m] xi[p][j] for m < M, j < d: the
+// back-projection onto the directions as a GEMM (M x P)(P x d), Q slice-major
+// with row stride ldQ, xi P x d row-major.  CTA tile: 128 targets x 64
+// components, 256 threads with 8 x 4 outputs each; the slices go in chunks of
+// 16 staged in shared memory (both operands coalesced), each chunk's products
+// summed by FMA in slice order and the chunk sums accumulated by TwoSum, so
+// the result does not depend on the tiling and is reproducible.
+constexpr int BP_TM = 128, BP_TN = 64, BP_TK = 16;
+
+__global__ void __launch_bounds__(256) backproj_kernel(const float* __restrict__ Q, int64_t ldQ, int64_t M, int P,
+                                                       const float* __restrict__ xi, int d, float scale,
+                                                       const float* __restrict__ fac, float* __restrict__ out)
+{
+    __shared__ __align__(16) float As[BP_TK][BP_TM];
+    __shared__ __align__(16) float Bs[BP_TK][BP_TN];
+    const int64_t m0 = (int64_t)blockIdx.x * BP_TM;
+    const int j0 = blockIdx.y * BP_TN;
+    const int tx = threadIdx.x & 15;  // components j0 + 4 tx .. + 3
+    const int ty = threadIdx.x >> 4;  // targets m0 + 8 ty .. + 7
+    float hi[8][4], lo[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) hi[i][k] = lo[i][k] = 0.0f;
+    for (int p0 = 0; p0 < P; p0 += BP_TK) {
+        for (int i = threadIdx.x; i < BP_TK * BP_TM; i += blockDim.x) {
+            const int r = i / BP_TM, c = i - r * BP_TM;
+            const int64_t m = m0 + c;
+            As[r][c] = (p0 + r < P && m < M) ? __ldg(&Q[(size_t)(p0 + r) * ldQ + m]) : 0.0f;
+        }
+        for (int i = threadIdx.x; i < BP_TK * BP_TN; i += blockDim.x) {
+            const int r = i / BP_TN, c = i - r * BP_TN;
+            Bs[r][c] = (p0 + r < P && j0 + c < d) ? __ldg(&xi[(size_t)(p0 + r) * d + j0 + c]) : 0.0f;
+        }
+        __syncthreads();
+        float acc[8][4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][k] = 0.0f;
+#pragma unroll 4
+        for (int r = 0; r < BP_TK; ++r) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[r][8 * ty]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[r][8 * ty + 4]);
+            const float4 b = *reinterpret_cast<const float4*>(&Bs[r][4 * tx]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(a[i], bb[k], acc[i][k]);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) qs_two_sum(hi[i][k], lo[i][k], acc[i][k]);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t m = m0 + 8 * ty + i;
+        if (m >= M) break;
+        const float f = scale * (fac ? __ldg(&fac[m]) : 1.0f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = j0 + 4 * tx + k;
+            if (j < d) out[(size_t)m * d + j] = (hi[i][k] + lo[i][k]) * f;
+        }
+    }
+}
+
 // g[m][j] = scale * fac_m * sum over slice groups (in order) of the partials.
 __global__ void reduce_grad_kernel(const float* __restrict__ part, int S, int64_t M, int d, float scale,
                                    const float* __restrict__ fac, float* __restrict__ out)
@@ -1226,6 +1336,38 @@ cudaError_t qs_launch_interp_grad(const qs_launch& L, int W, const float* y, con
         case 12: return launch_interp_grad_w<12>(L, y, Hd, xi, part, fused, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t qs_launch_interp_deriv(const qs_launch& L, int W, const float* Hd, cudaStream_t st)
+{
+    if (L.M <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((L.M + 256 * ID_TPT - 1) / (256 * ID_TPT)), (unsigned)L.P);
+    const size_t smem = ((size_t)L.G + ROW_PAD) * sizeof(float);
+#define QS_LAUNCH_DERIV(WW)                                                                                 \
+    do {                                                                                                    \
+        cudaError_t e_ = cudaFuncSetAttribute(interp_deriv_kernel<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                              (int)smem);                                                   \
+        if (e_ != cudaSuccess) return e_;                                                                   \
+        interp_deriv_kernel<WW><<<grid, 256, smem, st>>>(L, Hd);                                            \
+    } while (0)
+    switch (W) {
+        case 6: QS_LAUNCH_DERIV(6); break;
+        case 8: QS_LAUNCH_DERIV(8); break;
+        case 10: QS_LAUNCH_DERIV(10); break;
+        case 12: QS_LAUNCH_DERIV(12); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef QS_LAUNCH_DERIV
+    return cudaGetLastError();
+}
+
+cudaError_t qs_launch_backproj(const float* Q, int64_t ldQ, int64_t M, int P, const float* xi, int d, float scale,
+                               const float* fac, float* out, cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((M + BP_TM - 1) / BP_TM), (unsigned)((d + BP_TN - 1) / BP_TN));
+    backproj_kernel<<<grid, 256, 0, st>>>(Q, ldQ, M, P, xi, d, scale, fac, out);
+    return cudaGetLastError();
 }
 
 cudaError_t qs_launch_reduce_grad(const float* part, int S, int64_t M, int d, float scale, const float* fac,

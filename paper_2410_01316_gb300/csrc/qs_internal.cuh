@@ -29,9 +29,10 @@ constexpr int QS_MAX_HALF = QS_MAX_W / 2;
 constexpr int QS_MAX_TERMS = QS_MAX_HALF + 1;  // terms per even / odd part
 constexpr int QS_MAX_G = 16384;                // grid cells per slice (64 KB shared)
 constexpr int QS_FUSED_MAX_D = 64;             // largest d of the fused form
-constexpr int QS_GRAD_MAX_D = 32;              // largest d of the gradients
+constexpr int QS_GRAD_MAX_D = 32;              // largest d of the fused back-projection (larger: a GEMM)
 constexpr int QS_BATCH_MAX_D = 64;             // largest d of a batched problem
 constexpr int QS_SOBOL_MAX_D = 4096;           // largest d of the Sobol' directions
+constexpr int QS_BATCH_STREAMS = 8;            // streams of a batch's concurrent mode
 
 // Spread kernel variants, in two families fixed by (G, W): the moment family
 // where its table fits two CTAs per SM, the tap family otherwise.  Within a
@@ -279,6 +280,11 @@ cudaError_t qs_launch_interp_grad(const qs_launch& L, int W, const float* y, con
                                   float* part, bool fused, cudaStream_t st);
 cudaError_t qs_launch_reduce_grad(const float* part, int S, int64_t M, int d, float scale, const float* fac,
                                   float* out, cudaStream_t st);
+// d > QS_GRAD_MAX_D: derivative interpolation written over L.U (targets [0, L.M)), then
+// out[m][j] = scale fac_m sum_p Q[p][m] xi[p][j]
+cudaError_t qs_launch_interp_deriv(const qs_launch& L, int W, const float* Hd, cudaStream_t st);
+cudaError_t qs_launch_backproj(const float* Q, int64_t ldQ, int64_t M, int P, const float* xi, int d, float scale,
+                               const float* fac, float* out, cudaStream_t st);
 bool qs_make_tmap(void* map_out, const void* base, int elem_bytes, int d, int64_t rows, int ldk, int box_rows);
 // max_blocks > 0 caps the grid (a split running beside another kernel).
 cudaError_t qs_launch_split_bf16(const float* X, int64_t rows, int d, int ldk, void* hi, void* lo, cudaStream_t st,

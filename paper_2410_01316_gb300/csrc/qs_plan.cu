@@ -552,9 +552,13 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
             if ((size_t)(S * rows) > sm) sm = (size_t)(S * rows);
         }
         p->gpart_elems = 2 * sm * (size_t)d;
+        QS_ALLOC(p->d_gpart, p->gpart_elems);
+    }
+    if (d <= QS_GRAD_MAX_D || proj != QS_PROJ_FP32_FUSED) {
+        // derivative filter and grid; above QS_GRAD_MAX_D the unfused forms
+        // back-project with a GEMM from the projection buffer instead of d partials
         QS_ALLOC(p->d_Dd, (size_t)G / 2 + 1);
         QS_ALLOC(p->d_H2, (size_t)P * G);
-        QS_ALLOC(p->d_gpart, p->gpart_elems);
     }
     QS_ALLOC(p->d_flag, 1);
     QS_ALLOC(p->d_wscale, 2);
@@ -891,15 +895,18 @@ qs_status qs_grad(qs_plan p, const float* x, int64_t N, const float* w, const fl
         return fail(QS_ERR_ARG, "qs_grad: sizes outside the plan's limits");
     if ((N > 0 && !x) || (M > 0 && !y)) return fail(QS_ERR_ARG, "qs_grad: NULL point array");
     if (!gx && !gw && !gy) return QS_OK;
-    if (!p->d_gpart)
-        return fail(QS_ERR_UNSUPPORTED, "qs_grad: gradients need d <= %d (the plan has d = %d)", QS_GRAD_MAX_D,
-                    p->desc.d);
+    if (!p->d_H2)
+        return fail(QS_ERR_UNSUPPORTED, "qs_grad: the fused projection form needs d <= %d for gradients (the plan "
+                    "has d = %d); use an unfused form (FP32, BF16X3, TF32)", QS_GRAD_MAX_D, p->desc.d);
     DeviceGuard g(p->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int d = p->desc.d;
     const float scale = (float)(p->tau / (double)p->desc.P);
     // unfused plans project sources and targets with their GEMM into U first
     const bool fused = p->proj == QS_PROJ_FP32_FUSED;
+    // above QS_GRAD_MAX_D the derivative values q_{m,p} are written over the
+    // projections in U and back-projected onto the directions by a GEMM
+    const bool gemm_bp = d > QS_GRAD_MAX_D;
     cudaError_t e = cudaSuccess;
     // dL/dy_m = (tau/P) v_m sum_p xi_p sum_n w_n g'(b_{m,p} - a_{n,p}): sources x, targets y
     if (gy && M > 0) {
@@ -911,8 +918,15 @@ qs_status qs_grad(qs_plan p, const float* x, int64_t N, const float* w, const fl
             if (e == cudaSuccess && !fused) e = project(p, x, N, st);
             if (e == cudaSuccess) e = qs_launch_spread_grad(L, p->W, x, w, 1, fused, p->d_Dd, p->d_H2, st);
             if (e == cudaSuccess && !fused) e = project(p, y, M, st);
-            if (e == cudaSuccess) e = qs_launch_interp_grad(L, p->W, y, p->d_H2, p->d_dirs, p->d_gpart, fused, st);
-            if (e == cudaSuccess) e = qs_launch_reduce_grad(p->d_gpart, L.S, M, d, scale, v, gy, st);
+            if (gemm_bp) {
+                if (e == cudaSuccess) e = qs_launch_interp_deriv(L, p->W, p->d_H2, st);
+                if (e == cudaSuccess)
+                    e = qs_launch_backproj(p->d_U, p->ldU, M, p->desc.P, p->d_dirs, d, scale, v, gy, st);
+            } else {
+                if (e == cudaSuccess)
+                    e = qs_launch_interp_grad(L, p->W, y, p->d_H2, p->d_dirs, p->d_gpart, fused, st);
+                if (e == cudaSuccess) e = qs_launch_reduce_grad(p->d_gpart, L.S, M, d, scale, v, gy, st);
+            }
         }
         if (e != cudaSuccess) return cuda_fail(e, "qs_grad: gradient in y");
     }
@@ -936,11 +950,21 @@ qs_status qs_grad(qs_plan p, const float* x, int64_t N, const float* w, const fl
                     e = qs_launch_spread(L, p->W, y, v, fused, st);
             }
             if (e == cudaSuccess && !fused) e = project(p, x, N, st);
-            if (e == cudaSuccess && gx)
-                e = qs_launch_interp_grad(L, p->W, x, p->d_H2, p->d_dirs, p->d_gpart, fused, st);
-            if (e == cudaSuccess && gx) e = qs_launch_reduce_grad(p->d_gpart, L.S, N, d, scale, w, gx, st);
-            if (e == cudaSuccess && gw) e = qs_launch_interp(Lw, p->W, x, fused, st);
-            if (e == cudaSuccess && gw) e = qs_launch_reduce(Lw, gw, st);
+            if (gemm_bp) {
+                // the plain interpolation reads the projections before the
+                // derivative values overwrite them
+                if (e == cudaSuccess && gw) e = qs_launch_interp(Lw, p->W, x, fused, st);
+                if (e == cudaSuccess && gw) e = qs_launch_reduce(Lw, gw, st);
+                if (e == cudaSuccess && gx) e = qs_launch_interp_deriv(L, p->W, p->d_H2, st);
+                if (e == cudaSuccess && gx)
+                    e = qs_launch_backproj(p->d_U, p->ldU, N, p->desc.P, p->d_dirs, d, scale, w, gx, st);
+            } else {
+                if (e == cudaSuccess && gx)
+                    e = qs_launch_interp_grad(L, p->W, x, p->d_H2, p->d_dirs, p->d_gpart, fused, st);
+                if (e == cudaSuccess && gx) e = qs_launch_reduce_grad(p->d_gpart, L.S, N, d, scale, w, gx, st);
+                if (e == cudaSuccess && gw) e = qs_launch_interp(Lw, p->W, x, fused, st);
+                if (e == cudaSuccess && gw) e = qs_launch_reduce(Lw, gw, st);
+            }
         }
         if (e != cudaSuccess) return cuda_fail(e, "qs_grad: gradients in x / w");
     }

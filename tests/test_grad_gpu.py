@@ -107,11 +107,42 @@ def test_autograd_function_backward_equals_qs_grad():
             assert torch.equal(t.grad, g[name]), name
 
 
-def test_grad_rejects_large_dimension():
+# d > 32: derivative values written over the projection buffer, back-projected
+# by the GEMM (points x P)(P x d); measured errors are printed, the bar is the
+# FP32 one (TF32 projections: 10x looser)
+@pytest.mark.parametrize("kernel,kp,d,proj,tol", [("negdist", 0.0, 64, "fp32", TOL), ("gauss", 6.0, 64, "bf16x3", TOL),
+                                                  ("laplace", 0.15, 784, "bf16x3", TOL),
+                                                  ("negdist", 0.0, 40, "tf32", 10 * TOL)])
+def test_grad_large_dimension_by_back_projection_gemm(kernel, kp, d, proj, tol):
+    prob = W.tiny(d=d, N=1300, M=900, P=40, kernel=kernel, kparam=kp, n_ft=256, seed=70 + d)
+    v = np.random.default_rng(6).standard_normal(prob.M).astype(np.float32)
+    with _plan(prob, proj) as plan:
+        g = plan.grad(_cuda(prob.x), _cuda(prob.w), _cuda(prob.y), _cuda(v))
+        plan.check()
+        g = {k: t.cpu().numpy().astype(np.float64) for k, t in g.items()}
+    t = oracle.tau(prob.kernel, prob.kparam, prob.R)
+    c = oracle.coeffs(prob.kernel, prob.kparam, prob.d, t, prob.n_ft)
+    rng = np.random.default_rng(8)
+    idx_n, idx_m = rng.choice(prob.N, 100, replace=False), rng.choice(prob.M, 100, replace=False)
+    ref = oracle.o1_grad(prob.x, prob.w, prob.y, v, prob.xi, t, c, idx_n=idx_n, idx_m=idx_m)
+    k = np.arange(-prob.n_ft // 2, prob.n_ft // 2)
+    D1 = float(np.sum(np.abs(2 * np.pi * k * c)))
+    sw, mw = float(np.abs(prob.w).sum()), float(np.abs(prob.w).max())
+    sv, mv = float(np.abs(v).sum()), float(np.abs(v).max())
+    maxF = prob.R if kernel == "negdist" else 1.0
+    ey = np.max(np.abs(g["y"][idx_m] - ref["y"])) / (t * sw * mv * D1)
+    ex = np.max(np.abs(g["x"][idx_n] - ref["x"])) / (t * mw * sv * D1)
+    ew = np.max(np.abs(g["w"][idx_n] - ref["w"])) / (sv * maxF)
+    print(f"gradient d={d} {proj} {kernel}: dy {ey:.3e} dx {ex:.3e} dw {ew:.3e}")
+    assert ey < tol and ex < tol and ew < tol
+    assert np.max(np.abs(ref["y"])) / (t * sw * mv * D1) > 1e-4
+
+
+def test_grad_fused_form_rejects_large_dimension():
     from paper_2410_01316_gb300 import QSError
 
     prob = W.tiny(d=40, N=100, M=50, P=8, kernel="gauss", kparam=3.0, n_ft=64, seed=1)
-    with _plan(prob, proj="fp32") as plan:
+    with _plan(prob, proj="fp32_fused") as plan:
         with pytest.raises(QSError) as ei:
             plan.grad(_cuda(prob.x), _cuda(prob.w), _cuda(prob.y), None)
         assert ei.value.status == 6
