@@ -89,6 +89,12 @@ typedef enum {
     QS_PROJ_TF32 = 4        /* tensor-core GEMM in TF32 */
 } qs_proj;
 
+/* Window of the oversampled grid (App. C; the paper uses NFFT's default and does not name it). */
+typedef enum {
+    QS_WINDOW_ES = 0,      /* exponential of semicircle exp(beta (sqrt(1 - (v/m)^2) - 1)), beta = 2.3 W */
+    QS_WINDOW_KB = 1       /* Kaiser-Bessel, sinh form: sinh(b sqrt(m^2 - v^2)) / sqrt(m^2 - v^2), b = 3 pi / 2 */
+} qs_window_kind;
+
 typedef struct {
     int d;                 /* dimension, >= 1 */
     qs_kernel kernel;
@@ -104,6 +110,7 @@ typedef struct {
     qs_proj proj;
     int64_t max_n, max_m;  /* largest N and M the plan will be called with */
     double kparam2;        /* nu (Matern); else ignored */
+    int window_kind;       /* qs_window_kind (0 = QS_WINDOW_ES); W = 2m taps either way */
 } qs_plan_desc;
 
 /*
@@ -114,7 +121,9 @@ typedef struct {
  * closed-form transforms on the device for Gauss / Laplace / Matern / negative
  * distance; for Riesz and the thin plate spline, which have no classical
  * transform, the integrals of the periodised 1D function over one period by
- * host quadrature), the window tables, and all device workspace.  Runs on the
+ * host quadrature), the window tables (tap polynomials of the chosen window
+ * and its Fourier transform by quadrature of those polynomials), and all
+ * device workspace.  Runs on the
  * current CUDA device and synchronises it.  On success *out holds the plan.
  * Errors: QS_ERR_ARG, QS_ERR_UNSUPPORTED, QS_ERR_OOM, QS_ERR_CUDA.
  */

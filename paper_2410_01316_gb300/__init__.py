@@ -55,7 +55,7 @@ class QSPlan:
 
     def __init__(self, d: int, kernel: str, P: int, n_ft: int, radius: float, kparam: float = 0.0,
                  dirs="orthogonal", seed: int = 0, window: int = 8, proj: str = "auto",
-                 max_n: int = 0, max_m: int = 0, device=None, kparam2: float = 0.0):
+                 max_n: int = 0, max_m: int = 0, device=None, kparam2: float = 0.0, window_kind: str = "es"):
         import torch
 
         lib = _lib.load()
@@ -80,6 +80,8 @@ class QSPlan:
         desc.proj = _lib.PROJ[proj]
         desc.max_n, desc.max_m = int(max_n), int(max_m)
         desc.kparam2 = float(kparam2)
+        desc.window_kind = _lib.WINDOWS[window_kind]
+        self.window_kind = window_kind
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         with torch.cuda.device(self.device):
             _lib.check(lib.qs_plan_create(ctypes.byref(self._handle), ctypes.byref(desc)), "qs_plan_create")

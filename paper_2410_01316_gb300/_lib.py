@@ -26,6 +26,7 @@ STATUS = {
 KERNELS = {"gauss": 0, "laplace": 1, "negdist": 2, "matern": 3, "riesz": 4, "tps": 5}
 DIRS = {"user": 0, "fibonacci": 1, "orthogonal": 2, "iid": 3, "distance": 4, "sobol": 5}
 PROJ = {"auto": 0, "fp32": 1, "fp32_fused": 2, "bf16x3": 3, "tf32": 4}
+WINDOWS = {"es": 0, "kb": 1}
 
 # every symbol declared in include/qmcslice.h
 EXPORTS = ("qs_plan_create", "qs_plan_destroy", "qs_plan_info", "qs_plan_directions", "qs_sum",
@@ -42,7 +43,7 @@ class PlanDesc(ctypes.Structure):
         ("d", c_int), ("kernel", c_int), ("kparam", c_dbl), ("P", c_int), ("dirs", c_int),
         ("seed", c_u64), ("dirs_host", c_vp), ("n_ft", c_int), ("window", c_int),
         ("oversampling", c_dbl), ("radius", c_dbl), ("proj", c_int), ("max_n", c_i64), ("max_m", c_i64),
-        ("kparam2", c_dbl),
+        ("kparam2", c_dbl), ("window_kind", c_int),
     ]
 
 

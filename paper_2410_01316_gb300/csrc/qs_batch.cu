@@ -336,7 +336,8 @@ extern "C" qs_status qs_batch_create(qs_batch* out, const qs_plan* plans, int np
         const qs_plan p = plans[k];
         if (!p) return bfail(QS_ERR_ARG, "qs_batch_create: plan %d is NULL", k);
         if (p->device != dev) return bfail(QS_ERR_ARG, "qs_batch_create: plans on different devices");
-        if (p->W != plans[0]->W) return bfail(QS_ERR_UNSUPPORTED, "qs_batch_create: plans must share the window width");
+        if (p->W != plans[0]->W || p->window_kind != plans[0]->window_kind)
+            return bfail(QS_ERR_UNSUPPORTED, "qs_batch_create: plans must share the window (width and kind)");
         if (p->desc.d > QS_BATCH_MAX_D)
             return bfail(QS_ERR_UNSUPPORTED, "qs_batch_create: d = %d exceeds %d", p->desc.d, QS_BATCH_MAX_D);
         for (int j = 0; j < k; ++j)

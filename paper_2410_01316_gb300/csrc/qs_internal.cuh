@@ -111,7 +111,7 @@ struct qs_plan_s {
     qs_proj proj;         // resolved form
     double tau;
     int G, W;
-    double beta;
+    int window_kind;      // QS_WINDOW_ES / QS_WINDOW_KB
     int64_t ldU;
     int S_max;            // slice-group capacity of the partial buffer
     size_t U_elems;
@@ -249,15 +249,18 @@ __host__ __device__ inline int qs_interp_tpt(bool fused, int d, int G)
 // ---------------------------------------------------------------------------
 double qs_tau_rule(qs_kernel kernel, double kparam, double R);
 void qs_gauss_legendre(int n, double* x, double* w);
-void qs_fit_window(int W, double beta, qs_window* win);
+void qs_fit_window(int W, int kind, qs_window* win);
 double qs_window_tap(const qs_window* win, int W, int j, double s);
 void qs_window_transform(const qs_window* win, int W, int K, int G, double* out);  // out[K + 1]
 void qs_twiddles(int G, float2* out);                                               // out[G / 2]
 // Sobol' points (qs_sobol.cu): u in (0,1)^d (P x d) and the unit rows Phi^{-1}(u) / |Phi^{-1}(u)|
 qs_status qs_sobol_cube(int d, int P, uint64_t seed, double* out);
 qs_status qs_sobol_sphere(int d, int P, uint64_t seed, float* out);
-// window shape parameter of the exponential of semicircle for sigma_os = 2
-inline double qs_window_beta(int W) { return 2.30 * W; }
+// autotune cache (qs_tune.cu): tuned spread variant / SM-pair GEMM choice (-1 = not tuned) of
+// the plan's shape class (d bucket, N_ft, P bucket, projection form, W)
+struct qs_plan_s;
+bool qs_tune_lookup(const qs_plan_s* p, int* spread_variant, int* gemm_pair);
+void qs_tune_store(const qs_plan_s* p, int spread_variant, int gemm_pair);
 
 // ---------------------------------------------------------------------------
 // launchers (defined in the .cu files); return cudaSuccess or the launch error

@@ -117,12 +117,12 @@ cudaError_t scratch_address(int dev, unsigned char** out)
 
 // ---- host tables, cached per (W, G) ------------------------------------------
 // The tap polynomials, the window transform (K + 1 = G/4 + 1 values) and the
-// twiddles depend only on the window width W and the grid size G.  They are
+// twiddles depend only on the window (width W, kind) and the grid size G.  They are
 // computed by the same host code as at plan creation (qs_tables.cu), so both
 // entry points use bitwise identical tables, and kept in a few static slots
 // (no heap) so repeated calls with the same sizes do not recompute them.
 struct TableEntry {
-    int W = 0, G = 0;
+    int W = 0, G = 0, kind = -1;
     qs_window win;
     double psihat[QS_MAX_G / 4 + 1];
     float2 tw[QS_MAX_G / 2];
@@ -131,17 +131,18 @@ TableEntry g_tables[QS_NOALLOC_TABLE_CACHE];
 int g_tables_next = 0;
 
 // Caller holds g_setup_mutex.
-const TableEntry& tables_for(int W, int G)
+const TableEntry& tables_for(int W, int kind, int G)
 {
     for (auto& t : g_tables)
-        if (t.W == W && t.G == G) return t;
+        if (t.W == W && t.G == G && t.kind == kind) return t;
     TableEntry& t = g_tables[g_tables_next];
     g_tables_next = (g_tables_next + 1) % QS_NOALLOC_TABLE_CACHE;
-    qs_fit_window(W, qs_window_beta(W), &t.win);
+    qs_fit_window(W, kind, &t.win);
     qs_window_transform(&t.win, W, G / 4, G, t.psihat);
     qs_twiddles(G, t.tw);
     t.W = W;
     t.G = G;
+    t.kind = kind;
     return t;
 }
 
@@ -189,6 +190,8 @@ extern "C" qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_
     if (W != 6 && W != 8 && W != 10 && W != 12) return nfail(QS_ERR_UNSUPPORTED, "qs_sum_noalloc: bad window");
     if (D.oversampling != 0.0 && D.oversampling != 2.0)
         return nfail(QS_ERR_UNSUPPORTED, "qs_sum_noalloc: only oversampling 2 is supported");
+    if (D.window_kind != QS_WINDOW_ES && D.window_kind != QS_WINDOW_KB)
+        return nfail(QS_ERR_ARG, "qs_sum_noalloc: unknown window kind");
     if (D.proj != QS_PROJ_AUTO && D.proj != QS_PROJ_FP32_FUSED)
         return nfail(QS_ERR_UNSUPPORTED, "qs_sum_noalloc: only the fused FP32 projection is available");
     if (N < 0 || M < 0) return nfail(QS_ERR_ARG, "qs_sum_noalloc: negative size");
@@ -248,7 +251,7 @@ extern "C" qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_
         e = scratch_address(dev, &base);
         if (e != cudaSuccess)
             return nfail(QS_ERR_CUDA, "qs_sum_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        const TableEntry& tb = tables_for(W, G);
+        const TableEntry& tb = tables_for(W, D.window_kind, G);
         L.win = tb.win;
         // pageable source: each copy has been staged when the call returns, so
         // the cache slot may be reused by a later call

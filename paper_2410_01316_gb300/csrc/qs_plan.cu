@@ -431,6 +431,8 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     const int W = D.window == 0 ? 8 : D.window;
     if (W != 6 && W != 8 && W != 10 && W != 12)
         return fail(QS_ERR_UNSUPPORTED, "qs_plan_create: window must be 6, 8, 10 or 12");
+    if (D.window_kind != QS_WINDOW_ES && D.window_kind != QS_WINDOW_KB)
+        return fail(QS_ERR_ARG, "qs_plan_create: unknown window kind %d", (int)D.window_kind);
     const double os = D.oversampling == 0.0 ? 2.0 : D.oversampling;
     if (os != 2.0) return fail(QS_ERR_UNSUPPORTED, "qs_plan_create: only oversampling 2 is supported");
     if (D.max_n < 0 || D.max_m < 0) return fail(QS_ERR_ARG, "qs_plan_create: max_n / max_m must be >= 0");
@@ -470,7 +472,7 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     p->W = W;
     p->G = 2 * D.n_ft;
     p->spread_variant = qs_spread_default(p->G, W);
-    p->beta = qs_window_beta(W);
+    p->window_kind = D.window_kind;
     p->tau = qs_tau_rule(D.kernel, D.kparam, D.radius);
     p->S_max = D.P < 64 ? D.P : 64;
     const int64_t maxnm = D.max_n > D.max_m ? D.max_n : D.max_m;
@@ -515,7 +517,7 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     for (size_t i = 0; i < dirs.size(); ++i) dirs_s[i] = (float)(scale * (double)dirs[i]);
 
     // window tables
-    qs_fit_window(W, p->beta, &p->win);
+    qs_fit_window(W, p->window_kind, &p->win);
     std::vector<double> psihat(K + 1);
     qs_window_transform(&p->win, W, K, G, psihat.data());
     std::vector<float2> tw(G / 2);

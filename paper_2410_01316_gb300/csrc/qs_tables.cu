@@ -15,12 +15,22 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
-// Exponential of semicircle window psi(v) = exp(beta (sqrt(1 - (v/m)^2) - 1)) on |v| < m.
-double es_window(double v, int m, double beta)
+// The window on |v| < m = W/2 grid cells, normalised to psi(0) = 1:
+//  QS_WINDOW_ES  exponential of semicircle, psi(v) = exp(beta (sqrt(1 - (v/m)^2) - 1)), beta = 2.30 W;
+//  QS_WINDOW_KB  Kaiser-Bessel in the sinh form used by NFFT (Keiner, Kunis, Potts 2009),
+//                psi(v) = [sinh(b r) / r] / [sinh(b m) / m], r = sqrt(m^2 - v^2), b = pi (2 - 1/sigma_os)
+//                = 3 pi / 2 for sigma_os = 2 (the limit b / (sinh(b m) / m) at r = 0).
+double window_value(int kind, int m, double v)
 {
+    if (fabs(v) >= m) return 0.0;
+    if (kind == QS_WINDOW_KB) {
+        const double b = 1.5 * kPi;
+        const double r = sqrt((double)m * m - v * v);
+        const double num = r > 1e-12 ? sinh(b * r) / r : b;
+        return num / (sinh(b * m) / m);
+    }
     const double z = v / m;
-    if (fabs(z) >= 1.0) return 0.0;
-    return exp(beta * (sqrt(1.0 - z * z) - 1.0));
+    return exp(2.30 * (2 * m) * (sqrt(1.0 - z * z) - 1.0));
 }
 
 }  // namespace
@@ -64,10 +74,10 @@ void qs_gauss_legendre(int n, double* x, double* w)
     }
 }
 
-// Tap polynomials: Chebyshev interpolation of degree qs_tap_degree(W) on s in
-// [-1/2, 1/2] for each tap of the first half, converted to monomials in s and
-// split into even and odd parts.
-void qs_fit_window(int W, double beta, qs_window* win)
+// Tap polynomials of the window `kind`: Chebyshev interpolation of degree
+// qs_tap_degree(W) on s in [-1/2, 1/2] for each tap of the first half,
+// converted to monomials in s and split into even and odd parts.
+void qs_fit_window(int W, int kind, qs_window* win)
 {
     const int m = W / 2;
     const int n = qs_tap_degree(W) + 1;
@@ -89,7 +99,7 @@ void qs_fit_window(int W, double beta, qs_window* win)
         double cheb[QS_MAX_W + 2], fval[QS_MAX_W + 2], mono[QS_MAX_W + 2];
         for (int i = 0; i < n; ++i) {
             const double th = kPi * (i + 0.5) / n;
-            fval[i] = es_window(0.5 * cos(th) + m - 0.5 - j, m, beta);
+            fval[i] = window_value(kind, m, 0.5 * cos(th) + m - 0.5 - j);
         }
         for (int k = 0; k < n; ++k) {
             double acc = 0.0;

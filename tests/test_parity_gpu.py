@@ -21,15 +21,16 @@ def _norm(prob, w=True):
     return sw * (prob.R if prob.kernel == "negdist" else 1.0)
 
 
-def _plan(prob, proj, window=8, max_n=None, max_m=None):
+def _plan(prob, proj, window=8, max_n=None, max_m=None, window_kind="es"):
     return QSPlan(prob.d, prob.kernel, prob.P, prob.n_ft, prob.R, prob.kparam, dirs=prob.xi, window=window,
-                  proj=proj, max_n=prob.N if max_n is None else max_n, max_m=prob.M if max_m is None else max_m)
+                  proj=proj, max_n=prob.N if max_n is None else max_n, max_m=prob.M if max_m is None else max_m,
+                  window_kind=window_kind)
 
 
-def _gpu_sum(prob, proj, window=8, use_w=True):
+def _gpu_sum(prob, proj, window=8, use_w=True, window_kind="es"):
     import torch
 
-    with _plan(prob, proj, window) as plan:
+    with _plan(prob, proj, window, window_kind=window_kind) as plan:
         x = torch.from_numpy(prob.x).cuda()
         y = torch.from_numpy(prob.y).cuda()
         w = torch.from_numpy(prob.w).cuda() if use_w else None
@@ -64,6 +65,26 @@ def test_ragged_sizes(kernel, kp, proj):
     # 128/256, P not a multiple of the 128-slice tile, d not a multiple of 4
     prob = W.tiny(d=5, N=1037, M=301, P=131, kernel=kernel, kparam=kp, n_ft=128, seed=31)
     s, _ = _gpu_sum(prob, proj)
+    assert _err(s, _oracle(prob), prob) < TOL_FP32
+
+
+@pytest.mark.parametrize("proj", ["fp32_fused", "fp32"])
+def test_small_gauss_config_kaiser_bessel(proj):
+    # the d = 3 configuration as stated: Kaiser-Bessel window of width 8
+    prob = W.small_gauss()
+    s, _ = _gpu_sum(prob, proj, window_kind="kb")
+    err = _err(s, _oracle(prob), prob)
+    print(f"small_gauss Kaiser-Bessel W=8 {proj}: error vs oracle {err:.3e}")
+    assert err < TOL_FP32
+
+
+@pytest.mark.parametrize("window", [8, 10, 12])
+@pytest.mark.parametrize("kernel,kp", [("laplace", 2.0), ("negdist", 0.0)])
+def test_kaiser_bessel_window_widths(window, kernel, kp):
+    # W = 6 is left out: the truncated Kaiser-Bessel window jumps by b m / sinh(b m) = 2e-5 at
+    # its edge there, which is the accuracy it can reach
+    prob = W.tiny(d=4, N=700, M=200, P=24, kernel=kernel, kparam=kp, n_ft=256, seed=6)
+    s, _ = _gpu_sum(prob, "fp32_fused", window=window, window_kind="kb")
     assert _err(s, _oracle(prob), prob) < TOL_FP32
 
 

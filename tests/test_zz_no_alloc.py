@@ -31,6 +31,7 @@ def _desc(prob):
     desc.dirs, desc.seed, desc.dirs_host = _lib.DIRS["user"], 0, None
     desc.n_ft, desc.window, desc.oversampling, desc.radius = prob.n_ft, prob.window, 2.0, float(prob.R)
     desc.proj, desc.max_n, desc.max_m = _lib.PROJ["fp32_fused"], 0, 0
+    desc.window_kind = _lib.WINDOWS[getattr(prob, "window_kind", "es")]
     return desc
 
 
@@ -46,7 +47,9 @@ def _case(name):
         return W.tiny(d=16, N=3000, M=900, P=48, kernel="negdist", kparam=0.0, n_ft=512, seed=17), False
     if name.startswith("laplace_W"):
         prob = W.tiny(d=4, N=1500, M=700, P=24, kernel="laplace", kparam=1.3, n_ft=256, seed=23)
-        prob.window = int(name[len("laplace_W"):])
+        prob.window = int(name[len("laplace_W"):].split("_")[0])
+        if name.endswith("_kb"):
+            prob.window_kind = "kb"
         return prob, True
     # d <= 8 with enough targets that the slice-group count falls below its cap
     # (two targets per interpolation thread in the fused form)
@@ -54,7 +57,7 @@ def _case(name):
 
 
 @pytest.mark.parametrize("case", ["small_gauss", "negdist_d16_unit_weights", "laplace_W6", "laplace_W10",
-                                  "laplace_W12", "gauss_d6_many_targets"])
+                                  "laplace_W12", "laplace_W8_kb", "gauss_d6_many_targets"])
 def test_noalloc_matches_plan_sum_on_two_calls_in_a_row(case):
     import torch
 
@@ -63,7 +66,8 @@ def test_noalloc_matches_plan_sum_on_two_calls_in_a_row(case):
     y = torch.from_numpy(prob.y).cuda()
     w = torch.from_numpy(prob.w).cuda() if use_w else None
     with QSPlan(prob.d, prob.kernel, prob.P, prob.n_ft, prob.R, prob.kparam, dirs=prob.xi, window=prob.window,
-                proj="fp32_fused", max_n=prob.N, max_m=prob.M) as plan:
+                proj="fp32_fused", max_n=prob.N, max_m=prob.M,
+                window_kind=getattr(prob, "window_kind", "es")) as plan:
         ref = plan.sum(x, w, y)
         plan.check()
         ref = ref.cpu().numpy().astype(np.float64)
