@@ -499,10 +499,12 @@ def precision_forms(args, flush, clocks, peaks, peak_src, sm_count):
                              f"64 sampled targets (oracle {oracle_s:.1f} s)",
            "rel_err_norm": "max_m |s - s_oracle| / (sum|w| R)",
            "l2": "flushed between steps (256 MB write); inputs also exceed L2", "forms": {}}
-    steps = max(3, min(args.steps, 10))
+    steps = max(3, min(args.steps, 5))
     sampler = ClockSampler(smi_gpu_id(dev))
     sampler.start()
-    for form in ("fp32", "tf32", "bf16x3"):
+    # fp32_fused: the projections formed inside the spread and interpolation (no projection
+    # buffer in HBM), the unfused forms' alternative for d <= 64
+    for form in ("fp32", "tf32", "bf16x3", "fp32_fused"):
         with QSPlan(prob.d, prob.kernel, prob.P, prob.n_ft, prob.R, prob.kparam, dirs=prob.xi, window=prob.window,
                     proj=form, max_n=prob.N, max_m=prob.M) as plan:
             variant = plan.autotune(x, w)
@@ -533,8 +535,13 @@ def precision_forms(args, flush, clocks, peaks, peak_src, sm_count):
             sp.check()
             err = float(np.max(np.abs(s.cpu().numpy().astype(np.float64)[idx] - ref))) / norm
         t = sum(ms) / len(ms)
+        # HBM bytes the form must move: inputs and output, plus, unfused, the projection buffer
+        # written by the GEMM and read by the spread and interpolation (4 B per point-slice each way)
+        io = 4.0 * ((prob.N + prob.M) * prob.d + prob.N + prob.M)
+        u_rt = 0.0 if form == "fp32_fused" else 8.0 * (prob.N + prob.M) * prob.P
         out["forms"][form] = {
             "ms_per_step": t, "value": prob.point_slices / (t / 1e3) / 1e9, "unit": UNIT,
+            "hbm_bytes_inputs_outputs": io, "hbm_bytes_projection_round_trip": u_rt,
             "rel_err_vs_oracle": err, "steps": steps, "spread_variant": variant, "gemm": gemm,
             "device_status": int(status), "stage_ms": {k: round(v, 4) for k, v in stages.items()},
             "stage_rooflines": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()
@@ -549,8 +556,9 @@ def precision_forms(args, flush, clocks, peaks, peak_src, sm_count):
 
 def small_gauss_latency(args):
     """The small d = 3 workload (N = M = 1000, Gauss sigma = 0.5, P = 64 spherical
-    Fibonacci, N_ft = 256, fused FP32 projection): launch-bound, so reported as
-    microseconds per call, directly and as a CUDA-graph replay of one call."""
+    Fibonacci, N_ft = 256, Kaiser-Bessel window of width 8, fused FP32 projection):
+    launch-bound, so reported as microseconds per call, directly and as a
+    CUDA-graph replay of one call."""
     import torch
 
     from paper_2410_01316_gb300 import QSPlan
@@ -563,7 +571,7 @@ def small_gauss_latency(args):
     s = torch.empty(prob.M, dtype=torch.float32, device=dev)
     reps = 200
     with QSPlan(prob.d, prob.kernel, prob.P, prob.n_ft, prob.R, prob.kparam, dirs=prob.xi, window=prob.window,
-                proj="fp32_fused", max_n=prob.N, max_m=prob.M) as plan:
+                proj="fp32_fused", max_n=prob.N, max_m=prob.M, window_kind="kb") as plan:
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
@@ -594,8 +602,7 @@ def small_gauss_latency(args):
     err, desc = error_vs_oracle(prob, s, prob.M)
     return {"workload": workload_desc(prob, "fp32_fused"), "us_per_call": direct_us, "us_per_graph_replay": graph_us,
             "calls": reps, "launches_per_call": 4, "rel_err_vs_oracle": err, "rel_err_sample": desc,
-            "window": "exponential of semicircle, W = 8 taps (in place of Kaiser-Bessel; same width, "
-                      "the oracle has no window)"}
+            "window": "Kaiser-Bessel, W = 8 taps (the oracle has no window)"}
 
 
 def run_gpu_compare(args, rank, world, local_rank):
@@ -924,25 +931,37 @@ def run_batch(args, rank, world, local_rank):
     batch = QSBatch(plans)
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
-    # tune the interpolation tiling (results are bitwise identical across tilings)
-    best = None
     with torch.cuda.stream(stream):
-        for tpt in (1, 2, 4):
-            batch.set_tiling(tpt)
-            batch.sum(data, stream=stream)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            batch.sum(data, stream=stream)
-            e1.record(stream)
-            e1.synchronize()
-            t = e0.elapsed_time(e1)
-            if best is None or t < best[1]:
-                best = (tpt, t)
-        batch.set_tiling(best[0])
-        g = torch.cuda.CUDAGraph()
+        # the library's tuner picks the mode (persistent kernel or concurrent per-problem
+        # pipelines) and the persistent kernel's interpolation tiling
+        best_tpt = batch.autotune(data, stream=stream)
         batch.sum(data, stream=stream)
         torch.cuda.synchronize()
+        # both modes timed for the record (graph replays of one call each)
+        mode_ms = {}
+        for name, conc in (("persistent", False), ("concurrent", True)):
+            batch.set_mode(conc)
+            if not conc:
+                batch.set_tiling(best_tpt if best_tpt else 4)
+            gm = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gm, stream=stream):
+                batch.sum(data, stream=stream)
+            gm.replay()
+            tm = []
+            for _ in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                gm.replay()
+                e1.record(stream)
+                e1.synchronize()
+                tm.append(e0.elapsed_time(e1))
+            mode_ms[name] = min(tm)
+            del gm
+        batch.set_mode(best_tpt == 0)
+        if best_tpt:
+            batch.set_tiling(best_tpt)
+        g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
             batch.sum(data, stream=stream)
     for _ in range(args.warmup):
@@ -976,14 +995,47 @@ def run_batch(args, rank, world, local_rank):
         e1.synchronize()
         seq.append(e0.elapsed_time(e1))
     t = sum(ms) / len(ms)
+    # per-problem ideal: the problem's point-slices at the throughput one GPU-filling problem of its
+    # d class reaches (N = M = 1e5, P = 256, N_ft = 512, the same projection form), summed
+    rate_big = {}
+    for dd in sorted({p.d for p in probs}):
+        big = W.tiny(d=dd, N=100000, M=100000, P=256, kernel="gauss", kparam=1.5 * math.sqrt(dd), n_ft=512,
+                     seed=77 + dd, dirs="fibonacci" if dd == 3 else "orthogonal")
+        xb, wb, yb = (torch.from_numpy(a).to(dev) for a in (big.x, big.w, big.y))
+        sb = torch.empty(big.M, device=dev)
+        with QSPlan(big.d, big.kernel, big.P, big.n_ft, big.R, big.kparam, dirs=big.xi, proj="auto", max_n=big.N,
+                    max_m=big.M) as bp:
+            bp.autotune(xb, wb)
+            for _ in range(3):
+                bp.sum(xb, wb, yb, out=sb)
+            tb = []
+            for _ in range(5):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                bp.sum(xb, wb, yb, out=sb)
+                e1.record()
+                e1.synchronize()
+                tb.append(e0.elapsed_time(e1))
+        rate_big[dd] = big.point_slices / (min(tb) / 1e3)
+    ideal_ms = 1e3 * sum(p.point_slices / rate_big[p.d] for p in probs)
     line = {"metric": METRIC, "value": ps / (t / 1e3) / 1e9, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch256: 256 Gauss problems, N, M log-uniform in [1e3, 1e5], d in {3,16,64}, "
-                                   "N_ft in {256,512,1024}, P=256, one persistent graph-captured launch",
-                       "point_slices": ps, "interp_targets_per_thread": best[0],
+                                   "N_ft in {256,512,1024}, P=256, one graph-captured qs_sum_batched call",
+                       "point_slices": ps,
+                       "mode": "concurrent per-problem pipelines on 8 streams" if best_tpt == 0 else
+                               f"persistent kernel, {best_tpt} targets per thread",
+                       "mode_ms": mode_ms,
                        "sequential_qs_sum_ms": min(seq),
                        "speedup_vs_sequential": min(seq) / t,
+                       "ideal_ms": ideal_ms, "persistent_efficiency": ideal_ms / t,
+                       "efficiency_definition": "sum over problems of point-slices / the Gpoint-slices/s of one "
+                                                "GPU-filling problem of the same d (N = M = 1e5, P = 256, N_ft = 512), "
+                                                "divided by the measured batched time",
+                       "big_problem_gps": {str(k): v / 1e9 for k, v in rate_big.items()},
                        "l2": "flushed between steps"},
             "clocks": clocks, "gpu_launches": args.steps}
     if rank == 0:

@@ -305,9 +305,10 @@ qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_dev, const 
  * d <= 64, P, N_ft, kernel and directions; all plans must share the window
  * width), run in ONE persistent launch that drains a queue of
  * (problem, slice) spread items followed by (problem, target block)
- * interpolation items, largest problems first.  Projections are FP32 dot
- * products inside the items.  Each target's slice sum is formed in slice
- * order by one thread, so results do not depend on the tiling.
+ * interpolation items, largest problems first.  Projections are FP32: SIMT
+ * GEMM tile items before the spread items for d > 4, dot products inside the
+ * items for d <= 4.  Each target's slice sum is formed in slice order by one
+ * thread, so results do not depend on the tiling.
  *
  * qs_batch_create: plans are borrowed (they must outlive the batch); their
  *   workspaces hold the intermediate grids.  Allocates the batch's
@@ -337,6 +338,28 @@ qs_status qs_batch_destroy(qs_batch batch);
 qs_status qs_sum_batched(qs_batch batch, const qs_problem* probs, void* stream);
 qs_status qs_batch_check(qs_batch batch, void* stream);
 qs_status qs_batch_set_tiling(qs_batch batch, int targets_per_thread);
+/*
+ * Execution mode of qs_sum_batched.  QS_BATCH_PERSISTENT (the default): the
+ * one persistent launch described above.  QS_BATCH_CONCURRENT: every problem
+ * runs its own plan's qs_sum pipeline (the plan's projection form, spread
+ * family and interpolation) on one of 8 streams owned by the batch, problems
+ * assigned largest first to the least-loaded stream; the streams are forked
+ * from and joined to `stream`, so the call is ordered on `stream` and can be
+ * captured into a CUDA graph.  Each problem's result is then bit for bit
+ * that of qs_sum on its plan.  QS_ERR_ARG for other values.
+ */
+typedef enum { QS_BATCH_PERSISTENT = 0, QS_BATCH_CONCURRENT = 1 } qs_batch_mode;
+qs_status qs_batch_set_mode(qs_batch batch, int mode);
+/*
+ * Time qs_sum_batched on these problems in the persistent mode with 1, 2 and
+ * 4 targets per thread of the interpolation items and in the concurrent mode
+ * (best of two after a warm-up, CUDA events on `stream`), keep the fastest in
+ * the batch and write it to *chosen (may be NULL): 1, 2 or 4 for the
+ * persistent kernel with that tiling, 0 for the concurrent mode.  The tilings
+ * give bitwise identical results; the modes differ within the sums'
+ * accuracy.  Synchronous; the problems' outputs are written (several times).
+ */
+qs_status qs_batch_autotune(qs_batch batch, const qs_problem* probs, int* chosen, void* stream);
 
 /*
  * Tuning.  The spread stage has variants in two families, fixed by the grid
@@ -354,6 +377,28 @@ qs_status qs_batch_set_tiling(qs_batch batch, int targets_per_thread);
  * (QS_ERR_ARG if out of range or of the other family).
  */
 qs_status qs_plan_autotune(qs_plan plan, const float* x, int64_t N, const float* w, int* chosen, void* stream);
+/*
+ * Projection GEMM form by timing (tensor-core plans): runs the projection of
+ * the N points in x (device, N x d) with one CTA per SM and, where two-CTA
+ * clusters can be resident, on SM pairs (best of 3 after a warm-up, CUDA
+ * events on `stream`) and keeps the faster (*chosen = pair, may be NULL).
+ * Unlike the spread variants, the two forms may differ in the last bits of
+ * the projections (the tensor cores' internal accumulation order; both stay
+ * within the rounding bound of the form).  Synchronous.  QS_ERR_UNSUPPORTED
+ * for plans without a tensor-core projection.
+ *
+ * Autotune cache: qs_plan_autotune and qs_plan_autotune_gemm record their
+ * choice under the plan's shape class (d rounded up to a power of two, N_ft,
+ * P rounded up to a power of two, projection form, window width); plans
+ * created later in the process for the same class start with the recorded
+ * choices.  The cache can be written to and read from a text file, cleared,
+ * and queried for its number of entries.
+ */
+qs_status qs_plan_autotune_gemm(qs_plan plan, const float* x, int64_t N, int* chosen, void* stream);
+qs_status qs_tune_cache_save(const char* path);
+qs_status qs_tune_cache_load(const char* path);
+qs_status qs_tune_cache_clear(void);
+int qs_tune_cache_size(void);
 qs_status qs_plan_set_variant(qs_plan plan, int spread_variant);
 /* Variants of the plan's family (bit v of *available set for variant v) and
  * the variant in use (*current); either pointer may be NULL.  Host only. */

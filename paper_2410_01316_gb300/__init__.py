@@ -19,7 +19,8 @@ from . import _lib
 from ._lib import QSError
 
 __all__ = ["QSPlan", "QSBatch", "QSError", "KernelSumFn", "directions", "sobol_points", "kernel_sum", "version",
-           "distance_design", "distance_energy"]
+           "distance_design", "distance_energy", "tune_cache_save", "tune_cache_load", "tune_cache_clear",
+           "tune_cache_size"]
 
 
 def version() -> str:
@@ -40,6 +41,24 @@ def sobol_points(d: int, P: int, seed: int = 0) -> np.ndarray:
     out = np.empty((P, d), dtype=np.float64)
     _lib.check(_lib.load().qs_sobol_points(d, P, seed, out.ctypes.data_as(ctypes.c_void_p)), "qs_sobol_points")
     return out
+
+
+def tune_cache_save(path: str) -> None:
+    """Write the library's autotune cache (tuned choices per shape class) to a text file."""
+    _lib.check(_lib.load().qs_tune_cache_save(path.encode()), "qs_tune_cache_save")
+
+
+def tune_cache_load(path: str) -> None:
+    """Merge a saved autotune cache into the library's cache."""
+    _lib.check(_lib.load().qs_tune_cache_load(path.encode()), "qs_tune_cache_load")
+
+
+def tune_cache_clear() -> None:
+    _lib.check(_lib.load().qs_tune_cache_clear(), "qs_tune_cache_clear")
+
+
+def tune_cache_size() -> int:
+    return int(_lib.load().qs_tune_cache_size())
 
 
 def _stream_handle(stream) -> int:
@@ -128,6 +147,14 @@ class QSPlan:
                                               None if w is None else w.data_ptr(), ctypes.byref(v),
                                               _stream_handle(stream)), "qs_plan_autotune")
         return self.SPREAD_VARIANTS[v.value]
+
+    def autotune_gemm(self, x, stream=None) -> bool:
+        """Time the projection GEMM forms on these points and keep the faster; True for SM pairs."""
+        self._check_points(x, "x")
+        v = ctypes.c_int(-1)
+        _lib.check(self._lib.qs_plan_autotune_gemm(self._handle, x.data_ptr(), x.shape[0], ctypes.byref(v),
+                                                   _stream_handle(stream)), "qs_plan_autotune_gemm")
+        return v.value == 1
 
     def set_variant(self, name: str) -> None:
         _lib.check(self._lib.qs_plan_set_variant(self._handle, self.SPREAD_VARIANTS.index(name)),
@@ -322,8 +349,26 @@ class QSBatch:
     def set_tiling(self, targets_per_thread: int) -> None:
         _lib.check(self._lib.qs_batch_set_tiling(self._handle, targets_per_thread), "qs_batch_set_tiling")
 
+    def set_mode(self, concurrent: bool) -> None:
+        """Persistent kernel (False, default) or every problem's own pipeline on the batch's streams."""
+        _lib.check(self._lib.qs_batch_set_mode(self._handle, 1 if concurrent else 0), "qs_batch_set_mode")
+
+    def autotune(self, problems, stream=None) -> int:
+        """Time the persistent kernel's interpolation tilings (1, 2, 4 targets per thread) and the
+        concurrent mode on these problems and keep the fastest; returns the tiling, or 0 for the
+        concurrent mode."""
+        self._fill(problems)
+        v = ctypes.c_int(-1)
+        _lib.check(self._lib.qs_batch_autotune(self._handle, self._probs, ctypes.byref(v), _stream_handle(stream)),
+                   "qs_batch_autotune")
+        return v.value
+
     def sum(self, problems, stream=None):
         """problems: list of (x, w, y, out) CUDA tensors (w may be None), one per plan."""
+        self._fill(problems)
+        _lib.check(self._lib.qs_sum_batched(self._handle, self._probs, _stream_handle(stream)), "qs_sum_batched")
+
+    def _fill(self, problems):
         if len(problems) != len(self.plans):
             raise ValueError("one problem per plan")
         for k, (x, w, y, out) in enumerate(problems):
@@ -335,7 +380,6 @@ class QSBatch:
                 pl._check_points(w, "w", rows=x.shape[0])
             self._probs[k] = _lib.Problem(x.data_ptr(), x.shape[0], None if w is None else w.data_ptr(),
                                           y.data_ptr(), y.shape[0], out.data_ptr())
-        _lib.check(self._lib.qs_sum_batched(self._handle, self._probs, _stream_handle(stream)), "qs_sum_batched")
 
     def check(self, stream=None) -> None:
         _lib.check(self._lib.qs_batch_check(self._handle, _stream_handle(stream)), "qs_batch_check")

@@ -35,7 +35,8 @@ EXPORTS = ("qs_plan_create", "qs_plan_destroy", "qs_plan_info", "qs_plan_directi
            "qs_plan_autotune", "qs_plan_set_variant", "qs_batch_create", "qs_batch_destroy", "qs_sum_batched",
            "qs_batch_check", "qs_batch_set_tiling", "qs_plan_variants", "qs_distance_design",
            "qs_distance_energy", "qs_sum_sorted", "qs_grad_sorted", "qs_plan_set_gemm", "qs_plan_gemm",
-           "qs_sobol_points")
+           "qs_sobol_points", "qs_batch_autotune", "qs_plan_autotune_gemm", "qs_tune_cache_save",
+           "qs_tune_cache_load", "qs_tune_cache_clear", "qs_tune_cache_size", "qs_batch_set_mode")
 
 
 class PlanDesc(ctypes.Structure):
@@ -82,6 +83,13 @@ def load() -> ctypes.CDLL:
         lib.qs_last_error.restype = c_char_p
         lib.qs_directions.argtypes = [c_int, c_int, c_int, c_u64, c_vp]
         lib.qs_sobol_points.argtypes = [c_int, c_int, c_u64, c_vp]
+        lib.qs_batch_set_mode.argtypes = [c_vp, c_int]
+        lib.qs_batch_autotune.argtypes = [c_vp, ctypes.POINTER(Problem), ctypes.POINTER(c_int), c_vp]
+        lib.qs_plan_autotune_gemm.argtypes = [c_vp, c_vp, c_i64, ctypes.POINTER(c_int), c_vp]
+        lib.qs_tune_cache_save.argtypes = [c_char_p]
+        lib.qs_tune_cache_load.argtypes = [c_char_p]
+        lib.qs_tune_cache_clear.argtypes = []
+        lib.qs_tune_cache_size.argtypes = []
         lib.qs_project.argtypes = [c_vp, c_vp, c_i64, c_vp, c_i64, c_vp]
         lib.qs_batch_create.argtypes = [ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_int]
         lib.qs_batch_destroy.argtypes = [c_vp]
@@ -108,7 +116,9 @@ def load() -> ctypes.CDLL:
                      "qs_sum_noalloc", "qs_grad", "qs_plan_autotune", "qs_plan_set_variant",
                      "qs_batch_create", "qs_batch_destroy", "qs_sum_batched", "qs_batch_check",
                      "qs_batch_set_tiling", "qs_plan_variants", "qs_distance_design", "qs_distance_energy",
-                     "qs_sum_sorted", "qs_grad_sorted", "qs_plan_set_gemm", "qs_plan_gemm", "qs_sobol_points"):
+                     "qs_sum_sorted", "qs_grad_sorted", "qs_plan_set_gemm", "qs_plan_gemm", "qs_sobol_points",
+                     "qs_batch_autotune", "qs_plan_autotune_gemm", "qs_tune_cache_save", "qs_tune_cache_load",
+                     "qs_tune_cache_clear", "qs_tune_cache_size", "qs_batch_set_mode"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib

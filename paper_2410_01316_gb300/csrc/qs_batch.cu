@@ -323,6 +323,12 @@ struct qs_batch_s {
     BatchDesc* d_desc;
     unsigned long long* d_counter;
     unsigned int* d_done;   // 3 counters per problem
+    // concurrent mode: every problem's own pipeline (qs_sum) on one of the
+    // batch's streams, forked from and joined to the caller's stream
+    int mode;               // QS_BATCH_PERSISTENT or QS_BATCH_CONCURRENT
+    cudaStream_t st[QS_BATCH_STREAMS];
+    cudaEvent_t fork_ev;
+    cudaEvent_t join_ev[QS_BATCH_STREAMS];
 };
 
 extern "C" qs_status qs_batch_destroy(qs_batch b);
@@ -361,6 +367,12 @@ extern "C" qs_status qs_batch_create(qs_batch* out, const qs_plan* plans, int np
     b->d_desc = nullptr;
     b->d_counter = nullptr;
     b->d_done = nullptr;
+    b->mode = QS_BATCH_PERSISTENT;
+    b->fork_ev = nullptr;
+    for (int i = 0; i < QS_BATCH_STREAMS; ++i) {
+        b->st[i] = nullptr;
+        b->join_ev[i] = nullptr;
+    }
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(dev);
@@ -369,6 +381,11 @@ extern "C" qs_status qs_batch_create(qs_batch* out, const qs_plan* plans, int np
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_done, sizeof(unsigned int) * 3 * nprob);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+    for (int i = 0; i < QS_BATCH_STREAMS && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&b->st[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev[i], cudaEventDisableTiming);
+    }
     for (int k = 0; k < nprob && e == cudaSuccess; ++k) {
         const qs_plan p = plans[k];
         if (p->desc.d <= FUSED_MAX_D) continue;
@@ -399,12 +416,25 @@ extern "C" qs_status qs_batch_destroy(qs_batch b)
     if (b->d_counter) cudaFree(b->d_counter);
     if (b->d_done) cudaFree(b->d_done);
     if (b->uploaded) cudaEventDestroy(b->uploaded);
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    for (int i = 0; i < QS_BATCH_STREAMS; ++i) {
+        if (b->st[i]) cudaStreamDestroy(b->st[i]);
+        if (b->join_ev[i]) cudaEventDestroy(b->join_ev[i]);
+    }
     for (float* u : b->Ux)
         if (u) cudaFree(u);
     for (float* u : b->Uy)
         if (u) cudaFree(u);
     cudaSetDevice(prev);
     delete b;
+    return QS_OK;
+}
+
+extern "C" qs_status qs_batch_set_mode(qs_batch b, int mode)
+{
+    if (!b || (mode != QS_BATCH_PERSISTENT && mode != QS_BATCH_CONCURRENT))
+        return bfail(QS_ERR_ARG, "qs_batch_set_mode: bad value");
+    b->mode = mode;
     return QS_OK;
 }
 
@@ -416,6 +446,42 @@ extern "C" qs_status qs_batch_set_tiling(qs_batch b, int tpt_cap)
 }
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// Concurrent mode: problems, largest first, each go to the batch stream with
+// the least work queued so far (longest-processing-time list scheduling by
+// (N + M) P) and run their own plan's qs_sum there; the streams wait for the
+// work already on `stream` and `stream` waits for all of them, so the call is
+// ordered like any other on `stream` and can be captured into a CUDA graph
+// (the fork and join become graph dependencies).
+static qs_status batched_concurrent(qs_batch b, const qs_problem* probs, const std::vector<int>& order,
+                                    cudaStream_t stream)
+{
+    double load[QS_BATCH_STREAMS] = {0.0};
+    bool used[QS_BATCH_STREAMS] = {false};
+    cudaError_t e = cudaEventRecord(b->fork_ev, stream);
+    for (size_t i = 0; i < order.size() && e == cudaSuccess; ++i) {
+        const int k = order[i];
+        const qs_problem& q = probs[k];
+        int si = 0;
+        for (int j = 1; j < QS_BATCH_STREAMS; ++j)
+            if (load[j] < load[si]) si = j;
+        if (!used[si]) {
+            e = cudaStreamWaitEvent(b->st[si], b->fork_ev, 0);
+            if (e != cudaSuccess) break;
+            used[si] = true;
+        }
+        load[si] += (double)(q.N + q.M) * b->plans[k]->desc.P + 1e6;  // + a launch-overhead term
+        const qs_status s = qs_sum(b->plans[k], q.x, q.N, q.w, q.y, q.M, q.s, b->st[si]);
+        if (s != QS_OK) return s;
+    }
+    for (int j = 0; j < QS_BATCH_STREAMS && e == cudaSuccess; ++j) {
+        if (!used[j]) continue;
+        e = cudaEventRecord(b->join_ev[j], b->st[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, b->join_ev[j], 0);
+    }
+    if (e != cudaSuccess) return bfail(QS_ERR_CUDA, "qs_sum_batched: %s", cudaGetErrorString(e));
+    return QS_OK;
+}
 
 extern "C" qs_status qs_sum_batched(qs_batch b, const qs_problem* probs, void* stream)
 {
@@ -432,6 +498,12 @@ extern "C" qs_status qs_sum_batched(qs_batch b, const qs_problem* probs, void* s
         order[k] = k;
     }
     // queue order: largest problems first
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        const double wa = (double)(probs[a].N + probs[a].M) * b->plans[a]->desc.P;
+        const double wc = (double)(probs[c].N + probs[c].M) * b->plans[c]->desc.P;
+        return wa > wc;
+    });
+    if (b->mode == QS_BATCH_CONCURRENT) return batched_concurrent(b, probs, order, (cudaStream_t)stream);
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
         const double wa = (double)(probs[a].N + probs[a].M) * b->plans[a]->desc.P;
         const double wc = (double)(probs[c].N + probs[c].M) * b->plans[c]->desc.P;
@@ -539,4 +611,56 @@ extern "C" qs_status qs_batch_check(qs_batch b, void* stream)
         if (s != QS_OK && (worst == QS_OK || s == QS_ERR_CUDA || s == QS_ERR_TIMEOUT)) worst = s;
     }
     return worst;
+}
+
+// Time the batched sum of these problems with the persistent kernel at each
+// interpolation tiling (1, 2 and 4 targets per thread) and in the concurrent
+// mode (best of two after a warm-up, CUDA events on `stream`) and keep the
+// fastest.  The tilings give the same bits; the concurrent mode gives each
+// plan's own qs_sum result.
+extern "C" qs_status qs_batch_autotune(qs_batch b, const qs_problem* probs, int* chosen, void* stream)
+{
+    if (!b || !probs) return bfail(QS_ERR_ARG, "qs_batch_autotune: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return bfail(QS_ERR_CUDA, "qs_batch_autotune: event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return bfail(QS_ERR_CUDA, "qs_batch_autotune: event");
+    }
+    const int keep = b->tpt_cap, keep_mode = b->mode;
+    int best = keep_mode == QS_BATCH_CONCURRENT ? 0 : keep;
+    float best_ms = 3.4e38f;
+    qs_status s = QS_OK;
+    // tpt 1, 2, 4: the persistent kernel with that tiling; 0 (tried last): concurrent pipelines
+    for (int tpt = 1; tpt <= 8 && s == QS_OK; tpt *= 2) {
+        b->mode = tpt == 8 ? QS_BATCH_CONCURRENT : QS_BATCH_PERSISTENT;
+        if (tpt < 8) b->tpt_cap = tpt;
+        s = qs_sum_batched(b, probs, stream);  // warm-up
+        float tb = 3.4e38f;
+        for (int r = 0; r < 2 && s == QS_OK; ++r) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) s = QS_ERR_CUDA;
+            if (s == QS_OK) s = qs_sum_batched(b, probs, stream);
+            if (s == QS_OK && cudaEventRecord(e1, st) != cudaSuccess) s = QS_ERR_CUDA;
+            float ms = 0.0f;
+            if (s == QS_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                s = QS_ERR_CUDA;
+            if (s == QS_OK && ms < tb) tb = ms;
+        }
+        if (s == QS_OK && tb < best_ms) {
+            best_ms = tb;
+            best = tpt == 8 ? 0 : tpt;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != QS_OK) {
+        b->tpt_cap = keep;
+        b->mode = keep_mode;
+        return s == QS_ERR_CUDA ? bfail(QS_ERR_CUDA, "qs_batch_autotune: timing failed") : s;
+    }
+    b->mode = best == 0 ? QS_BATCH_CONCURRENT : QS_BATCH_PERSISTENT;
+    b->tpt_cap = best == 0 ? keep : best;
+    if (chosen) *chosen = best;
+    return QS_OK;
 }

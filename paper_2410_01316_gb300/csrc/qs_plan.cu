@@ -669,6 +669,15 @@ qs_status qs_plan_create(qs_plan* out, const qs_plan_desc* desc)
     }
     QS_CHECK(cudaDeviceSynchronize(), "coefficient kernel");
 #undef QS_CHECK
+    // choices tuned earlier for this shape class (autotune cache)
+    {
+        int tv = -1, tp = -1;
+        if (qs_tune_lookup(p, &tv, &tp)) {
+            if (tv >= 0 && qs_spread_variant_ok(G, W, tv)) p->spread_variant = tv;
+            if (tp >= 0 && tc && (tp == 0 || qs_tc_pair_available(proj == QS_PROJ_BF16X3 ? 0 : 1)))
+                p->gemm_pair = tp == 1;
+        }
+    }
     *out = p;
     g_last_error[0] = 0;
     return QS_OK;
@@ -1065,6 +1074,58 @@ qs_status qs_plan_autotune(qs_plan p, const float* x, int64_t N, const float* w,
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail(e, "qs_plan_autotune: timing");
     p->spread_variant = best;
+    qs_tune_store(p, best, -1);
+    if (chosen) *chosen = best;
+    return QS_OK;
+}
+
+qs_status qs_plan_autotune_gemm(qs_plan p, const float* x, int64_t N, int* chosen, void* stream)
+{
+    if (!p) return fail(QS_ERR_ARG, "qs_plan_autotune_gemm: NULL plan");
+    if (N <= 0 || N > (p->desc.max_n > p->desc.max_m ? p->desc.max_n : p->desc.max_m) || !x)
+        return fail(QS_ERR_ARG, "qs_plan_autotune_gemm: need 0 < N <= max(max_n, max_m) points");
+    if (p->proj != QS_PROJ_BF16X3 && p->proj != QS_PROJ_TF32)
+        return fail(QS_ERR_UNSUPPORTED, "qs_plan_autotune_gemm: the plan has no tensor-core projection");
+    DeviceGuard g(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool pair_ok = qs_tc_pair_available(p->proj == QS_PROJ_BF16X3 ? 0 : 1);
+    const bool keep = p->gemm_pair;
+    cudaError_t e = project_prep(p, x, N, st);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_plan_autotune_gemm: operand split");
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return fail(QS_ERR_CUDA, "qs_plan_autotune_gemm: event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(QS_ERR_CUDA, "qs_plan_autotune_gemm: event");
+    }
+    int best = keep ? 1 : 0;
+    float best_ms = 3.4e38f;
+    for (int pair = 0; pair <= (pair_ok ? 1 : 0) && e == cudaSuccess; ++pair) {
+        p->gemm_pair = pair == 1;
+        e = project_gemm(p, x, N, st);  // warm-up
+        float vbest = 3.4e38f;
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+            cudaEventRecord(e0, st);
+            e = project_gemm(p, x, N, st);
+            cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < vbest) vbest = ms;
+        }
+        if (vbest < best_ms) {
+            best_ms = vbest;
+            best = pair;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        p->gemm_pair = keep;
+        return cuda_fail(e, "qs_plan_autotune_gemm: timing");
+    }
+    p->gemm_pair = best == 1;
+    qs_tune_store(p, -1, best);
     if (chosen) *chosen = best;
     return QS_OK;
 }

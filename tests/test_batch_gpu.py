@@ -122,3 +122,45 @@ def test_batch_rejects_repeated_plan():
     plan = QSPlan(p.d, p.kernel, p.P, p.n_ft, p.R, p.kparam, dirs=p.xi, proj="fp32_fused", max_n=p.N, max_m=p.M)
     with pytest.raises(QSError):
         QSBatch([plan, plan])
+
+
+@pytest.mark.parametrize("proj", ["fp32_fused", "auto"])
+def test_concurrent_mode_equals_each_plans_sum_and_replays_in_a_graph(proj):
+    # the concurrent mode runs each plan's own qs_sum on the batch's streams: bit for bit that
+    # sum, also when the forked call is captured into a CUDA graph and replayed
+    import torch
+
+    probs = _problems()
+    plans = [QSPlan(p.d, p.kernel, p.P, p.n_ft, p.R, p.kparam, dirs=p.xi, proj=proj, max_n=max(p.N, 1), max_m=p.M)
+             for p in probs]
+    _, data = _setup(probs)
+    refs = []
+    for plan, (x, w, y, _) in zip(plans, data):
+        refs.append(plan.sum(x, w, y).cpu().numpy())
+    batch = QSBatch(plans)
+    batch.set_mode(True)
+    batch.sum(data)
+    batch.check()
+    for p, r, (_, _, _, out) in zip(probs, refs, data):
+        got = out.cpu().numpy()
+        assert np.array_equal(got, r)
+        if p.N:
+            assert np.max(np.abs(got.astype(np.float64) - oracle.o1_problem(p))) / _norm(p) < TOL
+    for (_, _, _, out) in data:
+        out.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            batch.sum(data, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        for r, (_, _, _, out) in zip(refs, data):
+            assert np.array_equal(r, out.cpu().numpy())
+    batch.check()
+    batch.close()
+    for pl in plans:
+        pl.close()
