@@ -143,15 +143,109 @@ __global__ void __launch_bounds__(256) esym_step_kernel(float* __restrict__ xi, 
     for (int j = threadIdx.x; j < d; j += blockDim.x) x[j] *= inv;
 }
 
+// Split-K form of the second contraction Gm[p][j] = sum_q W[p][q] T[j][q]
+// (W the P x ldc weights, T = Xi^T padded to ldc columns): its P x d output
+// has few 128 x 128 tiles (80 at P = 5000, d = 200) for a long inner length,
+// so CTA (p tile, j tile, z) sums the inner range [z kc, (z + 1) kc) into its
+// own partial (parts[z], P x ldg) with the FP32 SIMT tile of the projection
+// (8 x 8 outputs per thread, 8-deep slabs double-buffered in shared memory),
+// and gm_reduce_kernel adds the partials in z order, so the result does not
+// depend on scheduling.  kc is a multiple of the slab depth.
+constexpr int SK_BM = 128, SK_BN = 128, SK_BK = 8;
+
+__global__ void __launch_bounds__(256) gm_splitk_kernel(const float* __restrict__ Wt, int P, int64_t ldc,
+                                                        const float* __restrict__ T, int d, int64_t kc,
+                                                        float* __restrict__ parts, int64_t ldg)
+{
+    __shared__ __align__(16) float As[2][SK_BK][SK_BM];
+    __shared__ __align__(16) float Bs[2][SK_BK][SK_BN];
+    const int p0 = blockIdx.x * SK_BM, j0 = blockIdx.y * SK_BN;
+    const int64_t k0 = (int64_t)blockIdx.z * kc;
+    const int64_t k1 = k0 + kc < ldc ? k0 + kc : ldc;
+    float* out = parts + (size_t)blockIdx.z * (size_t)P * ldg;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int lrow = tid >> 1, lk = (tid & 1) * 4;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    // slab loads: row lrow of the W tile and of the T tile, 4 consecutive inner indices from k + lk
+    auto load = [&](int64_t k, float (&ra)[4], float (&rb)[4]) {
+        const int gp = p0 + lrow, gj = j0 + lrow;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t kk = k + lk + i;
+            ra[i] = (gp < P && kk < k1) ? __ldg(&Wt[(size_t)gp * ldc + kk]) : 0.0f;
+            rb[i] = (gj < d && kk < k1) ? __ldg(&T[(size_t)gj * ldc + kk]) : 0.0f;
+        }
+    };
+    float ra[4], rb[4];
+    load(k0, ra, rb);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        As[0][lk + i][lrow] = ra[i];
+        Bs[0][lk + i][lrow] = rb[i];
+    }
+    __syncthreads();
+    const int nk = (int)((k1 - k0 + SK_BK - 1) / SK_BK);
+    for (int kt = 0; kt < nk; ++kt) {
+        const int cur = kt & 1;
+        if (kt + 1 < nk) load(k0 + (int64_t)(kt + 1) * SK_BK, ra, rb);
+#pragma unroll
+        for (int k = 0; k < SK_BK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][k][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][k][64 + tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (kt + 1 < nk) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                As[cur ^ 1][lk + i][lrow] = ra[i];
+                Bs[cur ^ 1][lk + i][lrow] = rb[i];
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int p = p0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+        if (p >= P) continue;
+        float* row = out + (size_t)p * ldg + j0;
+        *reinterpret_cast<float4*>(row + tx * 4) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        *reinterpret_cast<float4*>(row + 64 + tx * 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    }
+}
+
+// Gm[p][j] = sum_z parts[z][p][j] in z order (j < ldg; the padding columns are zero in every part)
+__global__ void gm_reduce_kernel(const float* __restrict__ parts, int ks, int64_t n, float* __restrict__ Gm)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float v = 0.0f;
+    for (int z = 0; z < ks; ++z) v += parts[(size_t)z * n + i];
+    Gm[i] = v;
+}
+
 // Device workspace of one call (allocated per call: this is a set-up
 // routine, not part of the sum).  The GEMM stores whole 128-column blocks,
 // so the Gram rows (ldc) and the gradient rows (ldg) are padded to 128.
 struct DesignWork {
     float *C = nullptr, *T = nullptr, *Gm = nullptr, *r = nullptr, *m = nullptr, *v = nullptr;
+    float* parts = nullptr;  // split-K partials of Gm (ks x P x ldg)
     double* e = nullptr;
-    int64_t ldc = 0, ldg = 0;
+    int64_t ldc = 0, ldg = 0, kc = 0;
+    int ks = 1;
     ~DesignWork()
     {
+        cudaFree(parts);
         cudaFree(C);
         cudaFree(T);
         cudaFree(Gm);
@@ -173,6 +267,16 @@ struct DesignWork {
         if (adam && err == cudaSuccess) err = cudaMalloc(&v, sizeof(float) * (size_t)P * d);
         if (adam && err == cudaSuccess) err = cudaMemset(m, 0, sizeof(float) * (size_t)P * d);
         if (adam && err == cudaSuccess) err = cudaMemset(v, 0, sizeof(float) * (size_t)P * d);
+        // split the inner length of the second contraction so that its tiles fill the GPU
+        // about four times over (152 SMs); each range a multiple of the slab depth
+        const int64_t tiles = (((int64_t)P + 127) / 128) * (ldg / 128);
+        ks = (int)((4 * 152 + tiles - 1) / tiles);
+        if (ks > 16) ks = 16;
+        if (ks > ldc / 256) ks = (int)(ldc / 256);
+        if (ks < 1) ks = 1;
+        kc = ((ldc + ks - 1) / ks + 7) / 8 * 8;
+        ks = (int)((ldc + kc - 1) / kc);
+        if (ks > 1 && err == cudaSuccess) err = cudaMalloc(&parts, sizeof(float) * (size_t)ks * P * ldg);
         return err;
     }
 };
@@ -190,7 +294,14 @@ cudaError_t esym_pieces(const float* xi, int d, int P, DesignWork& w, cudaStream
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // Gm[p][j] = sum_q W[p][q] Xi[q][j]: rows of W against rows of Xi^T, inner length ldc
-    return qs_launch_project_fp32(w.T, d, (int)w.ldc, w.C, P, w.Gm, w.ldg, st);
+    if (w.ks <= 1) return qs_launch_project_fp32(w.T, d, (int)w.ldc, w.C, P, w.Gm, w.ldg, st);
+    dim3 g((unsigned)((P + SK_BM - 1) / SK_BM), (unsigned)(w.ldg / SK_BN), (unsigned)w.ks);
+    gm_splitk_kernel<<<g, 256, 0, st>>>(w.C, P, w.ldc, w.T, d, w.kc, w.parts, w.ldg);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t n = (int64_t)P * w.ldg;
+    gm_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w.parts, w.ks, n, w.Gm);
+    return cudaGetLastError();
 }
 
 qs_status sum_energy(const DesignWork& w, int P, cudaStream_t st, double* energy)
