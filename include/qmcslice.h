@@ -428,13 +428,16 @@ qs_status qs_plan_gemm(qs_plan plan, int* pair, int* ctas);
  * kernel_sum_sliced with f(t) = -c_d |t|; the sorting evaluation the paper
  * uses for this kernel): the sliced sum over the plan's directions computed
  * exactly, without the Fourier truncation, by sorting each slice's source
- * and target projections together and scanning prefix sums of w and w a in
- * FP64: sum_n w_n |b - a_n| = b (2 W_< - W) - (2 S_< - S).  Arguments as
- * for qs_sum.  Needs a QS_NEGDIST plan with d <= 64 (QS_ERR_UNSUPPORTED
- * otherwise).  The first call allocates the plan's sorting workspace (about
- * 16 CS (max_n + max_m) + 4 CS max_m bytes, CS = min(P, 32) slices per
- * chunk) and so synchronises; later calls are asynchronous and allocate
- * nothing.  Data errors (non-finite projections) go to the device flag.
+ * and target projections (FP32, from the FP32 SIMT projection) together and
+ * scanning prefix sums of w and w a in 64-bit fixed point (exact integer
+ * sums with per-slice scales, converted to FP64 per target):
+ * sum_n w_n |b - a_n| =
+ * b (2 W_< - W) - (2 S_< - S).  Arguments as for qs_sum.  Needs a QS_NEGDIST
+ * plan with d <= 64 (QS_ERR_UNSUPPORTED otherwise).  The first call allocates
+ * the plan's sorting workspace (about 20 CS (max_n + max_m) + 8 CS max_m
+ * bytes, CS = min(P, 128) slices per chunk) and so synchronises; later calls
+ * are asynchronous and allocate nothing.  Data errors (non-finite
+ * projections or weights) go to the device flag.
  */
 qs_status qs_sum_sorted(qs_plan plan, const float* x, int64_t N, const float* w, const float* y, int64_t M,
                         float* s, void* stream);

@@ -9,16 +9,22 @@
 // projections, sort sources and targets together; with W_<(b) and S_<(b) the
 // sums of w_n and w_n a_n over the sources before b in that order,
 //   sum_n w_n |b - a_n| = b (2 W_< - W) - (2 S_< - S),    W, S the totals,
-// one FP64 scan per slice.  (Sources equal to b contribute 0 on either side.)
+// one prefix scan per slice.  (Sources equal to b contribute 0 on either side.)
 //
-// Slices are processed in chunks of CS.  Per chunk: an init kernel forms the
-// FP32 projections (the dot products of the fused form) as order-preserving
-// 32-bit keys with the point index as payload; four stable LSD radix passes
-// of 8 bits (per-tile digit histograms, a per-slice scan, a scatter that
-// ranks within each warp with __match_any_sync); FP64 sums per sorted tile, a
-// per-slice scan of those, and a per-tile evaluation that adds the tile's
-// prefix; then a TwoSum accumulation of the chunk's slice values in slice
-// order.  Every sum has a fixed order, so results are reproducible.
+// Slices are processed in chunks of CS.  Per chunk: the FP32 SIMT GEMM forms
+// the chunk's projections of sources and targets (one fmaf chain per pair in
+// j order); four stable LSD radix passes of 8 bits sort them as
+// order-preserving 32-bit keys with the point index as payload (the first
+// pass reads the projections directly), each pass a per-tile digit
+// histogram, a per-slice scan and a scatter that ranks within each warp by
+// ballots on the digit's bits, stages the tile in digit order in shared
+// memory and writes each digit's run with consecutive threads; then 64-bit
+// fixed-point sums of w and w a per sorted tile, a per-slice scan of those,
+// and a per-tile evaluation that adds the tile's prefix (integer sums are
+// exact, so their order does not matter; the per-target formula in
+// error-free FP32 arithmetic); then a TwoSum accumulation of the chunk's
+// slice values in slice order, and the kernel's factor once per target.
+// Results are reproducible.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -42,152 +48,385 @@ __device__ __forceinline__ float key_float(uint32_t k)
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// keys[pl][i]: projection of source i (i < N) or target i - N on slice p0 + pl,
-// u = <xi_s_p, point> in the grid units of the plan (FP32, j order).
-__global__ void sort_init_kernel(const float* __restrict__ x, int64_t N, const float* __restrict__ y, int64_t M,
-                                 const float* __restrict__ xi_s, int d, int p0, int64_t LS,
-                                 uint32_t* __restrict__ key, uint32_t* __restrict__ pay, unsigned int* flag)
+// Where a radix pass reads element e of slice pl: the previous pass's keys
+// and payloads, or (first pass) the chunk's projections proj[pl][.] (sources
+// at columns 0 .. N-1, targets from column Nr = N rounded up to 128), which
+// the FP32 SIMT GEMM formed as one fmaf chain in j order per (slice, point),
+// turned into order-preserving keys with the point index as payload.  A
+// non-finite projection sorts as 0 and raises the data flag (in the first
+// histogram pass).
+struct KeySrc {
+    const uint32_t* key;
+    const uint32_t* pay;
+    const float* proj;
+    int64_t N, Nr, ldp;
+    unsigned int* flag;
+};
+
+template <bool FROM_PROJ>
+__device__ __forceinline__ uint32_t src_key(const KeySrc& s, int pl, int64_t LS, int64_t e, bool check)
 {
-    __shared__ float xs[QS_FUSED_MAX_D];
-    const int pl = blockIdx.y;
-    for (int j = threadIdx.x; j < d; j += blockDim.x) xs[j] = xi_s[(size_t)(p0 + pl) * d + j];
-    __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N + M) return;
-    const float* pt = i < N ? x + (size_t)i * d : y + (size_t)(i - N) * d;
-    float u = 0.0f;
-    for (int j = 0; j < d; ++j) u = fmaf(xs[j], __ldg(&pt[j]), u);
-    if (!isfinite(u)) {
-        atomicOr(flag, QS_FLAG_NONFINITE);
-        u = 0.0f;
+    if (FROM_PROJ) {
+        float u = __ldg(&s.proj[(size_t)pl * s.ldp + (e < s.N ? e : s.Nr + (e - s.N))]);
+        if (!isfinite(u)) {
+            if (check) atomicOr(s.flag, QS_FLAG_NONFINITE);
+            u = 0.0f;
+        }
+        return float_key(u);
     }
-    key[(size_t)pl * LS + i] = float_key(u);
-    pay[(size_t)pl * LS + i] = (uint32_t)i;
+    return __ldg(&s.key[(size_t)pl * LS + e]);
 }
 
-// hist[(pl * 256 + digit) * T + tile] = count of the digit in the tile
-__global__ void __launch_bounds__(SORT_THREADS) sort_hist_kernel(const uint32_t* __restrict__ key, int64_t L,
-                                                                 int64_t LS, int T, int shift,
-                                                                 uint32_t* __restrict__ hist)
+template <bool FROM_PROJ>
+__device__ __forceinline__ uint32_t src_pay(const KeySrc& s, int pl, int64_t LS, int64_t e)
+{
+    return FROM_PROJ ? (uint32_t)e : __ldg(&s.pay[(size_t)pl * LS + e]);
+}
+
+// The lanes of the warp whose 8-bit digit equals this lane's: the AND over the
+// digit's bits of the ballot of that bit (or of its complement), restricted to
+// the active lanes (dg < 256); an inactive lane (dg = 256) gets 0.  Eight
+// ballots cost less than __match_any_sync, which throttles the MIO pipe here.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t dg)
+{
+    uint32_t peers = __ballot_sync(0xffffffffu, dg < 256u);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const uint32_t bit = (dg >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return dg < 256u ? peers : 0u;
+}
+
+// hist[(pl * 256 + digit) * T + tile] = count of the digit in the tile, by
+// shared-memory atomics (three of the four digits of a projection's key are
+// close to uniform, so lanes rarely collide; aggregating equal digits first
+// costs more issue slots than the collisions of the top digit)
+template <bool FROM_PROJ>
+__global__ void __launch_bounds__(SORT_THREADS) sort_hist_kernel(KeySrc src, int64_t L, int64_t LS, int T,
+                                                                 int shift, uint32_t* __restrict__ hist)
 {
     __shared__ uint32_t h[256];
     const int t = blockIdx.x, pl = blockIdx.y;
     h[threadIdx.x] = 0;
     __syncthreads();
-    const uint32_t* k = key + (size_t)pl * LS;
     const int64_t e0 = (int64_t)t * SORT_TILE;
     for (int r = 0; r < SORT_ROUNDS; ++r) {
         const int64_t e = e0 + r * SORT_THREADS + threadIdx.x;
-        if (e < L) atomicAdd(&h[(k[e] >> shift) & 255u], 1u);
+        if (e < L) atomicAdd(&h[(src_key<FROM_PROJ>(src, pl, LS, e, true) >> shift) & 255u], 1u);
     }
     __syncthreads();
     hist[((size_t)pl * 256 + threadIdx.x) * T + t] = h[threadIdx.x];
 }
 
-// per slice: exclusive scan of its 256 x T counts (digit-major), in place
+// per slice: exclusive scan of its 256 x T counts (digit-major), in place,
+// 4096 entries at a time (four consecutive per thread, 16-byte accesses; the
+// count array of a slice starts on a 16-byte boundary because 256 T is a
+// multiple of 4): a block scan of the threads' sums plus the running carry
 __global__ void __launch_bounds__(1024) sort_scan_kernel(uint32_t* __restrict__ hist, int T)
 {
-    __shared__ uint32_t part[1024];
-    uint32_t* h = hist + (size_t)blockIdx.x * 256 * T;
-    const int n = 256 * T;
-    const int per = (n + 1023) / 1024;
-    const int b = threadIdx.x * per, e = min(n, b + per);
-    uint32_t sum = 0;
-    for (int i = b; i < e; ++i) sum += h[i];
-    part[threadIdx.x] = sum;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {  // inclusive Hillis-Steele scan
-        const uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry_s;
+    uint4* h4 = reinterpret_cast<uint4*>(hist + (size_t)blockIdx.x * 256 * T);
+    const int n4 = 64 * T;  // 256 T / 4
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t carry = 0;
+    for (int b0 = 0; b0 < n4; b0 += 1024) {
+        const int i = b0 + threadIdx.x;
+        uint4 v = i < n4 ? h4[i] : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t tsum = v.x + v.y + v.z + v.w;
+        uint32_t inc = tsum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t nv = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += nv;
+        }
+        if (lane == 31) wsum[warp] = inc;
         __syncthreads();
-        part[threadIdx.x] += v;
+        if (warp == 0) {
+            const uint32_t x = wsum[lane];
+            uint32_t y = x;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t nv = __shfl_up_sync(0xffffffffu, y, o);
+                if (lane >= o) y += nv;
+            }
+            wsum[lane] = y - x;  // exclusive over the warps
+            if (lane == 31) carry_s = y;
+        }
         __syncthreads();
-    }
-    uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-    for (int i = b; i < e; ++i) {
-        const uint32_t c = h[i];
-        h[i] = run;
-        run += c;
+        uint32_t run = carry + wsum[warp] + inc - tsum;
+        const uint32_t block_total = carry_s;
+        if (i < n4) {
+            uint4 o;
+            o.x = run;
+            run += v.x;
+            o.y = run;
+            run += v.y;
+            o.z = run;
+            run += v.z;
+            o.w = run;
+            h4[i] = o;
+        }
+        carry += block_total;
+        __syncthreads();  // wsum and carry_s are rewritten by the next block of entries
     }
 }
 
-// stable scatter of one tile: element order (round, thread) is index order
-__global__ void __launch_bounds__(SORT_THREADS) sort_scatter_kernel(const uint32_t* __restrict__ kin,
-                                                                    const uint32_t* __restrict__ pin, int64_t L,
-                                                                    int64_t LS, int T, int shift,
-                                                                    const uint32_t* __restrict__ hist,
+// Stable scatter of one tile.  Warp w ranks the w-th run of SORT_TILE / NW
+// consecutive elements, 32 at a time, against its own digit counters (lanes
+// with equal digits found by digit_peers; the first of them updates the
+// counter), so no block barrier is needed until the tile is ranked; then one
+// pass over the 256 digits turns the warps' counts into offsets, the tile is
+// placed in digit order in shared memory, and written out with consecutive
+// threads on consecutive positions of each digit's run.  The tile's count of
+// a digit is the difference of consecutive scanned offsets in the flattened
+// (digit, tile) order.
+template <bool FROM_PROJ>
+__global__ void __launch_bounds__(SORT_THREADS, 6) sort_scatter_kernel(KeySrc src, int64_t L, int64_t LS, int T,
+                                                                    int shift, const uint32_t* __restrict__ hist,
                                                                     uint32_t* __restrict__ kout,
                                                                     uint32_t* __restrict__ pout)
 {
-    __shared__ uint32_t gbase[256], base[256];
-    __shared__ uint32_t wc[2][SORT_THREADS / 32][256];
+    constexpr int NW = SORT_THREADS / 32;
+    constexpr int R = SORT_TILE / SORT_THREADS;  // rounds of 32 elements per warp
+    __shared__ uint32_t gbase[256], lbase[256], wsum[NW];
+    __shared__ uint32_t wcnt[NW][256];
+    __shared__ uint32_t sk[SORT_TILE], sp[SORT_TILE];
     const int t = blockIdx.x, pl = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    gbase[threadIdx.x] = hist[((size_t)pl * 256 + threadIdx.x) * T + t];
-    base[threadIdx.x] = 0;
-    for (int w = 0; w < SORT_THREADS / 32; ++w) {
-        wc[0][w][threadIdx.x] = 0;
-        wc[1][w][threadIdx.x] = 0;
+    {
+        const size_t flat = ((size_t)pl * 256 + threadIdx.x) * T + t;
+        const uint32_t g0 = hist[flat];
+        const uint32_t g1 = (threadIdx.x == 255 && t == T - 1) ? (uint32_t)L : hist[flat + 1];
+        gbase[threadIdx.x] = g0;
+        // exclusive scan of the tile's digit counts over the 256 digits
+        const uint32_t c = g1 - g0;
+        uint32_t inc = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t n = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += n;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        for (int w = 0; w < NW; ++w) wcnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        uint32_t off = 0;
+        for (int w = 0; w < warp; ++w) off += wsum[w];
+        lbase[threadIdx.x] = off + inc - c;
     }
     __syncthreads();
-    const uint32_t* ki = kin + (size_t)pl * LS;
-    const uint32_t* pi = pin + (size_t)pl * LS;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t e0 = (int64_t)t * SORT_TILE + (int64_t)warp * (R * 32);
+    uint32_t kk[R], pp[R], rk[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t e = e0 + r * 32 + lane;
+        const bool active = e < L;
+        kk[r] = active ? src_key<FROM_PROJ>(src, pl, LS, e, false) : 0u;
+        pp[r] = active ? src_pay<FROM_PROJ>(src, pl, LS, e) : 0u;
+        const uint32_t dg = active ? ((kk[r] >> shift) & 255u) : 256u;
+        const uint32_t peers = digit_peers(dg);
+        const int leader = peers ? __ffs(peers) - 1 : 0;
+        uint32_t before = 0;
+        if (active && lane == leader) {
+            before = wcnt[warp][dg];
+            wcnt[warp][dg] = before + __popc(peers);
+        }
+        before = __shfl_sync(0xffffffffu, before, leader);
+        rk[r] = before + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        // digit threadIdx.x: exclusive offsets of the warps' runs, in warp order
+        uint32_t run = 0;
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t c = wcnt[w][threadIdx.x];
+            wcnt[w][threadIdx.x] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (e0 + r * 32 + lane < L) {
+            const uint32_t dg = (kk[r] >> shift) & 255u;
+            const uint32_t lp = lbase[dg] + wcnt[warp][dg] + rk[r];
+            sk[lp] = kk[r];
+            sp[lp] = pp[r];
+        }
+    }
+    __syncthreads();
     uint32_t* ko = kout + (size_t)pl * LS;
     uint32_t* po = pout + (size_t)pl * LS;
-    const uint32_t lt = (1u << lane) - 1u;
-    const int64_t e0 = (int64_t)t * SORT_TILE;
-    for (int r = 0; r < SORT_ROUNDS; ++r) {
-        const int b = r & 1;
-        const int64_t e = e0 + r * SORT_THREADS + threadIdx.x;
-        const bool active = e < L;
-        const uint32_t k = active ? ki[e] : 0u;
-        const uint32_t pv = active ? pi[e] : 0u;
-        const uint32_t dg = active ? ((k >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-        const uint32_t rank = __popc(peers & lt);
-        if (active && rank == 0) wc[b][warp][dg] = __popc(peers);
-        __syncthreads();
-        {
-            // digit threadIdx.x: exclusive offsets of the warps, after the earlier rounds;
-            // the other buffer is cleared for the next round
-            uint32_t run = base[threadIdx.x];
-            for (int w = 0; w < SORT_THREADS / 32; ++w) {
-                const uint32_t c = wc[b][w][threadIdx.x];
-                wc[b][w][threadIdx.x] = run;
-                run += c;
-                wc[b ^ 1][w][threadIdx.x] = 0;
-            }
-            base[threadIdx.x] = run;
-        }
-        __syncthreads();
-        if (active) {
-            const uint32_t pos = gbase[dg] + wc[b][warp][dg] + rank;
-            ko[pos] = k;
-            po[pos] = pv;
-        }
+    const int n = (int)min((int64_t)SORT_TILE, L - (int64_t)t * SORT_TILE);
+    for (int j = threadIdx.x; j < n; j += SORT_THREADS) {
+        const uint32_t k = sk[j];
+        const uint32_t dg = (k >> shift) & 255u;
+        const uint32_t pos = gbase[dg] + (uint32_t)j - lbase[dg];
+        ko[pos] = k;
+        po[pos] = sp[j];
     }
 }
 
-// FP64 sums of (w, w a) over the sources of each sorted tile (fixed order)
+// The prefix sums W_< = sum of w_n and S_< = sum of w_n a_n over the sources
+// before a target run in 64-bit fixed point: each source contributes
+// qw = [w 2^ew] and qs = [p 2^es] + [e 2^es], where p + e = w a exactly
+// (p = fl(w a), e = fma(w, a, -p)) and [.] rounds to nearest, with powers of
+// two chosen per slice so that every partial sum stays below 2^51 in
+// magnitude: sum|w| <= N max|w| and max|a| <= the larger of the slice's first
+// and last sorted keys in magnitude.  Integer sums are exact and do not depend
+// on their order.  Everything per element is integer or FP32 arithmetic (FP64
+// is slow on this GPU): a target's value comes from the prefix sums by
+// splitting them into two exact FP32 parts and combining them with
+// error-free products and sums.
+struct SortScale {
+    unsigned int wmax;    // bits of max |w| over the sources (a float >= 0; order-independent)
+};
+
+struct SliceScale {
+    int ew, es;           // fixed-point exponents of w and w a
+};
+
+// k with |x| < 2^k for a finite float x (from its exponent field; denormals and 0 give -126)
+__device__ __forceinline__ int pow2_above(float x) { return (int)((__float_as_uint(x) >> 23) & 255u) - 126; }
+
+// The scales of one slice from max|w| and the slice's sorted keys k[0 .. L-1]:
+// N <= 2^lgN, so sum |w| < 2^(lgN + pow2_above(max|w|)) and sum |w a| below that times
+// 2^pow2_above(max|a|); ew, es leave sum |qw| < 2^51 + N and sum |qs| < 2^50 (1 + 2^-23) + 2 N.
+__device__ __forceinline__ SliceScale slice_scale(const SortScale* rec, bool unit_w, int64_t N,
+                                                  const uint32_t* k, int64_t L)
+{
+    const float wm = unit_w ? 1.0f : __uint_as_float(rec->wmax);
+    const float am = fmaxf(fabsf(key_float(k[0])), fabsf(key_float(k[L - 1])));
+    const int lgN = N > 1 ? 64 - __clzll((unsigned long long)(N - 1)) : 0;
+    SliceScale sc;
+    sc.ew = 51 - (lgN + pow2_above(wm));
+    sc.es = 50 - (lgN + pow2_above(wm) + pow2_above(am));
+    if (sc.es > 250) sc.es = 250;  // only for max|w| max|a| below ~1e-61: a coarser unit, the same bound
+    return sc;
+}
+
+// max |w| over the sources as the bits of a non-negative float (atomicMax on
+// the bits is order-independent); non-finite weights raise the data flag.
+// rec->wmax is cleared before the launch.
+__global__ void sort_wmax_kernel(const float* __restrict__ w, int64_t N, SortScale* __restrict__ rec,
+                                 unsigned int* flag)
+{
+    unsigned int m = 0u;
+    bool bad = false;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        const float a = fabsf(w[n]);
+        if (a <= 3.4e38f) m = max(m, __float_as_uint(a));
+        else bad = true;
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&rec->wmax, m);
+    if (bad) atomicOr(flag, QS_FLAG_NONFINITE);
+}
+
+// x 2^s rounded to the nearest integer (halves away from zero), from the bits
+// of a finite float, in integer arithmetic; the scales above keep |x 2^s| < 2^52.
+__device__ __forceinline__ long long fixed_of(float x, int s)
+{
+    const uint32_t b = __float_as_uint(x);
+    const int ex = (int)((b >> 23) & 255u);
+    const uint32_t m = ex ? ((b & 0x7fffffu) | 0x800000u) : (b & 0x7fffffu);
+    const int sh = (ex ? ex : 1) - 150 + s;  // x = m 2^((ex ? ex : 1) - 150)
+    long long v;
+    if (sh >= 0) v = (long long)m << min(sh, 38);
+    else v = sh > -25 ? (long long)((m + (1u << (-sh - 1))) >> -sh) : 0ll;
+    return (b >> 31) ? -v : v;
+}
+
+__device__ __forceinline__ void src_fixed(float wn, float a, const SliceScale& sc, long long& qw, long long& qs)
+{
+    qw = fixed_of(wn, sc.ew);
+    const float p = wn * a;
+    const float e = fmaf(wn, a, -p);
+    qs = fixed_of(p, sc.es) + fixed_of(e, sc.es);
+}
+
+// x 2^k for |k| <= 252, as two exact multiplications by powers of two
+// (each factor a normal float; no intermediate overflow or underflow beyond the result's own)
+__device__ __forceinline__ float mul_pow2(float x, int k)
+{
+    const int k1 = k / 2, k2 = k - k1;
+    return x * __int_as_float((127 + k1) << 23) * __int_as_float((127 + k2) << 23);
+}
+
+// X (|X| < 2^53) as hi + lo: hi = 2^32 (X >> 32) exactly, lo = fl(X mod 2^32), |lo - (X mod 2^32)| <= 2^7
+__device__ __forceinline__ void split_fixed(long long X, float& hi, float& lo)
+{
+    hi = (float)(int)(X >> 32) * 4294967296.0f;
+    lo = (float)(unsigned int)(X & 0xffffffffll);
+}
+
+// sum_n w_n |b - a_n| = b (2 W_< - W) - (2 S_< - S) with XW = 2^ew (2 W_< - W),
+// XS = 2^es (2 S_< - S), evaluated in the units of 2^-es with an error-free
+// product of b and XW's high part and an error-free sum against XS's high part;
+// the rest (products' rounding, low parts) is below 2^-40 of the terms.
+__device__ __forceinline__ float sorted_value(float b, long long XW, long long XS, const SliceScale& sc)
+{
+    float wh, wl, sh, sl;
+    split_fixed(XW, wh, wl);
+    split_fixed(XS, sh, sl);
+    const int c = sc.es - sc.ew;  // |b 2^c| <= 1/2 (2^es max|a| and 2^ew differ by >= 2 max|a|)
+    wh = mul_pow2(wh, c);
+    wl = mul_pow2(wl, c);
+    const float p1 = b * wh;
+    const float e1 = fmaf(b, wh, -p1);
+    const float t = p1 - sh;  // TwoSum(p1, -sh)
+    const float bv = t - p1;
+    const float u = (p1 - (t - bv)) + (-sh - bv);
+    const float rest = e1 + fmaf(b, wl, -sl) + u;
+    return mul_pow2(t + rest, -sc.es);
+}
+
+// consecutive elements of a tile per thread, loaded as 16-byte vectors
+constexpr int SORT_VPT = SORT_TILE / SORT_THREADS;
+static_assert(SORT_VPT % 4 == 0, "vector loads of keys and payloads");
+
+__device__ __forceinline__ void load_run(const uint32_t* __restrict__ a, int64_t e0, uint32_t (&v)[SORT_VPT])
+{
+    const uint4* a4 = reinterpret_cast<const uint4*>(a + e0);
+#pragma unroll
+    for (int q = 0; q < SORT_VPT / 4; ++q) {
+        const uint4 x = __ldg(a4 + q);
+        v[4 * q + 0] = x.x;
+        v[4 * q + 1] = x.y;
+        v[4 * q + 2] = x.z;
+        v[4 * q + 3] = x.w;
+    }
+}
+
+// fixed-point sums of (w, w a) over the sources of each sorted tile; thread j
+// takes the tile's elements SORT_VPT j .. SORT_VPT (j + 1) - 1 (the buffers
+// hold whole tiles, so the vector loads stay inside them; elements >= L are
+// skipped)
 __global__ void __launch_bounds__(SORT_THREADS) sort_tilesum_kernel(const uint32_t* __restrict__ key,
                                                                     const uint32_t* __restrict__ pay, int64_t N,
                                                                     int64_t L, int64_t LS, int T,
                                                                     const float* __restrict__ w,
-                                                                    double* __restrict__ tsum)
+                                                                    const SortScale* __restrict__ scp,
+                                                                    long long* __restrict__ tsum)
 {
-    __shared__ double rw[SORT_THREADS / 32], ra[SORT_THREADS / 32];
+    __shared__ long long rw[SORT_THREADS / 32], ra[SORT_THREADS / 32];
     const int t = blockIdx.x, pl = blockIdx.y;
     const uint32_t* k = key + (size_t)pl * LS;
     const uint32_t* p = pay + (size_t)pl * LS;
-    double sw = 0.0, sa = 0.0;
-    for (int r = 0; r < SORT_ROUNDS; ++r) {
-        const int64_t e = (int64_t)t * SORT_TILE + r * SORT_THREADS + threadIdx.x;
-        if (e < L) {
-            const uint32_t i = p[e];
-            if (i < N) {
-                const double wn = w ? (double)w[i] : 1.0;
-                sw += wn;
-                sa += wn * (double)key_float(k[e]);
-            }
+    const SliceScale sc = slice_scale(scp, w == nullptr, N, k, L);
+    const int64_t e0 = (int64_t)t * SORT_TILE + (int64_t)threadIdx.x * SORT_VPT;
+    uint32_t kk[SORT_VPT], pp[SORT_VPT];
+    load_run(k, e0, kk);
+    load_run(p, e0, pp);
+    long long sw = 0, sa = 0;
+#pragma unroll
+    for (int j = 0; j < SORT_VPT; ++j) {
+        if (e0 + j < L && pp[j] < N) {
+            long long qw, qs;
+            src_fixed(w ? __ldg(&w[pp[j]]) : 1.0f, key_float(kk[j]), sc, qw, qs);
+            sw += qw;
+            sa += qs;
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -200,7 +439,7 @@ __global__ void __launch_bounds__(SORT_THREADS) sort_tilesum_kernel(const uint32
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double tw = 0.0, ta = 0.0;
+        long long tw = 0, ta = 0;
         for (int q = 0; q < SORT_THREADS / 32; ++q) {
             tw += rw[q];
             ta += ra[q];
@@ -210,90 +449,116 @@ __global__ void __launch_bounds__(SORT_THREADS) sort_tilesum_kernel(const uint32
     }
 }
 
-// per slice, serially: exclusive prefix of the tile sums in place, totals in tot[pl]
-__global__ void sort_tilescan_kernel(double* __restrict__ tsum, int T, int cs, double* __restrict__ tot)
+// per slice (one warp each, 32 tiles at a time): exclusive prefix of the tile
+// sums in place, totals in tot[pl] (integer sums: exact in any order)
+__global__ void sort_tilescan_kernel(long long* __restrict__ tsum, int T, int cs, long long* __restrict__ tot)
 {
-    const int pl = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pl >= cs) return;
-    double* ts = tsum + (size_t)pl * T * 2;
-    double rw = 0.0, ra = 0.0;
-    for (int t = 0; t < T; ++t) {
-        const double cw = ts[2 * t], ca = ts[2 * t + 1];
-        ts[2 * t] = rw;
-        ts[2 * t + 1] = ra;
-        rw += cw;
-        ra += ca;
-    }
-    tot[2 * pl] = rw;
-    tot[2 * pl + 1] = ra;
-}
-
-// per sorted tile: exclusive FP64 prefix of (w, w a) over the sources before
-// each element; for every target m the slice's value
-// amp * (b (2 W_< - W) - (2 S_< - S)) goes to t[pl][m]
-// GRAD: t[pl][m] = 2 W_< - W = sum_n w_n sign(b - a_n) instead (sources whose
-// key equals b's sort before it and count as below: a one-sided subgradient)
-template <bool GRAD>
-__global__ void __launch_bounds__(SORT_THREADS) sort_eval_kernel(const uint32_t* __restrict__ key,
-                                                                 const uint32_t* __restrict__ pay, int64_t N,
-                                                                 int64_t M, int64_t LS, int T,
-                                                                 const float* __restrict__ w,
-                                                                 const double* __restrict__ tsum,
-                                                                 const double* __restrict__ tot, double amp,
-                                                                 float* __restrict__ tout)
-{
-    __shared__ double sw[SORT_THREADS / 32], sa[SORT_THREADS / 32];
-    const int t = blockIdx.x, pl = blockIdx.y;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t* k = key + (size_t)pl * LS;
-    const uint32_t* p = pay + (size_t)pl * LS;
-    const int64_t L = N + M;
-    const double W = tot[2 * pl], S = tot[2 * pl + 1];
-    double carry_w = tsum[((size_t)pl * T + t) * 2 + 0];
-    double carry_a = tsum[((size_t)pl * T + t) * 2 + 1];
-    for (int r = 0; r < SORT_ROUNDS; ++r) {
-        const int64_t e = (int64_t)t * SORT_TILE + r * SORT_THREADS + threadIdx.x;
-        double vw = 0.0, va = 0.0, b = 0.0;
-        uint32_t i = 0xffffffffu;
-        if (e < L) {
-            i = p[e];
-            b = (double)key_float(k[e]);
-            if (i < N) {
-                vw = w ? (double)w[i] : 1.0;
-                va = vw * b;
-            }
-        }
-        double iw = vw, ia = va;  // inclusive warp scan
+    const int pl = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (pl >= cs) return;  // whole warps
+    long long* ts = tsum + (size_t)pl * T * 2;
+    long long rw = 0, ra = 0;
+    for (int t0 = 0; t0 < T; t0 += 32) {
+        const int t = t0 + lane;
+        const long long cw = t < T ? ts[2 * t] : 0, ca = t < T ? ts[2 * t + 1] : 0;
+        long long iw = cw, ia = ca;
         for (int o = 1; o < 32; o <<= 1) {
-            const double nw = __shfl_up_sync(0xffffffffu, iw, o);
-            const double na = __shfl_up_sync(0xffffffffu, ia, o);
+            const long long nw = __shfl_up_sync(0xffffffffu, iw, o);
+            const long long na = __shfl_up_sync(0xffffffffu, ia, o);
             if (lane >= o) {
                 iw += nw;
                 ia += na;
             }
         }
-        if (lane == 31) {
-            sw[warp] = iw;
-            sa[warp] = ia;
+        if (t < T) {
+            ts[2 * t] = rw + iw - cw;
+            ts[2 * t + 1] = ra + ia - ca;
         }
-        __syncthreads();
-        double ow = carry_w, oa = carry_a, bw = carry_w, ba = carry_a;
-        for (int q = 0; q < SORT_THREADS / 32; ++q) {
-            if (q < warp) {
-                ow += sw[q];
-                oa += sa[q];
+        rw += __shfl_sync(0xffffffffu, iw, 31);
+        ra += __shfl_sync(0xffffffffu, ia, 31);
+    }
+    if (lane == 0) {
+        tot[2 * pl] = rw;
+        tot[2 * pl + 1] = ra;
+    }
+}
+
+// per sorted tile (elements per thread as in the tile sums): the fixed-point
+// prefix of (w, w a) over the sources before each element; for every target m
+// the slice's value b (2 W_< - W) - (2 S_< - S) goes to t[pl][m] (the factor
+// of the kernel and the grid is applied once per target at the end)
+// GRAD: t[pl][m] = 2 W_< - W = sum_n w_n sign(b - a_n) instead (sources whose
+// projection equals b count as below).
+template <bool GRAD>
+__global__ void __launch_bounds__(SORT_THREADS) sort_eval_kernel(const uint32_t* __restrict__ key,
+                                                                 const uint32_t* __restrict__ pay, int64_t N,
+                                                                 int64_t M, int64_t LS, int T,
+                                                                 const float* __restrict__ w,
+                                                                 const SortScale* __restrict__ scp,
+                                                                 const long long* __restrict__ tsum,
+                                                                 const long long* __restrict__ tot,
+                                                                 float* __restrict__ tout)
+{
+    __shared__ long long sw[SORT_THREADS / 32], sa[SORT_THREADS / 32];
+    const int t = blockIdx.x, pl = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t* k = key + (size_t)pl * LS;
+    const uint32_t* p = pay + (size_t)pl * LS;
+    const int64_t L = N + M;
+    const SliceScale sc = slice_scale(scp, w == nullptr, N, k, L);
+    const int64_t e0 = (int64_t)t * SORT_TILE + (int64_t)threadIdx.x * SORT_VPT;
+    uint32_t kk[SORT_VPT], pp[SORT_VPT];
+    load_run(k, e0, kk);
+    load_run(p, e0, pp);
+    long long qw[SORT_VPT], qs[SORT_VPT];
+    long long tw = 0, ta = 0;
+#pragma unroll
+    for (int j = 0; j < SORT_VPT; ++j) {
+        qw[j] = 0;
+        qs[j] = 0;
+        if (e0 + j < L && pp[j] < N)
+            src_fixed(w ? __ldg(&w[pp[j]]) : 1.0f, key_float(kk[j]), sc, qw[j], qs[j]);
+        tw += qw[j];
+        ta += qs[j];
+    }
+    long long iw = tw, ia = ta;  // inclusive warp scan of the threads' sums
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long nw = __shfl_up_sync(0xffffffffu, iw, o);
+        const long long na = __shfl_up_sync(0xffffffffu, ia, o);
+        if (lane >= o) {
+            iw += nw;
+            ia += na;
+        }
+    }
+    if (lane == 31) {
+        sw[warp] = iw;
+        sa[warp] = ia;
+    }
+    __syncthreads();
+    long long ow = tsum[((size_t)pl * T + t) * 2 + 0] + iw - tw;
+    long long oa = tsum[((size_t)pl * T + t) * 2 + 1] + ia - ta;
+    for (int q = 0; q < warp; ++q) {
+        ow += sw[q];
+        oa += sa[q];
+    }
+    const long long W = tot[2 * pl], S = tot[2 * pl + 1];
+#pragma unroll
+    for (int j = 0; j < SORT_VPT; ++j) {
+        // sources strictly before (a target contributes nothing of its own)
+        if (e0 + j < L && pp[j] >= N) {
+            const long long XW = 2 * ow - W;
+            float v;
+            if (GRAD) {
+                float hi, lo;
+                split_fixed(XW, hi, lo);
+                v = mul_pow2(hi + lo, -sc.ew);
+            } else {
+                v = sorted_value(key_float(kk[j]), XW, 2 * oa - S, sc);
             }
-            bw += sw[q];
-            ba += sa[q];
+            tout[(size_t)pl * M + (pp[j] - N)] = v;
         }
-        if (e < L && i >= N) {
-            const double Wl = ow + iw - vw, Sl = oa + ia - va;  // sources strictly before
-            tout[(size_t)pl * M + (i - N)] =
-                GRAD ? (float)(2.0 * Wl - W) : (float)(amp * (b * (2.0 * Wl - W) - (2.0 * Sl - S)));
-        }
-        carry_w = bw;
-        carry_a = ba;
-        __syncthreads();
+        ow += qw[j];
+        oa += qs[j];
     }
 }
 
@@ -333,17 +598,18 @@ __global__ void sort_gfinal_kernel(const float* __restrict__ ghi, const float* _
     for (int j = 0; j < d; ++j) gy[(size_t)m * d + j] = vm * (ghi[(size_t)j * M + m] + glo[(size_t)j * M + m]);
 }
 
-__global__ void sort_final_kernel(const float* __restrict__ hi, const float* __restrict__ lo, int64_t M, int P,
-                                  float* __restrict__ s)
+// s[m] = amp (hi + lo) / P: the factor of the kernel and the grid, once per target
+__global__ void sort_final_kernel(const float* __restrict__ hi, const float* __restrict__ lo, int64_t M,
+                                  double amp_p, float* __restrict__ s)
 {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (m < M) s[m] = (hi[m] + lo[m]) / (float)P;
+    if (m < M) s[m] = (float)(((double)hi[m] + (double)lo[m]) * amp_p);
 }
 
 }  // namespace
 
 // Chunk of slices and the workspace for up to L = N + M points.
-int qs_sort_chunk(int P) { return P < 32 ? P : 32; }
+int qs_sort_chunk(int P) { return P < 128 ? P : 128; }
 
 size_t qs_sort_workspace_bytes(int P, int64_t max_n, int64_t max_m)
 {
@@ -351,10 +617,13 @@ size_t qs_sort_workspace_bytes(int P, int64_t max_n, int64_t max_m)
     const int64_t L = max_n + max_m;
     const int64_t LS = (L + SORT_TILE - 1) / SORT_TILE * SORT_TILE;
     const int64_t T = LS / SORT_TILE;
+    const int64_t PR = (max_n + 127) / 128 * 128 + (max_m + 127) / 128 * 128;
     return (size_t)4 * CS * LS * sizeof(uint32_t)         // key / payload, two buffers each
+           + (size_t)CS * PR * sizeof(float)              // projections of a chunk
            + (size_t)CS * 256 * T * sizeof(uint32_t)      // digit offsets
-           + (size_t)CS * T * 2 * sizeof(double)          // tile sums
-           + (size_t)CS * 2 * sizeof(double)              // slice totals
+           + (size_t)CS * T * 2 * sizeof(long long)       // tile sums (fixed point)
+           + (size_t)CS * 2 * sizeof(long long)           // slice totals
+           + 64                                           // max |w|
            + (size_t)CS * max_m * sizeof(float)           // slice values of a chunk
            + (size_t)2 * max_m * QS_FUSED_MAX_D * sizeof(float) + 1024;  // hi / lo (x d for gradients)
 }
@@ -380,24 +649,43 @@ cudaError_t qs_launch_sum_sorted(const float* x, int64_t N, const float* w, cons
     uint32_t* kB = pA + (size_t)CS * LS;
     uint32_t* pB = kB + (size_t)CS * LS;
     uint32_t* hist = pB + (size_t)CS * LS;
-    double* tsum = reinterpret_cast<double*>(hist + (size_t)CS * 256 * Tmax);  // 8-byte aligned: even count
-    double* tot = tsum + (size_t)CS * Tmax * 2;
-    float* tb = reinterpret_cast<float*>(tot + (size_t)CS * 2);
+    long long* tsum = reinterpret_cast<long long*>(hist + (size_t)CS * 256 * Tmax);  // 8-byte aligned: even count
+    long long* tot = tsum + (size_t)CS * Tmax * 2;
+    SortScale* scale_rec = reinterpret_cast<SortScale*>(tot + (size_t)CS * 2);
+    float* tb = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(scale_rec) + 64);
     float* hi = tb + (size_t)CS * max_m;
     float* lo = hi + max_m;
+    // the chunk's projections after the accumulators (at most 2 max_m d floats), on a 256-byte
+    // boundary inside the workspace's 1 KB of slack (the GEMM stores 16-byte vectors)
+    const int64_t ldp = (max_n + 127) / 128 * 128 + (max_m + 127) / 128 * 128;
+    const int64_t Nr = (N + 127) / 128 * 128;
+    float* proj = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(hi + (size_t)2 * max_m * QS_FUSED_MAX_D) + 255) & ~(uintptr_t)255);
     const size_t acc = (size_t)M * (grad ? d : 1);  // accumulators of this call, hi then lo
     lo = hi + acc;
     cudaError_t e = cudaMemsetAsync(hi, 0, sizeof(float) * 2 * acc, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scale_rec, 0, sizeof(SortScale), st);
+    if (e == cudaSuccess && w && N > 0) {
+        const int64_t nb = (N + 255) / 256;
+        sort_wmax_kernel<<<(unsigned)(nb < 2 * 152 ? nb : 2 * 152), 256, 0, st>>>(w, N, scale_rec, flag);
+        e = cudaGetLastError();
+    }
     for (int p0 = 0; p0 < P && e == cudaSuccess; p0 += CS) {
         const int cs = P - p0 < CS ? P - p0 : CS;
-        sort_init_kernel<<<dim3((unsigned)((L + 255) / 256), (unsigned)cs), 256, 0, st>>>(x, N, y, M, xi_s, d, p0, LS,
-                                                                                          kA, pA, flag);
-        uint32_t *ki = kA, *pi = pA, *ko = kB, *po = pB;
-        for (int shift = 0; shift < 32 && (e = cudaGetLastError()) == cudaSuccess; shift += 8) {
-            sort_hist_kernel<<<dim3((unsigned)T, (unsigned)cs), SORT_THREADS, 0, st>>>(ki, L, LS, T, shift, hist);
+        if (N > 0) e = qs_launch_project_fp32(x, N, d, xi_s + (size_t)p0 * d, cs, proj, ldp, st);
+        if (e == cudaSuccess) e = qs_launch_project_fp32(y, M, d, xi_s + (size_t)p0 * d, cs, proj + Nr, ldp, st);
+        if (e != cudaSuccess) break;
+        // pass 0 reads the projections and writes A; then A -> B -> A -> B
+        uint32_t *ki = kB, *pi = pB, *ko = kA, *po = pA;
+        const dim3 tg((unsigned)T, (unsigned)cs);
+        for (int shift = 0; shift < 32; shift += 8) {
+            const KeySrc ks{ki, pi, proj, N, Nr, ldp, flag};
+            if (shift == 0) sort_hist_kernel<true><<<tg, SORT_THREADS, 0, st>>>(ks, L, LS, T, shift, hist);
+            else sort_hist_kernel<false><<<tg, SORT_THREADS, 0, st>>>(ks, L, LS, T, shift, hist);
             sort_scan_kernel<<<cs, 1024, 0, st>>>(hist, T);
-            sort_scatter_kernel<<<dim3((unsigned)T, (unsigned)cs), SORT_THREADS, 0, st>>>(ki, pi, L, LS, T, shift,
-                                                                                         hist, ko, po);
+            if (shift == 0) sort_scatter_kernel<true><<<tg, SORT_THREADS, 0, st>>>(ks, L, LS, T, shift, hist, ko, po);
+            else sort_scatter_kernel<false><<<tg, SORT_THREADS, 0, st>>>(ks, L, LS, T, shift, hist, ko, po);
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
             uint32_t* tk = ki;
             ki = ko;
             ko = tk;
@@ -406,15 +694,16 @@ cudaError_t qs_launch_sum_sorted(const float* x, int64_t N, const float* w, cons
             po = tk;
         }
         if (e != cudaSuccess) break;
-        // four passes: the sorted data are back in the A buffers
-        sort_tilesum_kernel<<<dim3((unsigned)T, (unsigned)cs), SORT_THREADS, 0, st>>>(ki, pi, N, L, LS, T, w, tsum);
-        sort_tilescan_kernel<<<1, 32, 0, st>>>(tsum, T, cs, tot);
+        // four passes: the sorted data are in the B buffers (ki, pi)
+        sort_tilesum_kernel<<<dim3((unsigned)T, (unsigned)cs), SORT_THREADS, 0, st>>>(ki, pi, N, L, LS, T, w,
+                                                                                     scale_rec, tsum);
+        sort_tilescan_kernel<<<(unsigned)((cs + 7) / 8), 256, 0, st>>>(tsum, T, cs, tot);
         const dim3 eg((unsigned)T, (unsigned)cs);
         if (grad) {
-            sort_eval_kernel<true><<<eg, SORT_THREADS, 0, st>>>(ki, pi, N, M, LS, T, w, tsum, tot, amp, tb);
+            sort_eval_kernel<true><<<eg, SORT_THREADS, 0, st>>>(ki, pi, N, M, LS, T, w, scale_rec, tsum, tot, tb);
             sort_gaccum_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(tb, cs, M, xi, d, p0, hi, lo);
         } else {
-            sort_eval_kernel<false><<<eg, SORT_THREADS, 0, st>>>(ki, pi, N, M, LS, T, w, tsum, tot, amp, tb);
+            sort_eval_kernel<false><<<eg, SORT_THREADS, 0, st>>>(ki, pi, N, M, LS, T, w, scale_rec, tsum, tot, tb);
             sort_accum_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(tb, cs, M, hi, lo);
         }
         e = cudaGetLastError();
@@ -423,7 +712,7 @@ cudaError_t qs_launch_sum_sorted(const float* x, int64_t N, const float* w, cons
         if (grad)
             sort_gfinal_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(hi, lo, M, d, v, scale, gy);
         else
-            sort_final_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(hi, lo, M, P, s);
+            sort_final_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(hi, lo, M, amp / P, s);
         e = cudaGetLastError();
     }
     return e;
