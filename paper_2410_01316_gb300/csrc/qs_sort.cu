@@ -218,11 +218,14 @@ __global__ void __launch_bounds__(SORT_THREADS, 6) sort_scatter_kernel(KeySrc sr
     const int64_t e0 = (int64_t)t * SORT_TILE + (int64_t)warp * (R * 32);
     uint32_t kk[R], pp[R], rk[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < R; ++r) {  // all loads first: 2 R in flight per thread
         const int64_t e = e0 + r * 32 + lane;
-        const bool active = e < L;
-        kk[r] = active ? src_key<FROM_PROJ>(src, pl, LS, e, false) : 0u;
-        pp[r] = active ? src_pay<FROM_PROJ>(src, pl, LS, e) : 0u;
+        kk[r] = e < L ? src_key<FROM_PROJ>(src, pl, LS, e, false) : 0u;
+        pp[r] = e < L ? src_pay<FROM_PROJ>(src, pl, LS, e) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const bool active = e0 + r * 32 + lane < L;
         const uint32_t dg = active ? ((kk[r] >> shift) & 255u) : 256u;
         const uint32_t peers = digit_peers(dg);
         const int leader = peers ? __ffs(peers) - 1 : 0;
