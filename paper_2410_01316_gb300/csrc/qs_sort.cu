@@ -273,8 +273,8 @@ __global__ void __launch_bounds__(SORT_THREADS, 6) sort_scatter_kernel(KeySrc sr
 
 // The prefix sums W_< = sum of w_n and S_< = sum of w_n a_n over the sources
 // before a target run in 64-bit fixed point: each source contributes
-// qw = [w 2^ew] and qs = [p 2^es] + [e 2^es], where p + e = w a exactly
-// (p = fl(w a), e = fma(w, a, -p)) and [.] rounds to nearest, with powers of
+// qw = [w 2^ew] and qs = [w a 2^es], [.] rounding to nearest (w a is the
+// exact integer product of the two significands, rounded once), with powers of
 // two chosen per slice so that every partial sum stays below 2^51 in
 // magnitude: sum|w| <= N max|w| and max|a| <= the larger of the slice's first
 // and last sorted keys in magnitude.  Integer sums are exact and do not depend
@@ -288,14 +288,28 @@ struct SortScale {
 
 struct SliceScale {
     int ew, es;           // fixed-point exponents of w and w a
+    float c1, c2;         // 2^(es - ew) as two factors (the units of 2^-ew into those of 2^-es)
+    float s1, s2;         // 2^-es as two factors
+    float g1, g2;         // 2^-ew as two factors
 };
+
+// 2^k as a float, -126 <= k <= 127
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+
+// 2^k as two normal-float factors, |k| <= 252
+__device__ __forceinline__ void pow2_pair(int k, float& f1, float& f2)
+{
+    const int k1 = k / 2;
+    f1 = pow2f(k1);
+    f2 = pow2f(k - k1);
+}
 
 // k with |x| < 2^k for a finite float x (from its exponent field; denormals and 0 give -126)
 __device__ __forceinline__ int pow2_above(float x) { return (int)((__float_as_uint(x) >> 23) & 255u) - 126; }
 
 // The scales of one slice from max|w| and the slice's sorted keys k[0 .. L-1]:
 // N <= 2^lgN, so sum |w| < 2^(lgN + pow2_above(max|w|)) and sum |w a| below that times
-// 2^pow2_above(max|a|); ew, es leave sum |qw| < 2^51 + N and sum |qs| < 2^50 (1 + 2^-23) + 2 N.
+// 2^pow2_above(max|a|); ew, es leave sum |qw| < 2^51 + N / 2 and sum |qs| < 2^50 + N / 2.
 __device__ __forceinline__ SliceScale slice_scale(const SortScale* rec, bool unit_w, int64_t N,
                                                   const uint32_t* k, int64_t L)
 {
@@ -306,6 +320,9 @@ __device__ __forceinline__ SliceScale slice_scale(const SortScale* rec, bool uni
     sc.ew = 51 - (lgN + pow2_above(wm));
     sc.es = 50 - (lgN + pow2_above(wm) + pow2_above(am));
     if (sc.es > 250) sc.es = 250;  // only for max|w| max|a| below ~1e-61: a coarser unit, the same bound
+    pow2_pair(sc.es - sc.ew, sc.c1, sc.c2);
+    pow2_pair(-sc.es, sc.s1, sc.s2);
+    pow2_pair(-sc.ew, sc.g1, sc.g2);
     return sc;
 }
 
@@ -327,34 +344,45 @@ __global__ void sort_wmax_kernel(const float* __restrict__ w, int64_t N, SortSca
     if (bad) atomicOr(flag, QS_FLAG_NONFINITE);
 }
 
-// x 2^s rounded to the nearest integer (halves away from zero), from the bits
-// of a finite float, in integer arithmetic; the scales above keep |x 2^s| < 2^52.
-__device__ __forceinline__ long long fixed_of(float x, int s)
+// A finite float as (-1)^neg m 2^(e - 150) with 2^23 <= m < 2^24 for every
+// nonzero x (denormals normalised), m = 0 for zeros
+struct FDec {
+    uint32_t m;
+    int e;
+    uint32_t neg;
+};
+
+__device__ __forceinline__ FDec fdec(float x)
 {
     const uint32_t b = __float_as_uint(x);
-    const int ex = (int)((b >> 23) & 255u);
-    const uint32_t m = ex ? ((b & 0x7fffffu) | 0x800000u) : (b & 0x7fffffu);
-    const int sh = (ex ? ex : 1) - 150 + s;  // x = m 2^((ex ? ex : 1) - 150)
-    long long v;
-    if (sh >= 0) v = (long long)m << min(sh, 38);
-    else v = sh > -25 ? (long long)((m + (1u << (-sh - 1))) >> -sh) : 0ll;
-    return (b >> 31) ? -v : v;
+    const uint32_t ex = (b >> 23) & 255u;
+    FDec r;
+    const uint32_t m = (b & 0x7fffffu) | (ex ? 0x800000u : 0u);
+    const int z = __clz(m) - 8;  // 0 for normal x
+    r.m = m << z;
+    r.e = (ex ? (int)ex : 1) - z;
+    r.neg = b >> 31;
+    return r;
 }
 
+// (-1)^neg round(t 2^-k), halves away from zero, for t < 2^62 and k clamped to [1, 63]
+// (branch-free; with normalised significands the scales keep k >= 4)
+__device__ __forceinline__ long long shr_round(unsigned long long t, int k, uint32_t neg)
+{
+    k = min(max(k, 1), 63);
+    const long long v = (long long)((t + (1ull << (k - 1))) >> k);
+    return neg ? -v : v;
+}
+
+// qw = [w 2^ew] from m_w 2^32 shifted down; qs = [w a 2^es] from the 48-bit
+// product m_w m_a, shifted up by 8 and down again (m_w m_a >= 2^46 for nonzero
+// inputs and |w a 2^es| < 2^51 keep the shift >= 4; |w 2^ew| < 2^51 keeps the
+// shift of qw >= 5)
 __device__ __forceinline__ void src_fixed(float wn, float a, const SliceScale& sc, long long& qw, long long& qs)
 {
-    qw = fixed_of(wn, sc.ew);
-    const float p = wn * a;
-    const float e = fmaf(wn, a, -p);
-    qs = fixed_of(p, sc.es) + fixed_of(e, sc.es);
-}
-
-// x 2^k for |k| <= 252, as two exact multiplications by powers of two
-// (each factor a normal float; no intermediate overflow or underflow beyond the result's own)
-__device__ __forceinline__ float mul_pow2(float x, int k)
-{
-    const int k1 = k / 2, k2 = k - k1;
-    return x * __int_as_float((127 + k1) << 23) * __int_as_float((127 + k2) << 23);
+    const FDec dw = fdec(wn), da = fdec(a);
+    qw = shr_round((unsigned long long)dw.m << 32, 32 - (dw.e - 150 + sc.ew), dw.neg);
+    qs = shr_round(((unsigned long long)dw.m * da.m) << 8, 8 - (dw.e + da.e - 300 + sc.es), dw.neg ^ da.neg);
 }
 
 // X (|X| < 2^53) as hi + lo: hi = 2^32 (X >> 32) exactly, lo = fl(X mod 2^32), |lo - (X mod 2^32)| <= 2^7
@@ -368,21 +396,21 @@ __device__ __forceinline__ void split_fixed(long long X, float& hi, float& lo)
 // XS = 2^es (2 S_< - S), evaluated in the units of 2^-es with an error-free
 // product of b and XW's high part and an error-free sum against XS's high part;
 // the rest (products' rounding, low parts) is below 2^-40 of the terms.
+// |b 2^(es - ew)| <= 1/2: 2^es max|a| and 2^ew differ by at least 2 max|a|.
 __device__ __forceinline__ float sorted_value(float b, long long XW, long long XS, const SliceScale& sc)
 {
     float wh, wl, sh, sl;
     split_fixed(XW, wh, wl);
     split_fixed(XS, sh, sl);
-    const int c = sc.es - sc.ew;  // |b 2^c| <= 1/2 (2^es max|a| and 2^ew differ by >= 2 max|a|)
-    wh = mul_pow2(wh, c);
-    wl = mul_pow2(wl, c);
+    wh = wh * sc.c1 * sc.c2;
+    wl = wl * sc.c1 * sc.c2;
     const float p1 = b * wh;
     const float e1 = fmaf(b, wh, -p1);
     const float t = p1 - sh;  // TwoSum(p1, -sh)
     const float bv = t - p1;
     const float u = (p1 - (t - bv)) + (-sh - bv);
     const float rest = e1 + fmaf(b, wl, -sl) + u;
-    return mul_pow2(t + rest, -sc.es);
+    return (t + rest) * sc.s1 * sc.s2;
 }
 
 // consecutive elements of a tile per thread, loaded as 16-byte vectors
@@ -493,7 +521,7 @@ __global__ void sort_tilescan_kernel(long long* __restrict__ tsum, int T, int cs
 // GRAD: t[pl][m] = 2 W_< - W = sum_n w_n sign(b - a_n) instead (sources whose
 // projection equals b count as below).
 template <bool GRAD>
-__global__ void __launch_bounds__(SORT_THREADS) sort_eval_kernel(const uint32_t* __restrict__ key,
+__global__ void __launch_bounds__(SORT_THREADS, 4) sort_eval_kernel(const uint32_t* __restrict__ key,
                                                                  const uint32_t* __restrict__ pay, int64_t N,
                                                                  int64_t M, int64_t LS, int T,
                                                                  const float* __restrict__ w,
@@ -554,7 +582,7 @@ __global__ void __launch_bounds__(SORT_THREADS) sort_eval_kernel(const uint32_t*
             if (GRAD) {
                 float hi, lo;
                 split_fixed(XW, hi, lo);
-                v = mul_pow2(hi + lo, -sc.ew);
+                v = (hi + lo) * sc.g1 * sc.g2;
             } else {
                 v = sorted_value(key_float(kk[j]), XW, 2 * oa - S, sc);
             }
