@@ -29,8 +29,11 @@ qs_status design_fail(qs_status s, const char* msg)
 }
 
 // Row p of the Gram matrix C (stride ldc) -> weights W = B - A in place,
-// zero in the padding columns P .. ldc-1; r_p; and the row's share of the
-// energy, sum_q (|xi_p - xi_q| + |xi_p + xi_q|), in FP64.  One CTA per row.
+// zero in the padding columns P .. ldc-1; r_p; and (ENERGY) the row's share of
+// the energy, sum_q (|xi_p - xi_q| + |xi_p + xi_q|), in FP64.  One CTA per row.
+// The optimiser's steps need no energy: its two FP64 square roots per pair
+// would cost about as much as the step's contractions on this GPU's FP64 pipe.
+template <bool ENERGY>
 __global__ void __launch_bounds__(256) esym_weights_kernel(float* __restrict__ C, int P, int64_t ldc,
                                                            float* __restrict__ r, double* __restrict__ e_row)
 {
@@ -50,7 +53,7 @@ __global__ void __launch_bounds__(256) esym_weights_kernel(float* __restrict__ C
         const float b = dp2 > 0.0f ? rsqrtf(dp2) : 0.0f;
         row[q] = b - a;
         racc += a + b;
-        eacc += (q == p ? 0.0 : sqrt((double)dm2)) + sqrt((double)dp2);
+        if (ENERGY) eacc += (q == p ? 0.0 : sqrt((double)dm2)) + sqrt((double)dp2);
     }
     __shared__ float rs[8];
     __shared__ double es[8];
@@ -71,7 +74,7 @@ __global__ void __launch_bounds__(256) esym_weights_kernel(float* __restrict__ C
             et += es[i];
         }
         r[p] = rt;
-        e_row[p] = et;
+        if (ENERGY) e_row[p] = et;
     }
 }
 
@@ -171,22 +174,28 @@ __global__ void __launch_bounds__(256) gm_splitk_kernel(const float* __restrict_
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
     // slab loads: row lrow of the W tile and of the T tile, 4 consecutive inner indices from k + lk
-    auto load = [&](int64_t k, float (&ra)[4], float (&rb)[4]) {
+    // as one 16-byte load (rows are 128-float aligned, k + lk is a multiple of 4, and the range end
+    // k1 is a multiple of 8, so a vector lies wholly inside or outside the range)
+    const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    auto load = [&](int64_t k, float4& ra, float4& rb) {
         const int gp = p0 + lrow, gj = j0 + lrow;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int64_t kk = k + lk + i;
-            ra[i] = (gp < P && kk < k1) ? __ldg(&Wt[(size_t)gp * ldc + kk]) : 0.0f;
-            rb[i] = (gj < d && kk < k1) ? __ldg(&T[(size_t)gj * ldc + kk]) : 0.0f;
-        }
+        const int64_t kk = k + lk;
+        ra = (gp < P && kk < k1) ? __ldg(reinterpret_cast<const float4*>(&Wt[(size_t)gp * ldc + kk])) : zero4;
+        rb = (gj < d && kk < k1) ? __ldg(reinterpret_cast<const float4*>(&T[(size_t)gj * ldc + kk])) : zero4;
     };
-    float ra[4], rb[4];
+    auto put = [&](int buf, const float4& ra, const float4& rb) {
+        As[buf][lk + 0][lrow] = ra.x;
+        As[buf][lk + 1][lrow] = ra.y;
+        As[buf][lk + 2][lrow] = ra.z;
+        As[buf][lk + 3][lrow] = ra.w;
+        Bs[buf][lk + 0][lrow] = rb.x;
+        Bs[buf][lk + 1][lrow] = rb.y;
+        Bs[buf][lk + 2][lrow] = rb.z;
+        Bs[buf][lk + 3][lrow] = rb.w;
+    };
+    float4 ra, rb;
     load(k0, ra, rb);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        As[0][lk + i][lrow] = ra[i];
-        Bs[0][lk + i][lrow] = rb[i];
-    }
+    put(0, ra, rb);
     __syncthreads();
     const int nk = (int)((k1 - k0 + SK_BK - 1) / SK_BK);
     for (int kt = 0; kt < nk; ++kt) {
@@ -205,13 +214,7 @@ __global__ void __launch_bounds__(256) gm_splitk_kernel(const float* __restrict_
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
-        if (kt + 1 < nk) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                As[cur ^ 1][lk + i][lrow] = ra[i];
-                Bs[cur ^ 1][lk + i][lrow] = rb[i];
-            }
-        }
+        if (kt + 1 < nk) put(cur ^ 1, ra, rb);
         __syncthreads();
     }
 #pragma unroll
@@ -267,13 +270,25 @@ struct DesignWork {
         if (adam && err == cudaSuccess) err = cudaMalloc(&v, sizeof(float) * (size_t)P * d);
         if (adam && err == cudaSuccess) err = cudaMemset(m, 0, sizeof(float) * (size_t)P * d);
         if (adam && err == cudaSuccess) err = cudaMemset(v, 0, sizeof(float) * (size_t)P * d);
-        // split the inner length of the second contraction so that its tiles fill the GPU
-        // about four times over (152 SMs); each range a multiple of the slab depth
+        // split the inner length of the second contraction into ks ranges (multiples of the
+        // slab depth, at least 256 long, at most 20) so that tiles x ks CTAs fill whole waves
+        // of the resident CTAs as nearly as possible (fewer ranges on a tie)
         const int64_t tiles = (((int64_t)P + 127) / 128) * (ldg / 128);
-        ks = (int)((4 * 152 + tiles - 1) / tiles);
-        if (ks > 16) ks = 16;
-        if (ks > ldc / 256) ks = (int)(ldc / 256);
-        if (ks < 1) ks = 1;
+        int dev = 0, sms = 1, occ = 1;
+        if (err == cudaSuccess) err = cudaGetDevice(&dev);
+        if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gm_splitk_kernel, 256, 0);
+        const int64_t resident = (int64_t)sms * (occ > 0 ? occ : 1);
+        ks = 1;
+        double best = -1.0;
+        for (int k = 1; k <= 20 && (k == 1 || ldc / k >= 256); ++k) {
+            const int64_t ctas = tiles * k;
+            const double eff = (double)ctas / (double)(((ctas + resident - 1) / resident) * resident);
+            if (eff > best + 1e-9) {
+                best = eff;
+                ks = k;
+            }
+        }
         kc = ((ldc + ks - 1) / ks + 7) / 8 * 8;
         ks = (int)((ldc + kc - 1) / kc);
         if (ks > 1 && err == cudaSuccess) err = cudaMalloc(&parts, sizeof(float) * (size_t)ks * P * ldg);
@@ -282,11 +297,12 @@ struct DesignWork {
 };
 
 // Energy terms and the gradient pieces (r, Gm) of the rows in xi.
-cudaError_t esym_pieces(const float* xi, int d, int P, DesignWork& w, cudaStream_t st)
+cudaError_t esym_pieces(const float* xi, int d, int P, DesignWork& w, cudaStream_t st, bool energy)
 {
     cudaError_t e = qs_launch_project_fp32(xi, P, d, xi, P, w.C, w.ldc, st);  // C = Xi Xi^T
     if (e != cudaSuccess) return e;
-    esym_weights_kernel<<<P, 256, 0, st>>>(w.C, P, w.ldc, w.r, w.e);
+    if (energy) esym_weights_kernel<true><<<P, 256, 0, st>>>(w.C, P, w.ldc, w.r, w.e);
+    else esym_weights_kernel<false><<<P, 256, 0, st>>>(w.C, P, w.ldc, w.r, w.e);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 tg((unsigned)((w.ldc + 31) / 32), (unsigned)((d + 31) / 32));
@@ -335,7 +351,7 @@ extern "C" qs_status qs_distance_energy(const float* dirs_dev, int d, int P, dou
     DesignWork w;
     cudaError_t e = w.alloc(d, P, false);
     if (e != cudaSuccess) return design_fail(QS_ERR_OOM, "qs_distance_energy: workspace allocation failed");
-    e = esym_pieces(dirs_dev, d, P, w, st);
+    e = esym_pieces(dirs_dev, d, P, w, st, true);
     if (e == cudaSuccess && grad_dev) {
         // m == NULL: the kernel only reads xi and writes the gradient
         esym_step_kernel<<<P, 256, 0, st>>>(const_cast<float*>(dirs_dev), d, w.r, w.Gm, w.ldg, grad_dev, nullptr,
@@ -363,7 +379,7 @@ extern "C" qs_status qs_distance_design(float* dirs_dev, int d, int P, int iters
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     double b1t = 1.0, b2t = 1.0;
     for (int it = 0; it < iters && e == cudaSuccess; ++it) {
-        e = esym_pieces(dirs_dev, d, P, w, st);
+        e = esym_pieces(dirs_dev, d, P, w, st, false);
         if (e != cudaSuccess) break;
         b1t *= b1;
         b2t *= b2;
@@ -374,7 +390,7 @@ extern "C" qs_status qs_distance_design(float* dirs_dev, int d, int P, int iters
                                             (float)b1t, (float)b2t, eps);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && energy) e = esym_pieces(dirs_dev, d, P, w, st);
+    if (e == cudaSuccess && energy) e = esym_pieces(dirs_dev, d, P, w, st, true);
     if (e != cudaSuccess) return design_fail(QS_ERR_CUDA, cudaGetErrorString(e));
     if (energy && sum_energy(w, P, st, energy) != QS_OK)
         return design_fail(QS_ERR_CUDA, "qs_distance_design: readback");
