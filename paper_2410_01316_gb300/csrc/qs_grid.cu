@@ -929,23 +929,13 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
     // from the even / odd tap polynomials), the bins' polynomials Q, the
     // block's bin range
     constexpr int KQ = qs_moment_count(W);
-    constexpr int TQ = qs_tap_terms(W);
     const int H0 = (G >> 1) + W / 2;
-    __shared__ float atab[W * KQ];
     __shared__ float qwin[KQ * QWIN];
     __shared__ int s_krange[2][2];  // per slice parity: block-wide [min, max] bin
     if (threadIdx.x < 2) {
         s_krange[threadIdx.x][0] = INT_MAX;
         s_krange[threadIdx.x][1] = INT_MIN;
     }  // first read after the loop's first barrier
-    for (int idx = threadIdx.x; idx < W * KQ; idx += IT_THREADS) {
-        const int j = idx / KQ, k = idx - j * KQ;
-        const int jj = j < W / 2 ? j : W - 1 - j;
-        const int i2 = k >> 1;
-        float a = 0.0f;
-        if (i2 < TQ) a = (k & 1) ? (j < W / 2 ? L.win.o[jj][i2] : -L.win.o[jj][i2]) : L.win.e[jj][i2];
-        atab[idx] = ldexpf(a, -k);
-    }
 
     float yr[FUSED ? DMAX * TPT : 1];
     float hi[TPT], lo[TPT];
@@ -1087,14 +1077,21 @@ __global__ void __launch_bounds__(IT_THREADS) interp_kernel(qs_launch L, const f
             // the CTA's targets of this slice fall in few bins: per bin b the
             // polynomial Q_b(t) = sum_j h[b + j] tap_j(t) (coefficients
             // sum_j a_jk h[b + j]), then a target costs a Horner evaluation
+            // one thread per bin: its W row cells read once, the tap coefficients
+            // a_jk 2^-k taken from the launch parameters as constant operands
             const int nb = kmax - kmin + 1;
-            for (int idx = threadIdx.x; idx < nb * KQ; idx += IT_THREADS) {
-                const int b = idx / KQ, k = idx - b * KQ;
+            for (int b = threadIdx.x; b < nb; b += IT_THREADS) {
                 const int c0 = kmin + b - H0;
-                float q = 0.0f;
+                float r[W];
 #pragma unroll
-                for (int j = 0; j < W; ++j) q = fmaf(atab[j * KQ + k], row[(c0 + j) & mask], q);
-                qwin[k * QWIN + b] = q;  // coefficient-major: lanes at different bins hit different banks
+                for (int j = 0; j < W; ++j) r[j] = row[(c0 + j) & mask];
+#pragma unroll
+                for (int k = 0; k < KQ; ++k) {
+                    float q = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < W; ++j) q = fmaf(L.atab[j * KQ + k], r[j], q);
+                    qwin[k * QWIN + b] = q;  // coefficient-major: lanes at different bins hit different banks
+                }
             }
             __syncthreads();
             if constexpr (TPT % 2 == 0) {

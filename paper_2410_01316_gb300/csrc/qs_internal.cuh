@@ -102,6 +102,10 @@ struct qs_launch {
     float* wscale;        // [0] = 2^30 / sum|w| (fixed-point scale of the grids), [1] = its inverse
     int spread_variant;   // QS_SPREAD_* (all variants give bitwise identical grids)
     qs_window win;
+    // tap polynomials in monomials of t = 2 s: tap_j(t) = sum_k atab[j K + k] t^k, K = qs_moment_count(W)
+    // (qs_fill_atab); in the launch parameters, so the interpolation's bin expansion takes them as
+    // constant operands
+    float atab[QS_MAX_W * QS_MAX_W];
 };
 
 struct qs_plan_s {
@@ -250,6 +254,7 @@ __host__ __device__ inline int qs_interp_tpt(bool fused, int d, int G)
 double qs_tau_rule(qs_kernel kernel, double kparam, double R);
 void qs_gauss_legendre(int n, double* x, double* w);
 void qs_fit_window(int W, int kind, qs_window* win);
+void qs_fill_atab(const qs_window* win, int W, float* atab);
 double qs_window_tap(const qs_window* win, int W, int j, double s);
 void qs_window_transform(const qs_window* win, int W, int K, int G, double* out);  // out[K + 1]
 void qs_twiddles(int G, float2* out);                                               // out[G / 2]

@@ -253,6 +253,7 @@ extern "C" qs_status qs_sum_noalloc(const qs_plan_desc* desc, const float* dirs_
             return nfail(QS_ERR_CUDA, "qs_sum_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
         const TableEntry& tb = tables_for(W, D.window_kind, G);
         L.win = tb.win;
+        qs_fill_atab(&tb.win, W, L.atab);  // into the launch parameters; no allocation
         // pageable source: each copy has been staged when the call returns, so
         // the cache slot may be reused by a later call
         e = cudaMemcpyAsync(base + o_psihat, tb.psihat, (size_t)(K + 1) * 8, cudaMemcpyHostToDevice, st);

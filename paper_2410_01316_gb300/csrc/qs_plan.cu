@@ -242,6 +242,7 @@ qs_launch make_launch(const qs_plan p, int64_t N, int64_t M, int64_t targets_per
     L.wscale = p->d_wscale;
     L.spread_variant = p->spread_variant;
     L.win = p->win;
+    qs_fill_atab(&p->win, p->W, L.atab);
     // slice groups of the interpolation: enough CTAs to fill the device,
     // chosen from M and P only so results do not depend on the GPU model
     const int64_t blocks_m = (M + targets_per_cta - 1) / targets_per_cta;

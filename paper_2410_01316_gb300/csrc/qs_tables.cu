@@ -116,6 +116,22 @@ void qs_fit_window(int W, int kind, qs_window* win)
     }
 }
 
+// The tap polynomials in monomials of t = 2 s (s the centred offset):
+// atab[j K + k] = a_jk 2^-k with tap_j(s) = sum_k a_jk s^k from the even / odd
+// parts (the second half mirrored: tap_{W-1-j}(s) = tap_j(-s)), K = qs_moment_count(W).
+void qs_fill_atab(const qs_window* win, int W, float* atab)
+{
+    const int K = qs_moment_count(W), T = qs_tap_terms(W);
+    for (int j = 0; j < W; ++j)
+        for (int k = 0; k < K; ++k) {
+            const int jj = j < W / 2 ? j : W - 1 - j;
+            const int i2 = k >> 1;
+            float a = 0.0f;
+            if (i2 < T) a = (k & 1) ? (j < W / 2 ? win->o[jj][i2] : -win->o[jj][i2]) : win->e[jj][i2];
+            atab[j * K + k] = ldexpf(a, -k);
+        }
+}
+
 // The FP32 tap polynomial of tap j at offset s, evaluated in double.
 double qs_window_tap(const qs_window* win, int W, int j, double s)
 {
