@@ -889,7 +889,9 @@ def run_mmd_flow(args, rank, world, local_rank, emit=True):
 def run_design(args, rank, world, local, emit=True):
     """Distance QMC design generator (Sec. 4.1 "Distance"; eq. distance-sym) at the paper's largest
     reported size, d = 200 and P = 5000: Adam steps per second.  One step = Gram matrix + pairwise
-    weights + (B - A) Xi + Adam/renormalise, i.e. 4 P^2 d FP32 flop in two SIMT GEMMs."""
+    weights + (B - A) Xi + Adam/renormalise, i.e. 4 P^2 d flop in two contractions on the tcgen05
+    GEMM in BF16x3 (12 P^2 d BF16 flop); the roofline divides that by the whole step's time and the
+    measured BF16 peak (the weights, operand splits and update take about as long as the GEMMs)."""
     import torch
 
     from paper_2410_01316_gb300 import build as qbuild
@@ -923,10 +925,9 @@ def run_design(args, rank, world, local, emit=True):
     clocks = sampler.stop()
     t = sum(ms) / 1e3
     n_it = iters * args.steps
-    flops = 4.0 * P * P * d
-    mhz = clocks.get("sm_mhz") or 2070.0
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sm_count * 128 * 2 * mhz * 1e6 / 1e12
+    flops = 3 * 4.0 * P * P * d
+    peaks, peak_src = _peaks()
+    peak = peaks["bf16_tflops"]
     achieved = flops * n_it / t / 1e12
     line = {"metric": "distance QMC design: Adam steps per second", "value": n_it / t, "unit": "steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / n_it,
@@ -934,10 +935,13 @@ def run_design(args, rank, world, local, emit=True):
             "config": {"workload": f"distance_design: d={d} P={P}, {iters} Adam steps per timed call "
                                    f"(workspace allocation included), start = seeded orthogonal design",
                        "energy_start": e_orth, "energy_after": energies},
-            "roofline": {"kernel": "design step", "bound": "alu", "achieved": achieved, "peak": peak,
+            "roofline": {"kernel": "design step", "bound": "tensor", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "algorithmic": f"4 P^2 d = {flops:.3e} FP32 flop per step (two P x P x d contractions)",
-                         "peak_source": f"{sm_count} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"},
+                         "algorithmic": f"3 x 4 P^2 d = {flops:.3e} BF16 flop per step (two P x P x d "
+                                        "contractions in BF16x3 on tcgen05) over the whole step, which also "
+                                        "holds the pairwise weights, the operand splits, the range "
+                                        "reduction and the Adam update",
+                         "peak_source": f"bf16_tflops ({peak_src}, burst)"},
             "clocks": clocks, "gpu_launches": n_it * 5 + args.steps * 4}
     if rank == 0 and emit:
         print(json.dumps(line), flush=True)

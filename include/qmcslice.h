@@ -430,9 +430,8 @@ qs_status qs_plan_gemm(qs_plan plan, int* pair, int* ctas);
  * exactly, without the Fourier truncation, by sorting each slice's source
  * and target projections (FP32, from the FP32 SIMT projection) together and
  * scanning prefix sums of w and w a in 64-bit fixed point (exact integer
- * sums with per-slice scales, converted to FP64 per target):
- * sum_n w_n |b - a_n| =
- * b (2 W_< - W) - (2 S_< - S).  Arguments as for qs_sum.  Needs a QS_NEGDIST
+ * sums with per-slice scales, combined per target in error-free FP32
+ * arithmetic): sum_n w_n |b - a_n| = b (2 W_< - W) - (2 S_< - S).  Arguments as for qs_sum.  Needs a QS_NEGDIST
  * plan with d <= 64 (QS_ERR_UNSUPPORTED otherwise).  The first call allocates
  * the plan's sorting workspace (about 20 CS (max_n + max_m) + 8 CS max_m
  * bytes, CS = min(P, 128) slices per chunk) and so synchronises; later calls
@@ -467,11 +466,18 @@ qs_status qs_grad_sorted(qs_plan plan, const float* x, int64_t N, const float* w
  * QS_DIR_ORTHOGONAL); if energy is not NULL it receives E_sym of the result.
  * qs_distance_energy: E_sym of the rows in dirs_dev and, if grad_dev is not
  * NULL, its Euclidean gradient dE/dxi (P x d device array, caller-owned).
- * Both are set-up routines, not part of the sum: they allocate and free a
- * workspace of about 4 P^2 + 12 P d bytes on the current device, run on
- * `stream` and return when it is done.  Errors: QS_ERR_ARG (NULL pointer,
+ * Both contractions of a step (the Gram matrix and (B - A) Xi, P x P x d
+ * each) run on the tcgen05 GEMM in BF16x3 (split operands, FP32
+ * accumulation), the second as up to 20 inner ranges on streams of the
+ * routine's own; the weights of near-parallel or near-antipodal pairs
+ * (|c_pq| > 1/2) take |xi_p -+ xi_q|^2 from the rows instead of 2 -+ 2 c_pq.
+ * d up to ~58000.  Both are set-up routines, not part of the sum: they
+ * allocate and free a workspace of about 8 P^2 + (20 + 4 ks) P d' bytes
+ * (d' = d rounded up to 128, ks <= 20 the ranges) on the current device,
+ * run on `stream` and return when it is done.  Errors: QS_ERR_ARG (NULL pointer,
  * d or P < 1, iters < 0, lr <= 0), QS_ERR_UNSUPPORTED (P^2 beyond 2^31),
- * QS_ERR_OOM, QS_ERR_CUDA.
+ * QS_ERR_OOM, QS_ERR_CUDA (also when a GEMM wait ran out; the device flag of
+ * plans is not involved).
  */
 qs_status qs_distance_design(float* dirs_dev, int d, int P, int iters, double lr, double* energy, void* stream);
 qs_status qs_distance_energy(const float* dirs_dev, int d, int P, double* energy, float* grad_dev, void* stream);

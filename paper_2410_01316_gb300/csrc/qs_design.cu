@@ -10,8 +10,13 @@
 // For unit rows |xi_p -+ xi_q|^2 = 2 -+ 2 c_pq with c = Xi Xi^T, so with
 // a_pq = 1/sqrt(2 - 2c) (0 on the diagonal) and b_pq = 1/sqrt(2 + 2c):
 //   dE/dxi_p = -4 [ xi_p r_p + sum_q (b_pq - a_pq) xi_q ],  r_p = sum_q (a_pq + b_pq),
-// i.e. two P x P x d contractions (the Gram matrix and (B - A) Xi) done by
-// the library's FP32 SIMT GEMM, plus elementwise work.
+// i.e. two P x P x d contractions plus elementwise work, both on the
+// library's tcgen05 GEMM in BF16x3 (split operands, FP32 accumulation; the
+// products carry ~2^-16 relative error).  a_pq would amplify an error in c_pq
+// by about a_pq^3 for near-coincident directions (in d = 3 with P = 1000,
+// taking 2 - 2c from the split-BF16 Gram moved the gradient by 6.5e-4 of its
+// largest entry), so the weights take |xi_p -+ xi_q|^2 from the rows for
+// |c| > 1/2 (esym_weights_kernel).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -31,13 +36,22 @@ qs_status design_fail(qs_status s, const char* msg)
 // Row p of the Gram matrix C (stride ldc) -> weights W = B - A in place,
 // zero in the padding columns P .. ldc-1; r_p; and (ENERGY) the row's share of
 // the energy, sum_q (|xi_p - xi_q| + |xi_p + xi_q|), in FP64.  One CTA per row.
-// The optimiser's steps need no energy: its two FP64 square roots per pair
-// would cost about as much as the step's contractions on this GPU's FP64 pipe.
+// |xi_p -+ xi_q|^2 is 2 -+ 2 c_pq except for near-parallel (c > 1/2) or
+// near-antipodal (c < -1/2) pairs, where it is summed from the rows
+// themselves: there 1/|xi_p -+ xi_q| would multiply the error of c by up to
+// its cube (and 2 -+ 2c cancels), elsewhere the weights change by at most the
+// error of c.  The optimiser's steps need no energy: its two FP64 square roots
+// per pair would cost about as much as the step's contractions on this GPU's
+// FP64 pipe.
 template <bool ENERGY>
 __global__ void __launch_bounds__(256) esym_weights_kernel(float* __restrict__ C, int P, int64_t ldc,
+                                                           const float* __restrict__ xi, int d,
                                                            float* __restrict__ r, double* __restrict__ e_row)
 {
+    extern __shared__ float xp[];  // row p of xi
     const int p = blockIdx.x;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) xp[j] = xi[(size_t)p * d + j];
+    __syncthreads();
     float* row = C + (size_t)p * ldc;
     float racc = 0.0f;
     double eacc = 0.0;
@@ -47,7 +61,18 @@ __global__ void __launch_bounds__(256) esym_weights_kernel(float* __restrict__ C
             continue;
         }
         const float c = fminf(1.0f, fmaxf(-1.0f, row[q]));
-        const float dm2 = 2.0f - 2.0f * c, dp2 = 2.0f + 2.0f * c;
+        float dm2 = 2.0f - 2.0f * c, dp2 = 2.0f + 2.0f * c;
+        if (c > 0.5f || c < -0.5f) {
+            const float sg = c > 0.0f ? -1.0f : 1.0f;  // xi_p - xi_q or xi_p + xi_q
+            const float* xq = xi + (size_t)q * d;
+            float s2 = 0.0f;
+            for (int j = 0; j < d; ++j) {
+                const float t = fmaf(sg, __ldg(&xq[j]), xp[j]);
+                s2 = fmaf(t, t, s2);
+            }
+            if (c > 0.0f) dm2 = s2;
+            else dp2 = s2;
+        }
         // coincident or antipodal pairs have no gradient direction: weight 0
         const float a = (q == p || dm2 <= 0.0f) ? 0.0f : rsqrtf(dm2);
         const float b = dp2 > 0.0f ? rsqrtf(dp2) : 0.0f;
@@ -146,88 +171,7 @@ __global__ void __launch_bounds__(256) esym_step_kernel(float* __restrict__ xi, 
     for (int j = threadIdx.x; j < d; j += blockDim.x) x[j] *= inv;
 }
 
-// Split-K form of the second contraction Gm[p][j] = sum_q W[p][q] T[j][q]
-// (W the P x ldc weights, T = Xi^T padded to ldc columns): its P x d output
-// has few 128 x 128 tiles (80 at P = 5000, d = 200) for a long inner length,
-// so CTA (p tile, j tile, z) sums the inner range [z kc, (z + 1) kc) into its
-// own partial (parts[z], P x ldg) with the FP32 SIMT tile of the projection
-// (8 x 8 outputs per thread, 8-deep slabs double-buffered in shared memory),
-// and gm_reduce_kernel adds the partials in z order, so the result does not
-// depend on scheduling.  kc is a multiple of the slab depth.
-constexpr int SK_BM = 128, SK_BN = 128, SK_BK = 8;
-
-__global__ void __launch_bounds__(256) gm_splitk_kernel(const float* __restrict__ Wt, int P, int64_t ldc,
-                                                        const float* __restrict__ T, int d, int64_t kc,
-                                                        float* __restrict__ parts, int64_t ldg)
-{
-    __shared__ __align__(16) float As[2][SK_BK][SK_BM];
-    __shared__ __align__(16) float Bs[2][SK_BK][SK_BN];
-    const int p0 = blockIdx.x * SK_BM, j0 = blockIdx.y * SK_BN;
-    const int64_t k0 = (int64_t)blockIdx.z * kc;
-    const int64_t k1 = k0 + kc < ldc ? k0 + kc : ldc;
-    float* out = parts + (size_t)blockIdx.z * (size_t)P * ldg;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int lrow = tid >> 1, lk = (tid & 1) * 4;
-    float acc[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
-    // slab loads: row lrow of the W tile and of the T tile, 4 consecutive inner indices from k + lk
-    // as one 16-byte load (rows are 128-float aligned, k + lk is a multiple of 4, and the range end
-    // k1 is a multiple of 8, so a vector lies wholly inside or outside the range)
-    const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    auto load = [&](int64_t k, float4& ra, float4& rb) {
-        const int gp = p0 + lrow, gj = j0 + lrow;
-        const int64_t kk = k + lk;
-        ra = (gp < P && kk < k1) ? __ldg(reinterpret_cast<const float4*>(&Wt[(size_t)gp * ldc + kk])) : zero4;
-        rb = (gj < d && kk < k1) ? __ldg(reinterpret_cast<const float4*>(&T[(size_t)gj * ldc + kk])) : zero4;
-    };
-    auto put = [&](int buf, const float4& ra, const float4& rb) {
-        As[buf][lk + 0][lrow] = ra.x;
-        As[buf][lk + 1][lrow] = ra.y;
-        As[buf][lk + 2][lrow] = ra.z;
-        As[buf][lk + 3][lrow] = ra.w;
-        Bs[buf][lk + 0][lrow] = rb.x;
-        Bs[buf][lk + 1][lrow] = rb.y;
-        Bs[buf][lk + 2][lrow] = rb.z;
-        Bs[buf][lk + 3][lrow] = rb.w;
-    };
-    float4 ra, rb;
-    load(k0, ra, rb);
-    put(0, ra, rb);
-    __syncthreads();
-    const int nk = (int)((k1 - k0 + SK_BK - 1) / SK_BK);
-    for (int kt = 0; kt < nk; ++kt) {
-        const int cur = kt & 1;
-        if (kt + 1 < nk) load(k0 + (int64_t)(kt + 1) * SK_BK, ra, rb);
-#pragma unroll
-        for (int k = 0; k < SK_BK; ++k) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][k][64 + ty * 4]);
-            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
-            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][k][64 + tx * 4]);
-            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-        if (kt + 1 < nk) put(cur ^ 1, ra, rb);
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int p = p0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
-        if (p >= P) continue;
-        float* row = out + (size_t)p * ldg + j0;
-        *reinterpret_cast<float4*>(row + tx * 4) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-        *reinterpret_cast<float4*>(row + 64 + tx * 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
-    }
-}
-
-// Gm[p][j] = sum_z parts[z][p][j] in z order (j < ldg; the padding columns are zero in every part)
+// Gm[p][j] = sum_z parts[z][p][j] in z order (j < ldg; every part covers all of it)
 __global__ void gm_reduce_kernel(const float* __restrict__ parts, int ks, int64_t n, float* __restrict__ Gm)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -237,87 +181,165 @@ __global__ void gm_reduce_kernel(const float* __restrict__ parts, int ks, int64_
     Gm[i] = v;
 }
 
+constexpr int KMAX_SPLITS = 20;
+constexpr int TMAP_BYTES = 128;  // sizeof(CUtensorMap)
+
 // Device workspace of one call (allocated per call: this is a set-up
-// routine, not part of the sum).  The GEMM stores whole 128-column blocks,
-// so the Gram rows (ldc) and the gradient rows (ldg) are padded to 128.
+// routine, not part of the sum).  Both contractions run on the tcgen05 GEMM
+// in BF16x3 (hi hi + hi lo + lo hi, FP32 accumulation), which computes
+// U[p][n] = <A_n, B_p> for rows A_n of its first operand and B_p of its
+// second and stores whole 128-row tiles of A:
+//   the Gram matrix C = Xi Xi^T      A = B = Xi (K = d), U = C (stride ldc);
+//   Gm = (B - A) Xi = W Xi            A = T = Xi^T (d rows), B = W (P rows),
+//                                     K = ldc split into ks ranges of kc, one
+//                                     GEMM each on its own stream (the d x P
+//                                     output has few tiles for its long inner
+//                                     length, so one launch would leave most
+//                                     SMs idle), whose partial Gm (stride ldg)
+//                                     are summed in range order.
+// Rows of C and Gm are padded to 128 for the whole-tile stores; the weights
+// are zero in the padding columns, so the ranges cover exactly the inner sum.
 struct DesignWork {
     float *C = nullptr, *T = nullptr, *Gm = nullptr, *r = nullptr, *m = nullptr, *v = nullptr;
-    float* parts = nullptr;  // split-K partials of Gm (ks x P x ldg)
+    float* parts = nullptr;  // partial Gm of the inner ranges (ks x P x ldg)
     double* e = nullptr;
+    void *xh = nullptr, *xl = nullptr, *wh = nullptr, *wl = nullptr, *th = nullptr, *tl = nullptr;  // BF16 hi / lo
+    unsigned int* flag = nullptr;  // the GEMM's timeout flag
+    cudaStream_t ss[KMAX_SPLITS] = {};  // one per inner range
+    cudaEvent_t fork = nullptr, done[KMAX_SPLITS] = {};
     int64_t ldc = 0, ldg = 0, kc = 0;
-    int ks = 1;
+    int ldk = 0, ks = 1;
+    alignas(64) unsigned char gram_maps[4 * TMAP_BYTES];             // A0 A1 (Xi), B0 B1 (Xi)
+    alignas(64) unsigned char gm_maps[KMAX_SPLITS][4 * TMAP_BYTES];  // per range: A0 A1 (T), B0 B1 (W)
     ~DesignWork()
     {
-        cudaFree(parts);
-        cudaFree(C);
-        cudaFree(T);
-        cudaFree(Gm);
-        cudaFree(r);
-        cudaFree(m);
-        cudaFree(v);
-        cudaFree(e);
+        void* bufs[] = {parts, C, T, Gm, r, m, v, e, xh, xl, wh, wl, th, tl, flag};
+        for (void* b : bufs) cudaFree(b);
+        for (int z = 0; z < KMAX_SPLITS; ++z) {
+            if (ss[z]) cudaStreamDestroy(ss[z]);
+            if (done[z]) cudaEventDestroy(done[z]);
+        }
+        if (fork) cudaEventDestroy(fork);
     }
     cudaError_t alloc(int d, int P, bool adam)
     {
         ldc = ((int64_t)P + 127) / 128 * 128;
         ldg = ((int64_t)d + 127) / 128 * 128;
+        ldk = (d + 7) / 8 * 8;
         cudaError_t err = cudaMalloc(&C, sizeof(float) * (size_t)P * ldc);
         if (err == cudaSuccess) err = cudaMalloc(&T, sizeof(float) * (size_t)d * ldc);
         if (err == cudaSuccess) err = cudaMalloc(&Gm, sizeof(float) * (size_t)P * ldg);
         if (err == cudaSuccess) err = cudaMalloc(&r, sizeof(float) * (size_t)P);
         if (err == cudaSuccess) err = cudaMalloc(&e, sizeof(double) * (size_t)P);
+        if (err == cudaSuccess) err = cudaMalloc(&xh, 2 * (size_t)P * ldk);
+        if (err == cudaSuccess) err = cudaMalloc(&xl, 2 * (size_t)P * ldk);
+        if (err == cudaSuccess) err = cudaMalloc(&wh, 2 * (size_t)P * ldc);
+        if (err == cudaSuccess) err = cudaMalloc(&wl, 2 * (size_t)P * ldc);
+        if (err == cudaSuccess) err = cudaMalloc(&th, 2 * (size_t)d * ldc);
+        if (err == cudaSuccess) err = cudaMalloc(&tl, 2 * (size_t)d * ldc);
+        if (err == cudaSuccess) err = cudaMalloc(&flag, sizeof(unsigned int));
+        if (err == cudaSuccess) err = cudaMemset(flag, 0, sizeof(unsigned int));
         if (adam && err == cudaSuccess) err = cudaMalloc(&m, sizeof(float) * (size_t)P * d);
         if (adam && err == cudaSuccess) err = cudaMalloc(&v, sizeof(float) * (size_t)P * d);
         if (adam && err == cudaSuccess) err = cudaMemset(m, 0, sizeof(float) * (size_t)P * d);
         if (adam && err == cudaSuccess) err = cudaMemset(v, 0, sizeof(float) * (size_t)P * d);
-        // split the inner length of the second contraction into ks ranges (multiples of the
-        // slab depth, at least 256 long, at most 20) so that tiles x ks CTAs fill whole waves
-        // of the resident CTAs as nearly as possible (fewer ranges on a tie)
-        const int64_t tiles = (((int64_t)P + 127) / 128) * (ldg / 128);
-        int dev = 0, sms = 1, occ = 1;
-        if (err == cudaSuccess) err = cudaGetDevice(&dev);
+        if (err != cudaSuccess) return err;
+        // inner ranges of the second contraction: multiples of 64, at least 256 long (unless
+        // there is one), at most KMAX_SPLITS, chosen so that the ranges' tiles together fill
+        // whole waves of one GEMM CTA per SM as nearly as possible (fewer ranges on a tie)
+        int dev = 0, sms = 1;
+        err = cudaGetDevice(&dev);
         if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gm_splitk_kernel, 256, 0);
-        const int64_t resident = (int64_t)sms * (occ > 0 ? occ : 1);
+        if (err != cudaSuccess) return err;
+        const int64_t tiles = (ldg / 128) * (((int64_t)P + 255) / 256);
         ks = 1;
+        kc = ldc;
         double best = -1.0;
-        for (int k = 1; k <= 20 && (k == 1 || ldc / k >= 256); ++k) {
-            const int64_t ctas = tiles * k;
-            const double eff = (double)ctas / (double)(((ctas + resident - 1) / resident) * resident);
+        for (int k = 1; k <= KMAX_SPLITS; ++k) {
+            const int64_t kck = ((ldc + k - 1) / k + 63) / 64 * 64;
+            const int ksk = (int)((ldc + kck - 1) / kck);
+            if (ksk > 1 && kck < 256) break;
+            const int64_t t = tiles * ksk;
+            const double eff = (double)t / (double)(((t + sms - 1) / sms) * sms);
             if (eff > best + 1e-9) {
                 best = eff;
-                ks = k;
+                ks = ksk;
+                kc = kck;
             }
         }
-        kc = ((ldc + ks - 1) / ks + 7) / 8 * 8;
-        ks = (int)((ldc + kc - 1) / kc);
-        if (ks > 1 && err == cudaSuccess) err = cudaMalloc(&parts, sizeof(float) * (size_t)ks * P * ldg);
-        return err;
+        if (ks > 1) err = cudaMalloc(&parts, sizeof(float) * (size_t)ks * P * ldg);
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        for (int z = 0; z < ks && err == cudaSuccess; ++z) {
+            err = cudaStreamCreateWithFlags(&ss[z], cudaStreamNonBlocking);
+            if (err == cudaSuccess) err = cudaEventCreateWithFlags(&done[z], cudaEventDisableTiming);
+        }
+        if (err != cudaSuccess) return err;
+        // tensor maps (K-major BF16 rows; coordinates past a range's end read zeros)
+        unsigned char* g = gram_maps;
+        bool ok = qs_make_tmap(g + 0 * TMAP_BYTES, xh, 2, d, P, ldk, 128) &&
+                  qs_make_tmap(g + 1 * TMAP_BYTES, xl, 2, d, P, ldk, 128) &&
+                  qs_make_tmap(g + 2 * TMAP_BYTES, xh, 2, d, P, ldk, 256) &&
+                  qs_make_tmap(g + 3 * TMAP_BYTES, xl, 2, d, P, ldk, 256);
+        for (int z = 0; ok && z < ks; ++z) {
+            const int64_t k0 = (int64_t)z * kc;
+            const int klen = (int)(ldc - k0 < kc ? ldc - k0 : kc);
+            unsigned char* q = gm_maps[z];
+            const size_t off = 2 * (size_t)k0;  // bytes: a multiple of 128
+            ok = qs_make_tmap(q + 0 * TMAP_BYTES, (char*)th + off, 2, klen, d, (int)ldc, 128) &&
+                 qs_make_tmap(q + 1 * TMAP_BYTES, (char*)tl + off, 2, klen, d, (int)ldc, 128) &&
+                 qs_make_tmap(q + 2 * TMAP_BYTES, (char*)wh + off, 2, klen, P, (int)ldc, 256) &&
+                 qs_make_tmap(q + 3 * TMAP_BYTES, (char*)wl + off, 2, klen, P, (int)ldc, 256);
+        }
+        return ok ? cudaSuccess : cudaErrorInvalidValue;
     }
 };
 
 // Energy terms and the gradient pieces (r, Gm) of the rows in xi.
 cudaError_t esym_pieces(const float* xi, int d, int P, DesignWork& w, cudaStream_t st, bool energy)
 {
-    cudaError_t e = qs_launch_project_fp32(xi, P, d, xi, P, w.C, w.ldc, st);  // C = Xi Xi^T
+    // C = Xi Xi^T
+    cudaError_t e = qs_launch_split_bf16(xi, P, d, w.ldk, w.xh, w.xl, st);
+    if (e == cudaSuccess) e = qs_launch_project_tc(0, w.gram_maps, 0, P, d, P, w.C, w.ldc, w.flag, st, false);
     if (e != cudaSuccess) return e;
-    if (energy) esym_weights_kernel<true><<<P, 256, 0, st>>>(w.C, P, w.ldc, w.r, w.e);
-    else esym_weights_kernel<false><<<P, 256, 0, st>>>(w.C, P, w.ldc, w.r, w.e);
+    const size_t xs = sizeof(float) * (size_t)d;  // row p in shared memory
+    if (xs > 48 * 1024) {
+        e = cudaFuncSetAttribute(esym_weights_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(esym_weights_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
+        if (e != cudaSuccess) return e;
+    }
+    if (energy) esym_weights_kernel<true><<<P, 256, xs, st>>>(w.C, P, w.ldc, xi, d, w.r, w.e);
+    else esym_weights_kernel<false><<<P, 256, xs, st>>>(w.C, P, w.ldc, xi, d, w.r, w.e);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 tg((unsigned)((w.ldc + 31) / 32), (unsigned)((d + 31) / 32));
     transpose_pad_kernel<<<tg, dim3(32, 8), 0, st>>>(xi, P, d, w.ldc, w.T);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // Gm[p][j] = sum_q W[p][q] Xi[q][j]: rows of W against rows of Xi^T, inner length ldc
-    if (w.ks <= 1) return qs_launch_project_fp32(w.T, d, (int)w.ldc, w.C, P, w.Gm, w.ldg, st);
-    dim3 g((unsigned)((P + SK_BM - 1) / SK_BM), (unsigned)(w.ldg / SK_BN), (unsigned)w.ks);
-    gm_splitk_kernel<<<g, 256, 0, st>>>(w.C, P, w.ldc, w.T, d, w.kc, w.parts, w.ldg);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e == cudaSuccess) e = qs_launch_split_bf16(w.T, d, (int)w.ldc, (int)w.ldc, w.th, w.tl, st);
+    if (e == cudaSuccess) e = qs_launch_split_bf16(w.C, P, (int)w.ldc, (int)w.ldc, w.wh, w.wl, st);
+    // Gm[p][j] = sum_q W[p][q] T[j][q]: the ranges on their own streams, forked from and
+    // joined back into st
+    if (e == cudaSuccess) e = cudaEventRecord(w.fork, st);
+    for (int z = 0; z < w.ks && e == cudaSuccess; ++z) {
+        const int64_t k0 = (int64_t)z * w.kc;
+        const int klen = (int)(w.ldc - k0 < w.kc ? w.ldc - k0 : w.kc);
+        float* out = w.ks > 1 ? w.parts + (size_t)z * P * w.ldg : w.Gm;
+        e = cudaStreamWaitEvent(w.ss[z], w.fork, 0);
+        if (e == cudaSuccess) e = qs_launch_project_tc(0, w.gm_maps[z], 0, d, klen, P, out, w.ldg, w.flag, w.ss[z], false);
+        if (e == cudaSuccess) e = cudaEventRecord(w.done[z], w.ss[z]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, w.done[z], 0);
+    }
+    if (e != cudaSuccess || w.ks <= 1) return e;
     const int64_t n = (int64_t)P * w.ldg;
     gm_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w.parts, w.ks, n, w.Gm);
     return cudaGetLastError();
+}
+
+// The GEMM's timeout flag after the stream has finished (0: none)
+bool gemm_timed_out(const DesignWork& w)
+{
+    unsigned int f = 0;
+    return cudaMemcpy(&f, w.flag, sizeof(f), cudaMemcpyDeviceToHost) != cudaSuccess || f != 0;
 }
 
 qs_status sum_energy(const DesignWork& w, int P, cudaStream_t st, double* energy)
@@ -350,7 +372,8 @@ extern "C" qs_status qs_distance_energy(const float* dirs_dev, int d, int P, dou
     cudaStream_t st = (cudaStream_t)stream;
     DesignWork w;
     cudaError_t e = w.alloc(d, P, false);
-    if (e != cudaSuccess) return design_fail(QS_ERR_OOM, "qs_distance_energy: workspace allocation failed");
+    if (e != cudaSuccess)
+        return design_fail(QS_ERR_OOM, "qs_distance_energy: workspace allocation or tensor-map setup failed");
     e = esym_pieces(dirs_dev, d, P, w, st, true);
     if (e == cudaSuccess && grad_dev) {
         // m == NULL: the kernel only reads xi and writes the gradient
@@ -361,6 +384,7 @@ extern "C" qs_status qs_distance_energy(const float* dirs_dev, int d, int P, dou
     if (e != cudaSuccess) return design_fail(QS_ERR_CUDA, cudaGetErrorString(e));
     double E = 0.0;
     if (sum_energy(w, P, st, &E) != QS_OK) return design_fail(QS_ERR_CUDA, "qs_distance_energy: readback");
+    if (gemm_timed_out(w)) return design_fail(QS_ERR_CUDA, "qs_distance_energy: tensor-core GEMM timed out");
     if (energy) *energy = E;
     return QS_OK;
 }
@@ -375,7 +399,8 @@ extern "C" qs_status qs_distance_design(float* dirs_dev, int d, int P, int iters
     cudaStream_t st = (cudaStream_t)stream;
     DesignWork w;
     cudaError_t e = w.alloc(d, P, true);
-    if (e != cudaSuccess) return design_fail(QS_ERR_OOM, "qs_distance_design: workspace allocation failed");
+    if (e != cudaSuccess)
+        return design_fail(QS_ERR_OOM, "qs_distance_design: workspace allocation or tensor-map setup failed");
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     double b1t = 1.0, b2t = 1.0;
     for (int it = 0; it < iters && e == cudaSuccess; ++it) {
@@ -396,5 +421,6 @@ extern "C" qs_status qs_distance_design(float* dirs_dev, int d, int P, int iters
         return design_fail(QS_ERR_CUDA, "qs_distance_design: readback");
     if (!energy && cudaStreamSynchronize(st) != cudaSuccess)
         return design_fail(QS_ERR_CUDA, "qs_distance_design: synchronise");
+    if (gemm_timed_out(w)) return design_fail(QS_ERR_CUDA, "qs_distance_design: tensor-core GEMM timed out");
     return QS_OK;
 }
