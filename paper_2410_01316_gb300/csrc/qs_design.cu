@@ -17,6 +17,7 @@
 // taking 2 - 2c from the split-BF16 Gram moved the gradient by 6.5e-4 of its
 // largest entry), so the weights take |xi_p -+ xi_q|^2 from the rows for
 // |c| > 1/2 (esym_weights_kernel).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -33,8 +34,9 @@ qs_status design_fail(qs_status s, const char* msg)
     return s;
 }
 
-// Row p of the Gram matrix C (stride ldc) -> weights W = B - A in place,
-// zero in the padding columns P .. ldc-1; r_p; and (ENERGY) the row's share of
+// Row p of the Gram matrix C (stride ldc) -> weights W = B - A as the split
+// BF16 operands of the second contraction (hi = bf16(W), lo = bf16(W - hi);
+// zero in the padding columns P .. ldc-1); r_p; and (ENERGY) the row's share of
 // the energy, sum_q (|xi_p - xi_q| + |xi_p + xi_q|), in FP64.  One CTA per row.
 // |xi_p -+ xi_q|^2 is 2 -+ 2 c_pq except for near-parallel (c > 1/2) or
 // near-antipodal (c < -1/2) pairs, where it is summed from the rows
@@ -44,20 +46,25 @@ qs_status design_fail(qs_status s, const char* msg)
 // per pair would cost about as much as the step's contractions on this GPU's
 // FP64 pipe.
 template <bool ENERGY>
-__global__ void __launch_bounds__(256) esym_weights_kernel(float* __restrict__ C, int P, int64_t ldc,
+__global__ void __launch_bounds__(256) esym_weights_kernel(const float* __restrict__ C, int P, int64_t ldc,
                                                            const float* __restrict__ xi, int d,
+                                                           __nv_bfloat16* __restrict__ wh,
+                                                           __nv_bfloat16* __restrict__ wl,
                                                            float* __restrict__ r, double* __restrict__ e_row)
 {
     extern __shared__ float xp[];  // row p of xi
     const int p = blockIdx.x;
     for (int j = threadIdx.x; j < d; j += blockDim.x) xp[j] = xi[(size_t)p * d + j];
     __syncthreads();
-    float* row = C + (size_t)p * ldc;
+    const float* row = C + (size_t)p * ldc;
+    __nv_bfloat16* hrow = wh + (size_t)p * ldc;
+    __nv_bfloat16* lrow = wl + (size_t)p * ldc;
     float racc = 0.0f;
     double eacc = 0.0;
     for (int64_t q = threadIdx.x; q < ldc; q += blockDim.x) {
         if (q >= P) {
-            row[q] = 0.0f;
+            hrow[q] = __float2bfloat16_rn(0.0f);
+            lrow[q] = __float2bfloat16_rn(0.0f);
             continue;
         }
         const float c = fminf(1.0f, fmaxf(-1.0f, row[q]));
@@ -76,7 +83,10 @@ __global__ void __launch_bounds__(256) esym_weights_kernel(float* __restrict__ C
         // coincident or antipodal pairs have no gradient direction: weight 0
         const float a = (q == p || dm2 <= 0.0f) ? 0.0f : rsqrtf(dm2);
         const float b = dp2 > 0.0f ? rsqrtf(dp2) : 0.0f;
-        row[q] = b - a;
+        const float wv = b - a;
+        const __nv_bfloat16 h = __float2bfloat16_rn(wv);
+        hrow[q] = h;
+        lrow[q] = __float2bfloat16_rn(wv - __bfloat162float(h));
         racc += a + b;
         if (ENERGY) eacc += (q == p ? 0.0 : sqrt((double)dm2)) + sqrt((double)dp2);
     }
@@ -308,15 +318,16 @@ cudaError_t esym_pieces(const float* xi, int d, int P, DesignWork& w, cudaStream
             e = cudaFuncSetAttribute(esym_weights_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
         if (e != cudaSuccess) return e;
     }
-    if (energy) esym_weights_kernel<true><<<P, 256, xs, st>>>(w.C, P, w.ldc, xi, d, w.r, w.e);
-    else esym_weights_kernel<false><<<P, 256, xs, st>>>(w.C, P, w.ldc, xi, d, w.r, w.e);
+    __nv_bfloat16* wh = static_cast<__nv_bfloat16*>(w.wh);
+    __nv_bfloat16* wl = static_cast<__nv_bfloat16*>(w.wl);
+    if (energy) esym_weights_kernel<true><<<P, 256, xs, st>>>(w.C, P, w.ldc, xi, d, wh, wl, w.r, w.e);
+    else esym_weights_kernel<false><<<P, 256, xs, st>>>(w.C, P, w.ldc, xi, d, wh, wl, w.r, w.e);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 tg((unsigned)((w.ldc + 31) / 32), (unsigned)((d + 31) / 32));
     transpose_pad_kernel<<<tg, dim3(32, 8), 0, st>>>(xi, P, d, w.ldc, w.T);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = qs_launch_split_bf16(w.T, d, (int)w.ldc, (int)w.ldc, w.th, w.tl, st);
-    if (e == cudaSuccess) e = qs_launch_split_bf16(w.C, P, (int)w.ldc, (int)w.ldc, w.wh, w.wl, st);
     // Gm[p][j] = sum_q W[p][q] T[j][q]: the ranges on their own streams, forked from and
     // joined back into st
     if (e == cudaSuccess) e = cudaEventRecord(w.fork, st);
