@@ -166,11 +166,12 @@ qs_status qs_sum(qs_plan plan, const float* x, int64_t N, const float* w,
  *   gw[n] = dL/dw_n = (1/P) sum_p sum_m v_m g(a_{n,p} - b_{m,p})
  * computed by the same spread / FFT / interpolation pipeline with the filter
  * 2 pi i k c_k / psi^2 and a back-projection onto the directions (x and w
- * swap roles with y and v).  For d <= 32 the back-projection is summed inside
- * the interpolation, per component; for d > 32 the derivative values of
- * every (point, slice) pair are written over the plan's projection buffer
- * and back-projected by a GEMM (points x P)(P x d), which needs an unfused
- * projection form (QS_PROJ_FP32, QS_PROJ_BF16X3, QS_PROJ_TF32).  x: N x d,
+ * swap roles with y and v).  The unfused projection forms (QS_PROJ_FP32,
+ * QS_PROJ_BF16X3, QS_PROJ_TF32) write the derivative values of every
+ * (point, slice) pair over the plan's projection buffer and back-project them
+ * by a GEMM (points x P)(P x d) with compensated slice-chunk sums; the fused
+ * form, which has no projection buffer, sums the back-projection inside the
+ * interpolation per component and so needs d <= 32.  x: N x d,
  * w: N (NULL = ones), y: M x d, v: M (NULL = ones), gx: N x d, gw: N,
  * gy: M x d; all device memory; any output may be NULL to skip it.
  * Asynchronous on `stream`, allocates nothing.  Errors: QS_ERR_ARG,

@@ -782,65 +782,94 @@ __global__ void __launch_bounds__(256) interp_deriv_kernel(qs_launch L, const fl
 
 // out[m][j] = scale * fac_m * sum_p Q[p][m] xi[p][j] for m < M, j < d: the
 // back-projection onto the directions as a GEMM (M x P)(P x d), Q slice-major
-// with row stride ldQ, xi P x d row-major.  CTA tile: 128 targets x 64
-// components, 256 threads with 8 x 4 outputs each; the slices go in chunks of
-// 16 staged in shared memory (both operands coalesced), each chunk's products
+// with row stride ldQ, xi P x d row-major.  CTA tile: BP_TM targets x TN
+// components (TN = 16, 32 or 64, the smallest covering d up to 64), 256
+// threads with RM x 4 outputs each; the slices go in chunks of 16 staged in
+// shared memory (both operands coalesced, the next chunk fetched into
+// registers during the current one), each chunk's products
 // summed by FMA in slice order and the chunk sums accumulated by TwoSum, so
 // the result does not depend on the tiling and is reproducible.
-constexpr int BP_TM = 128, BP_TN = 64, BP_TK = 16;
+constexpr int BP_TK = 16;
 
+template <int TN, int RM>
 __global__ void __launch_bounds__(256) backproj_kernel(const float* __restrict__ Q, int64_t ldQ, int64_t M, int P,
                                                        const float* __restrict__ xi, int d, float scale,
                                                        const float* __restrict__ fac, float* __restrict__ out)
 {
+    constexpr int GX = TN / 4, BP_TN = TN, BP_TM = RM * 256 / GX;
+    constexpr int NA = BP_TK * BP_TM / 256, NB = (BP_TK * BP_TN + 255) / 256;  // operand elements per thread
     __shared__ __align__(16) float As[BP_TK][BP_TM];
     __shared__ __align__(16) float Bs[BP_TK][BP_TN];
     const int64_t m0 = (int64_t)blockIdx.x * BP_TM;
     const int j0 = blockIdx.y * BP_TN;
-    const int tx = threadIdx.x & 15;  // components j0 + 4 tx .. + 3
-    const int ty = threadIdx.x >> 4;  // targets m0 + 8 ty .. + 7
-    float hi[8][4], lo[8][4];
+    const int tx = threadIdx.x % GX;  // components j0 + 4 tx .. + 3
+    const int ty = threadIdx.x / GX;  // targets m0 + RM ty .. + RM - 1
+    float hi[RM][4], lo[RM][4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < RM; ++i)
 #pragma unroll
         for (int k = 0; k < 4; ++k) hi[i][k] = lo[i][k] = 0.0f;
-    for (int p0 = 0; p0 < P; p0 += BP_TK) {
-        for (int i = threadIdx.x; i < BP_TK * BP_TM; i += blockDim.x) {
-            const int r = i / BP_TM, c = i - r * BP_TM;
+    // the next chunk's operands are fetched into registers while the current one is used
+    float pa[NA], pb[NB];
+    auto fetch = [&](int p0) {
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+            const int i = threadIdx.x + 256 * q, r = i / BP_TM, c = i - r * BP_TM;
             const int64_t m = m0 + c;
-            As[r][c] = (p0 + r < P && m < M) ? __ldg(&Q[(size_t)(p0 + r) * ldQ + m]) : 0.0f;
+            pa[q] = (p0 + r < P && m < M) ? __ldg(&Q[(size_t)(p0 + r) * ldQ + m]) : 0.0f;
         }
-        for (int i = threadIdx.x; i < BP_TK * BP_TN; i += blockDim.x) {
-            const int r = i / BP_TN, c = i - r * BP_TN;
-            Bs[r][c] = (p0 + r < P && j0 + c < d) ? __ldg(&xi[(size_t)(p0 + r) * d + j0 + c]) : 0.0f;
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int i = threadIdx.x + 256 * q, r = i / BP_TN, c = i - r * BP_TN;
+            pb[q] = (i < BP_TK * BP_TN && p0 + r < P && j0 + c < d) ? __ldg(&xi[(size_t)(p0 + r) * d + j0 + c]) : 0.0f;
+        }
+    };
+    fetch(0);
+    for (int p0 = 0; p0 < P; p0 += BP_TK) {
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+            const int i = threadIdx.x + 256 * q, r = i / BP_TM;
+            As[r][i - r * BP_TM] = pa[q];
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int i = threadIdx.x + 256 * q, r = i / BP_TN;
+            if (i < BP_TK * BP_TN) Bs[r][i - r * BP_TN] = pb[q];
         }
         __syncthreads();
-        float acc[8][4];
+        if (p0 + BP_TK < P) fetch(p0 + BP_TK);
+        float acc[RM][4];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < RM; ++i)
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[i][k] = 0.0f;
 #pragma unroll 4
         for (int r = 0; r < BP_TK; ++r) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&As[r][8 * ty]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&As[r][8 * ty + 4]);
+            float a[RM];
+#pragma unroll
+            for (int q = 0; q < RM; q += 4) {
+                const float4 a4 = *reinterpret_cast<const float4*>(&As[r][RM * ty + q]);
+                a[q] = a4.x;
+                a[q + 1] = a4.y;
+                a[q + 2] = a4.z;
+                a[q + 3] = a4.w;
+            }
             const float4 b = *reinterpret_cast<const float4*>(&Bs[r][4 * tx]);
-            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float bb[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < RM; ++i)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(a[i], bb[k], acc[i][k]);
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < RM; ++i)
 #pragma unroll
             for (int k = 0; k < 4; ++k) qs_two_sum(hi[i][k], lo[i][k], acc[i][k]);
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int64_t m = m0 + 8 * ty + i;
+    for (int i = 0; i < RM; ++i) {
+        const int64_t m = m0 + RM * ty + i;
         if (m >= M) break;
         const float f = scale * (fac ? __ldg(&fac[m]) : 1.0f);
 #pragma unroll
@@ -1362,8 +1391,17 @@ cudaError_t qs_launch_backproj(const float* Q, int64_t ldQ, int64_t M, int P, co
                                const float* fac, float* out, cudaStream_t st)
 {
     if (M <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((M + BP_TM - 1) / BP_TM), (unsigned)((d + BP_TN - 1) / BP_TN));
-    backproj_kernel<<<grid, 256, 0, st>>>(Q, ldQ, M, P, xi, d, scale, fac, out);
+    // tiles (targets x components): 256 x 16 and 128 x 32 (4 x 4 outputs per thread), 128 x 64 (8 x 4)
+    if (d <= 16) {
+        dim3 grid((unsigned)((M + 255) / 256), (unsigned)((d + 15) / 16));
+        backproj_kernel<16, 4><<<grid, 256, 0, st>>>(Q, ldQ, M, P, xi, d, scale, fac, out);
+    } else if (d <= 32) {
+        dim3 grid((unsigned)((M + 127) / 128), (unsigned)((d + 31) / 32));
+        backproj_kernel<32, 4><<<grid, 256, 0, st>>>(Q, ldQ, M, P, xi, d, scale, fac, out);
+    } else {
+        dim3 grid((unsigned)((M + 127) / 128), (unsigned)((d + 63) / 64));
+        backproj_kernel<64, 8><<<grid, 256, 0, st>>>(Q, ldQ, M, P, xi, d, scale, fac, out);
+    }
     return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ constexpr int QS_MAX_HALF = QS_MAX_W / 2;
 constexpr int QS_MAX_TERMS = QS_MAX_HALF + 1;  // terms per even / odd part
 constexpr int QS_MAX_G = 16384;                // grid cells per slice (64 KB shared)
 constexpr int QS_FUSED_MAX_D = 64;             // largest d of the fused form
-constexpr int QS_GRAD_MAX_D = 32;              // largest d of the fused back-projection (larger: a GEMM)
+constexpr int QS_GRAD_MAX_D = 32;              // largest d of the fused form's gradients (per-component sums)
 constexpr int QS_BATCH_MAX_D = 64;             // largest d of a batched problem
 constexpr int QS_SOBOL_MAX_D = 4096;           // largest d of the Sobol' directions
 constexpr int QS_BATCH_STREAMS = 8;            // streams of a batch's concurrent mode
@@ -133,7 +133,7 @@ struct qs_plan_s {
     float* d_part;
     unsigned int* d_flag;
     float* d_wscale;      // 2 floats, written by the weight-bound kernel of each sum
-    // gradients (d <= 32): derivative filter, second grid, vector partials
+    // gradients: derivative filter, second grid; per-component partials (fused form, d <= 32)
     float* d_Dd;          // G/2 + 1
     float* d_H2;          // P x G
     float* d_gpart;       // 2 x (S M)max x d
@@ -288,7 +288,7 @@ cudaError_t qs_launch_interp_grad(const qs_launch& L, int W, const float* y, con
                                   float* part, bool fused, cudaStream_t st);
 cudaError_t qs_launch_reduce_grad(const float* part, int S, int64_t M, int d, float scale, const float* fac,
                                   float* out, cudaStream_t st);
-// d > QS_GRAD_MAX_D: derivative interpolation written over L.U (targets [0, L.M)), then
+// unfused forms: derivative interpolation written over L.U (targets [0, L.M)), then
 // out[m][j] = scale fac_m sum_p Q[p][m] xi[p][j]
 cudaError_t qs_launch_interp_deriv(const qs_launch& L, int W, const float* Hd, cudaStream_t st);
 cudaError_t qs_launch_backproj(const float* Q, int64_t ldQ, int64_t M, int P, const float* xi, int d, float scale,

@@ -107,10 +107,12 @@ def test_autograd_function_backward_equals_qs_grad():
             assert torch.equal(t.grad, g[name]), name
 
 
-# d > 32: derivative values written over the projection buffer, back-projected
-# by the GEMM (points x P)(P x d); measured errors are printed, the bar is the
-# FP32 one (TF32 projections: 10x looser)
+# the unfused forms at d above the fused form's limit: derivative values written
+# over the projection buffer, back-projected by the GEMM (points x P)(P x d), as
+# they are at every d; measured errors are printed, the bar is the FP32 one
+# (TF32 projections: 10x looser)
 @pytest.mark.parametrize("kernel,kp,d,proj,tol", [("negdist", 0.0, 64, "fp32", TOL), ("gauss", 6.0, 64, "bf16x3", TOL),
+                                                  ("gauss", 3.0, 24, "fp32", TOL),
                                                   ("laplace", 0.15, 784, "bf16x3", TOL),
                                                   ("negdist", 0.0, 40, "tf32", 10 * TOL)])
 def test_grad_large_dimension_by_back_projection_gemm(kernel, kp, d, proj, tol):
