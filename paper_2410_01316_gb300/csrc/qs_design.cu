@@ -61,34 +61,39 @@ __global__ void __launch_bounds__(256) esym_weights_kernel(const float* __restri
     __nv_bfloat16* lrow = wl + (size_t)p * ldc;
     float racc = 0.0f;
     double eacc = 0.0;
-    for (int64_t q = threadIdx.x; q < ldc; q += blockDim.x) {
-        if (q >= P) {
-            hrow[q] = __float2bfloat16_rn(0.0f);
-            lrow[q] = __float2bfloat16_rn(0.0f);
-            continue;
-        }
-        const float c = fminf(1.0f, fmaxf(-1.0f, row[q]));
-        float dm2 = 2.0f - 2.0f * c, dp2 = 2.0f + 2.0f * c;
-        if (c > 0.5f || c < -0.5f) {
-            const float sg = c > 0.0f ? -1.0f : 1.0f;  // xi_p - xi_q or xi_p + xi_q
-            const float* xq = xi + (size_t)q * d;
-            float s2 = 0.0f;
-            for (int j = 0; j < d; ++j) {
-                const float t = fmaf(sg, __ldg(&xq[j]), xp[j]);
-                s2 = fmaf(t, t, s2);
+    // two columns per thread and step (8-byte loads, 4-byte stores of each BF16 pair)
+    for (int64_t q0 = 2 * (int64_t)threadIdx.x; q0 < ldc; q0 += 2 * (int64_t)blockDim.x) {
+        const float2 c2 = *reinterpret_cast<const float2*>(row + q0);
+        float wv[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t q = q0 + h;
+            wv[h] = 0.0f;
+            if (q >= P) continue;
+            const float c = fminf(1.0f, fmaxf(-1.0f, h ? c2.y : c2.x));
+            float dm2 = 2.0f - 2.0f * c, dp2 = 2.0f + 2.0f * c;
+            if (c > 0.5f || c < -0.5f) {
+                const float sg = c > 0.0f ? -1.0f : 1.0f;  // xi_p - xi_q or xi_p + xi_q
+                const float* xq = xi + (size_t)q * d;
+                float s2 = 0.0f;
+                for (int j = 0; j < d; ++j) {
+                    const float t = fmaf(sg, __ldg(&xq[j]), xp[j]);
+                    s2 = fmaf(t, t, s2);
+                }
+                if (c > 0.0f) dm2 = s2;
+                else dp2 = s2;
             }
-            if (c > 0.0f) dm2 = s2;
-            else dp2 = s2;
+            // coincident or antipodal pairs have no gradient direction: weight 0
+            const float a = (q == p || dm2 <= 0.0f) ? 0.0f : rsqrtf(dm2);
+            const float b = dp2 > 0.0f ? rsqrtf(dp2) : 0.0f;
+            wv[h] = b - a;
+            racc += a + b;
+            if (ENERGY) eacc += (q == p ? 0.0 : sqrt((double)dm2)) + sqrt((double)dp2);
         }
-        // coincident or antipodal pairs have no gradient direction: weight 0
-        const float a = (q == p || dm2 <= 0.0f) ? 0.0f : rsqrtf(dm2);
-        const float b = dp2 > 0.0f ? rsqrtf(dp2) : 0.0f;
-        const float wv = b - a;
-        const __nv_bfloat16 h = __float2bfloat16_rn(wv);
-        hrow[q] = h;
-        lrow[q] = __float2bfloat16_rn(wv - __bfloat162float(h));
-        racc += a + b;
-        if (ENERGY) eacc += (q == p ? 0.0 : sqrt((double)dm2)) + sqrt((double)dp2);
+        const __nv_bfloat162 hv = __floats2bfloat162_rn(wv[0], wv[1]);
+        const float2 hf = __bfloat1622float2(hv);
+        *reinterpret_cast<__nv_bfloat162*>(hrow + q0) = hv;
+        *reinterpret_cast<__nv_bfloat162*>(lrow + q0) = __floats2bfloat162_rn(wv[0] - hf.x, wv[1] - hf.y);
     }
     __shared__ float rs[8];
     __shared__ double es[8];
