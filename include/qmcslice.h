@@ -432,11 +432,12 @@ qs_status qs_plan_gemm(qs_plan plan, int* pair, int* ctas);
  * and target projections (FP32, from the FP32 SIMT projection) together and
  * scanning prefix sums of w and w a in 64-bit fixed point (exact integer
  * sums with per-slice scales, combined per target in error-free FP32
- * arithmetic): sum_n w_n |b - a_n| = b (2 W_< - W) - (2 S_< - S).  Arguments as for qs_sum.  Needs a QS_NEGDIST
- * plan with d <= 64 (QS_ERR_UNSUPPORTED otherwise).  The first call allocates
- * the plan's sorting workspace (about 20 CS (max_n + max_m) + 8 CS max_m
- * bytes, CS = min(P, 128) slices per chunk) and so synchronises; later calls
- * are asynchronous and allocate nothing.  Data errors (non-finite
+ * arithmetic): sum_n w_n |b - a_n| = b (2 W_< - W) - (2 S_< - S).
+ * Arguments as for qs_sum.  Needs a QS_NEGDIST plan with d <= 64
+ * (QS_ERR_UNSUPPORTED otherwise).  The first call allocates the plan's
+ * sorting workspace (about 21 CS (max_n + max_m) + 4 CS max_m + 512 max_m
+ * bytes, CS = min(P, 128) slices per chunk) and so synchronises; later
+ * calls are asynchronous and allocate nothing.  Data errors (non-finite
  * projections or weights) go to the device flag.
  */
 qs_status qs_sum_sorted(qs_plan plan, const float* x, int64_t N, const float* w, const float* y, int64_t M,
