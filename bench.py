@@ -1096,7 +1096,7 @@ def launches_per_step(plan) -> int:
 # (d = 784, N = M = 60000, P = 2048, N_ft = 1024, BF16x3 on the SM-pair GEMM, momentwin32
 # spread, 8 targets per interpolation thread; profiles/traffic_mnist_laplace.md).  Only for
 # that configuration and the kernels as captured.
-TRAFFIC_MNIST = {"project_x": 636.4e6, "project_y": 633.4e6, "spread_filter": 504.3e6, "interp": 520.9e6}
+TRAFFIC_MNIST = {"project_x": 636.4e6, "project_y": 633.4e6, "spread_filter": 504.3e6, "interp": 520.4e6}
 
 
 def _traffic(prob, plan, name):
