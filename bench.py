@@ -1125,7 +1125,7 @@ def stage_rooflines(prob, plan, stages, clocks, peaks, peak_src, sm_count):
 
     for name, rows in (("project_x", N), ("project_y", M)):
         t = stages.get(name, 0.0) / 1e3
-        if t <= 0:
+        if t <= 0 or plan.proj == "fp32_fused":  # the fused form projects inside the spread and interpolation
             continue
         if plan.proj == "bf16x3":
             fl = 6.0 * rows * P * d
