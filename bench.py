@@ -1112,7 +1112,6 @@ def _traffic(prob, plan, name):
 def stage_rooflines(prob, plan, stages, clocks, peaks, peak_src, sm_count):
     """Roofline entry per stage, from the in-stream stage events (ms)."""
     mhz = clocks.get("sm_mhz") or 2070.0
-    smem_lanes = 32.0 * sm_count * mhz * 1e6  # one conflict-free 32-lane shared wavefront per SM per clock
     fp32_peak = sm_count * 128 * 2 * mhz * 1e6 / 1e12
     N, M, P, d, W, G = prob.N, prob.M, prob.P, prob.d, prob.window, plan.G
     out = {}
@@ -1156,22 +1155,23 @@ def stage_rooflines(prob, plan, stages, clocks, peaks, peak_src, sm_count):
         out[name].update({"hbm_bytes": by, "hbm_algorithmic": what, "hbm_achieved_gbs": by / t_ / 1e9,
                           "hbm_frac": by / t_ / 1e9 / peaks["hbm_gbs"]})
 
-    t = stages.get("spread_filter", 0.0) / 1e3
-    if t > 0:
-        ops = float(N) * P * W
-        add("spread_filter", "alu", ops / t / 1e9, smem_lanes / 1e9, "Gop/s",
-            f"N P W = {ops:.3e} shared-memory atomic adds (grid accumulation)",
-            f"shared-memory pipe: 32 lanes x {sm_count} SMs x {mhz:.0f} MHz")
+    # spread and interpolation: unfused, bound by their HBM stream (U, weights, rows); fused, by the
+    # FP32 dot products of the projection they contain
+    for name, by, what, rows in (
+            ("spread_filter", 4.0 * N * P + 4.0 * N + 4.0 * P * G,
+             "4 N P (U) + 4 N (w) read, 4 P G (filtered rows) written", N),
+            ("interp", 4.0 * M * P + 4.0 * P * G, "4 M P (U) + 4 P G (filtered rows) read", M)):
+        t = stages.get(name, 0.0) / 1e3
+        if t <= 0:
+            continue
         if unfused:
-            hbm("spread_filter", 4.0 * N * P + 4.0 * N + 4.0 * P * G,
-                "4 N P (U) + 4 N (w) read, 4 P G (filtered rows) written")
-    t = stages.get("interp", 0.0) / 1e3
-    if t > 0:
-        ops = float(M) * P * W
-        add("interp", "alu", ops / t / 1e9, smem_lanes / 1e9, "Gop/s",
-            f"M P W = {ops:.3e} shared-memory tap reads", f"shared-memory pipe: 32 lanes x {sm_count} SMs x {mhz:.0f} MHz")
-        if unfused:
-            hbm("interp", 4.0 * M * P + 4.0 * P * G, "4 M P (U) + 4 P G (filtered rows) read")
+            add(name, "hbm", by / t / 1e9, peaks["hbm_gbs"], "GB/s", f"{what} = {by:.3e} B", f"hbm_gbs ({peak_src})")
+            hbm(name, by, what)
+        else:
+            fl = 2.0 * rows * P * d
+            add(name, "alu", fl / t / 1e12, fp32_peak, "TFLOP/s",
+                f"2 {'N' if name == 'spread_filter' else 'M'} P d = {fl:.3e} FP32 flop (the projection inside the kernel)",
+                f"{sm_count} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz")
     return out
 
 
