@@ -36,6 +36,24 @@ def test_energy_and_gradient_match_oracle(P, d):
     assert np.max(np.abs(g - go)) <= 1e-4 * np.max(np.abs(go))
 
 
+def test_energy_and_gradient_with_near_parallel_and_near_antipodal_pairs():
+    # |c_pq| > 1/2 takes the squared distance from the rows (c near 1 or -1 would otherwise
+    # amplify the Gram matrix's rounding in the weights); pairs at 1e-2 .. 1e-1 radians of each
+    # other or of each other's antipode, mixed with unrelated directions
+    rng = np.random.default_rng(21)
+    d, k = 6, 60
+    base = _unit(rng, k, d).astype(np.float64)
+    near = base + rng.uniform(1e-2, 1e-1, (k, 1)) * _unit(rng, k, d).astype(np.float64)
+    anti = -base + rng.uniform(1e-2, 1e-1, (k, 1)) * _unit(rng, k, d).astype(np.float64)
+    x = np.concatenate([base, near, anti, _unit(rng, 90, d).astype(np.float64)])
+    x = (x / np.linalg.norm(x, axis=1, keepdims=True)).astype(np.float32)
+    E, g = distance_energy(_cuda(x), grad=True)
+    Eo, go = oracle.esym(x)
+    assert E == pytest.approx(Eo, rel=2e-6)
+    g = g.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(g - go)) <= 1e-4 * np.max(np.abs(go))
+
+
 @pytest.mark.parametrize("P,d", [(8, 16), (16, 16), (3, 3)])
 def test_optimiser_reaches_orthonormal_minimum_when_p_le_d(P, d):
     x = _cuda(_unit(np.random.default_rng(11), P, d))
